@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the MSz correction loop on one GB300 (or N independent replicas).
+
+Workload: a 512^3 float32 turbulence-like field (256 random-phase sinusoidal
+modes, |k| log-uniform in [1, 64] cycles per box, amplitude |k|^-5/6, seed 3),
+decompressed by the uniform quantiser at xi = {1e-3, 1e-4, 1e-5} x range.
+A step is one full correction (msz_fix: C-loops and R-loops to zero false
+critical points and zero wrong labels, then the edit list) with inputs
+resident in HBM; step k uses bound k mod 3. The metric is vertices per
+second of full fixes (Mvertices/s); inputs (2 x 537 MB) exceed L2 (129 MB),
+so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank corrects its own replica: fields are
+independent units, there is no collective on the data path ("replicas only");
+the timed region is bracketed by barriers and the slowest rank's time is used.
+--impl reference times the CPU oracle (the plain restatement the tests use)
+on a bounded crop of the same workload on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+RELS = (1e-3, 1e-4, 1e-5)
+METRIC = "Mvertices/s of full MSz fix to 0 mismatches (512³ f32); batched vs plain; p99"
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join("/tmp", f"msz_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd.insert(1, f"--id={self.uuid}")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def make_workload(torch, dev, size):
+    from paper_2406_09423_gb300 import synth
+
+    f = synth.turbulence3d(size, 3, device=dev)
+    cases = []
+    for rel in RELS:
+        xi = synth.xi_for(f, rel)
+        cases.append((rel, xi, synth.quantise_torch(f, xi)))
+    torch.cuda.synchronize()
+    return f, cases
+
+
+def oracle_sample(f, cases, crop, max_seconds=30.0):
+    """Times the CPU oracle on the leading crop^3 block of the workload, one
+    fix per bound; returns (Mvertices/s, seconds, description)."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    tot_v, tot_s, done = 0, 0.0, []
+    fc = np.ascontiguousarray(f[:crop, :crop, :crop].cpu().numpy())
+    for rel, xi, fh in cases:
+        hc = np.ascontiguousarray(fh[:crop, :crop, :crop].cpu().numpy())
+        t = time.perf_counter()
+        r = oracle.fix(fc, hc, xi)
+        dt = time.perf_counter() - t
+        assert r.status == 0
+        tot_v += fc.size
+        tot_s += dt
+        done.append(rel)
+        if tot_s > max_seconds:
+            break
+    desc = (f"oracle fix of the leading {crop}^3 block of the 512^3 field "
+            f"({fc.size} vertices) at xi/range in {done}, single thread")
+    return tot_v / tot_s / 1e6, tot_s, desc
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import torch
+
+    dev = torch.device("cuda", local) if torch.cuda.is_available() else torch.device("cpu")
+    f, cases = make_workload(torch, dev if dev.type == "cuda" else None, args.size) if dev.type == "cuda" \
+        else _cpu_workload(args.size)
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(f, cases[:1], args.crop)
+    times = []
+    for k in range(args.steps):
+        v, s, desc = oracle_sample(f, [cases[k % 3]], args.crop)
+        vals.append(v)
+        times.append(s)
+    value = sum(args.crop ** 3 for _ in times) / sum(times) / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mvertices/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"turbulence {args.size}^3 f32, xi/range in {list(RELS)}, crop {args.crop}^3",
+                   "l2": "inputs > L2"},
+        "cpu_baseline": {"value": value, "unit": "Mvertices/s", "cores": 1, "kind": "oracle",
+                         "sample": f"leading {args.crop}^3 block of the workload, one bound per step"},
+        "e2e": {"value": value, "unit": "Mvertices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _cpu_workload(size):
+    from paper_2406_09423_gb300 import synth
+    import torch
+
+    f = torch.from_numpy(synth.turbulence3d(size, 3, shape=(64, 64, 64)))
+    cases = []
+    for rel in RELS:
+        xi = synth.xi_for(f, rel)
+        cases.append((rel, xi, torch.from_numpy(synth.quantise(f.numpy(), xi))))
+    return f, cases
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=9)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=512)
+    ap.add_argument("--crop", type=int, default=64, help="oracle sample block edge")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_2406_09423_gb300 as msz
+    from paper_2406_09423_gb300 import native
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    f, cases = make_workload(torch, dev, args.size)
+    n = f.numel()
+    plan = msz.Plan(tuple(f.shape), f.dtype, time_kernels=True)
+    for k in range(args.warmup):
+        rel, xi, fh = cases[k % 3]
+        plan.fix(f, fh, xi, copy=False)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    time.sleep(0.3)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    per_step, launches, kernel_ms, sweeps, counts = [], 0, {}, 0, []
+    barrier()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        rel, xi, fh = cases[k % 3]
+        r = plan.fix(f, fh, xi, copy=False)
+        ev[k + 1].record(stream)
+        launches += r.launches
+        sweeps += r.counts["sweeps"]
+        for key, val in r.kernel_ms.items():
+            kernel_ms[key] = kernel_ms.get(key, 0.0) + val
+        counts.append((rel, r.counts, r.n_edits))
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    total_ms = ev[0].elapsed_time(ev[-1])
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    if pg is not None:
+        t = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * n / (total_ms / 1e3) / 1e6
+
+    # End to end through the host-buffer entry point (msz_fix_host): every step
+    # copies f and fhat from pinned host memory and the edit list back.
+    e2e = None
+    if not args.no_e2e:
+        f_h = f.cpu().pin_memory()
+        fh_h = [fh.cpu().pin_memory() for _, _, fh in cases]
+        idx_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        val_h = torch.empty(n, dtype=torch.float32).pin_memory()
+        steps_e2e = 3
+        h2d = d2h = 0
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(steps_e2e):
+            rel, xi, _ = cases[k % 3]
+            r = native.msz_fix_host(plan._p, f_h.data_ptr(), fh_h[k % 3].data_ptr(), xi, idx_h.data_ptr(),
+                                    val_h.data_ptr(), 0, 0, stream.cuda_stream)
+            native.check(r.status, "msz_fix_host")
+            h2d += 2 * n * 4
+            d2h += int(r.n_edits) * 8
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        barrier()
+        e2e_ms = e0.elapsed_time(e1)
+        e2e = {"value": world * steps_e2e * n / (e2e_ms / 1e3) / 1e6, "unit": "Mvertices/s",
+               "h2d_bytes_per_step": h2d // steps_e2e, "d2h_bytes_per_step": d2h // steps_e2e,
+               "wall_s": wall, "steps": steps_e2e, "api": "msz_fix_host (pinned host buffers)"}
+
+    # Roofline of the dominant kernel (the C-loop sweep): algorithmic bytes per
+    # launch = N * (4 B of g + 0.25 B of packed extremum bits of f); duration =
+    # CUDA-event time of its launches on the fix stream / launches that swept.
+    pk = peaks()
+    peak_gbs = pk["hbm_gbs"] if pk else 6800.0
+    sweep_ms = kernel_ms.get("csweep", 0.0)
+    roofline = None
+    if sweep_ms > 0 and sweeps > 0:
+        bytes_per_launch = n * 4.25
+        avg_ms = sweep_ms / sweeps
+        ach = bytes_per_launch / (avg_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": ach, "peak": peak_gbs, "unit": "GB/s", "frac": ach / peak_gbs,
+                    "traffic": None, "kernel": "k_csweep<float,3,TMA>",
+                    "avg_launch_ms": avg_ms, "bytes_per_launch": bytes_per_launch,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if pk else "fallback 6.8 TB/s"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import multiprocessing
+
+        v, s, desc = oracle_sample(f, cases, args.crop)
+        cpu = {"value": v, "unit": "Mvertices/s", "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": s, "host_cores": multiprocessing.cpu_count()}
+
+    per_xi = {}
+    for (rel, c, ne), ms in zip(counts, step_ms):
+        d = per_xi.setdefault(str(rel), {"ms": [], "sweeps": c["sweeps"], "label_evals": c["label_evals"],
+                                         "edits": ne, "freezes": c["freezes"]})
+        d["ms"].append(ms)
+    for d in per_xi.values():
+        d["mvps"] = n / (statistics.median(d["ms"]) / 1e3) / 1e6
+    step_rates = sorted(n / (ms / 1e3) / 1e6 for ms in step_ms)
+    p50 = statistics.median(step_ms)
+    p99 = sorted(step_ms)[max(0, int(round(0.99 * len(step_ms))) - 1)]
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mvertices/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"turbulence {args.size}^3 f32 (256 modes, seed 3), uniform quantiser, "
+                                   f"xi/range cycling {list(RELS)}",
+                       "form": "plain (one field per msz_fix)", "parallelism": f"replicas x{world}",
+                       "l2": "inputs 2 x 537 MB > 129 MB L2, no flush"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "cpu_baseline": cpu,
+            "latency_ms": {"p50": p50, "p99": p99}, "per_xi": per_xi,
+            "step_mvps": {"min": step_rates[0], "max": step_rates[-1]},
+            "kernel_ms": kernel_ms,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

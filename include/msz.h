@@ -1,0 +1,157 @@
+/*
+ * msz.h: C ABI of the GB300 MSz correction library (libmsz.so).
+ *
+ * MSz (Li et al., "MSz: An Efficient Parallel Algorithm for Correcting
+ * Morse-Smale Segmentations in Error-Bounded Lossy Compressors") edits a
+ * decompressed scalar field fhat until the piecewise-linear Morse-Smale
+ * segmentation of the edited field g equals that of the original f, while
+ * every value stays within the absolute error bound xi (Sec. 3, "Problem
+ * Statement": |f_i - g_i| <= xi, M = Mhat, m = mhat). The edits are
+ * returned as a list of (vertex index, new value) pairs (Sec. 5.3) that
+ * msz_apply() writes into fhat on the decompression side (Fig. 3).
+ *
+ * Conventions shared by every entry point:
+ *   - Fields are dense 2D or 3D grids, x fastest: vertex (x, y, z) has the
+ *     linear index x + nx*(y + ny*z). dims[] = {nx, ny, nz}; for ndim == 2
+ *     dims[2] is ignored. Every extent is >= 1 and nx*ny*nz < 2^31.
+ *   - The mesh is the Freudenthal triangulation of the grid: the neighbours
+ *     of v are v + e and v - e for every nonzero e in {0,1}^ndim that stays
+ *     inside the grid (6 in 2D, 14 in 3D).
+ *   - Ties between equal values are broken by the linear index (the
+ *     simulation of simplicity of Sec. 3); IEEE comparison, so -0 == +0.
+ *   - xi is rounded once to the field's type; the lower bound of vertex i is
+ *     the smallest representable value >= f_i - xi.
+ *   - Pointers named *_dev are device pointers on the current CUDA device;
+ *     *_host are host pointers (pageable or pinned). Input buffers are
+ *     borrowed: they must stay valid and unmodified until the call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Every call returns when its results are ready.
+ *   - Errors are negative msz_status codes; no C++ exception crosses the ABI.
+ *     msz_strerror() names them.
+ */
+#ifndef MSZ_H_
+#define MSZ_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { MSZ_F32 = 0, MSZ_F64 = 1 } msz_dtype;
+
+typedef enum {
+  MSZ_OK = 0,
+  MSZ_ERR_ARG = -1,        /* bad argument: ndim, dims, NULL pointer, xi < 0 or not finite,
+                              or a lower bound f - xi that overflows */
+  MSZ_ERR_DTYPE = -2,      /* dtype is neither MSZ_F32 nor MSZ_F64 */
+  MSZ_ERR_NONFINITE = -3,  /* f or fhat holds a NaN or an infinity */
+  MSZ_ERR_BOUND = -4,      /* fhat violates |fhat - f| <= xi at some vertex */
+  MSZ_ERR_OOM = -5,        /* device or host allocation failed */
+  MSZ_ERR_NOCONVERGE = -6, /* round cap reached (msz_options.max_rounds) */
+  MSZ_ERR_TIMEOUT = -7,    /* a bounded device-side wait gave up */
+  MSZ_ERR_CUDA = -8,       /* a CUDA runtime call failed */
+  MSZ_ERR_BUSY = -9        /* server: no free slot / request id unknown or not finished */
+} msz_status;
+
+/* Counters of one fix. The same quantities are computed by the reference
+ * restatement of the method, so they are compared exactly in the tests. */
+typedef struct {
+  uint64_t sweeps;       /* evaluations of directions of a changed field */
+  uint64_t c_rounds[4];  /* C-loop edit rounds: FPmax, FPmin, FNmax, FNmin (Sec. 4.1) */
+  uint64_t c_cases[4];   /* false critical points edited, summed over those rounds */
+  uint64_t c_passes;     /* completed passes over the four C sub-loops */
+  uint64_t r_rounds;     /* R-loop edit rounds (Sec. 4.2) */
+  uint64_t r_cases[2];   /* troublemakers edited: wrong max label, wrong min label */
+  uint64_t label_evals;  /* max/min label computations of g */
+  uint64_t mismatch[2];  /* wrong max / min labels, summed over label computations */
+  uint64_t dec_edits;    /* decreasing edits applied (Eqs. 2-6) */
+  uint64_t freezes;      /* vertices reset to f by the termination guard */
+  uint64_t edits;        /* length of the final edit list */
+} msz_counts;
+
+/* msz_options.flags */
+#define MSZ_OPT_NO_TMA 1u        /* stage sweep planes with plain loads instead of TMA */
+#define MSZ_OPT_TIME_KERNELS 2u  /* fill msz_result.kernel_ms (CUDA events around each kernel kind) */
+
+typedef struct {
+  uint64_t max_rounds;   /* cap on C + R edit rounds; 0 = default (10^7) */
+  int32_t  label_tile;   /* reserved, 0 = automatic */
+  uint32_t flags;        /* MSZ_OPT_* bits */
+  int32_t  reserved[6];
+} msz_options;
+
+/* Results of msz_fix / msz_fix_host. For msz_fix the arrays are DEVICE
+ * memory owned by the plan: valid until the next msz_fix on that plan or
+ * msz_plan_destroy. For msz_fix_host they are the caller's host buffers. */
+typedef struct {
+  uint32_t* edit_idx;    /* n_edits vertex indices, strictly ascending */
+  void*     edit_val;    /* n_edits new values, the field's type */
+  uint64_t  n_edits;
+  int32_t*  label_max;   /* N labels: index of the maximum each vertex ascends to */
+  int32_t*  label_min;   /* N labels: index of the minimum each vertex descends to */
+  msz_counts counts;
+  int32_t   status;      /* msz_status of the fix */
+  float     device_ms;   /* device time of the fix (CUDA events), 0 if not timed */
+  uint64_t  launches;    /* kernels this library launched for the fix */
+  float     kernel_ms[4];/* with MSZ_OPT_TIME_KERNELS: summed device time of the C-loop sweep,
+                            label pointer jumping, R-loop check, and mark + apply kernels */
+} msz_result;
+
+typedef struct msz_plan_s* msz_plan;
+
+/* Allocates the device state for fields of one shape and type (Sec. 4 state:
+ * g, directions, labels of f and g, per-vertex flags, case and edit lists).
+ * opt may be NULL. Returns MSZ_ERR_OOM if device memory is insufficient. */
+int msz_plan_create(msz_plan* out, int ndim, const int64_t dims[3], int dtype,
+                    const msz_options* opt);
+
+/* Device bytes a plan of this shape and type allocates (for admission). */
+int64_t msz_plan_bytes(int ndim, const int64_t dims[3], int dtype);
+
+int msz_plan_destroy(msz_plan p);
+
+/* The correction loop (Sec. 4, Fig. 3 top): given the original field f and
+ * the decompressed field fhat (device, N values of the plan's type) and the
+ * bound xi, runs C-loops and R-loops until no false critical point and no
+ * wrong label is left, entirely on the device. Fills *out (device arrays
+ * owned by the plan). Returns out->status. */
+int msz_fix(msz_plan p, const void* orig_dev, const void* decomp_dev, double xi,
+            void* stream, msz_result* out);
+
+/* Same loop from host buffers: copies f and fhat to the plan's device
+ * buffers, runs msz_fix, and copies the edit list (and, if label_max_host /
+ * label_min_host are non-NULL, the labels) back. edit_idx_host / edit_val_host
+ * must hold N entries (the worst case). out->edit_idx / edit_val / label_*
+ * are set to the host buffers. */
+int msz_fix_host(msz_plan p, const void* orig_host, const void* decomp_host, double xi,
+                 uint32_t* edit_idx_host, void* edit_val_host, int32_t* label_max_host,
+                 int32_t* label_min_host, void* stream, msz_result* out);
+
+/* Decompression side (Fig. 3 bottom; g_i = fhat_i + delta_i, Sec. 3):
+ * writes edit_val[k] into decomp_dev[edit_idx[k]] for k < n_edits. Indices
+ * must be < N (checked on the device: out-of-range entries are skipped and
+ * MSZ_ERR_ARG is returned). n_edits == 0 is a no-op. */
+int msz_apply(void* decomp_dev, int ndim, const int64_t dims[3], int dtype,
+              const uint32_t* edit_idx_dev, const void* edit_val_dev, uint64_t n_edits,
+              void* stream);
+
+/* Directions of one field (the per-vertex step of Sec. 5.1 "Updating
+ * directions"): dir_dev[v] = ascending slot | descending slot << 4, where a
+ * slot s < 14 is the neighbour v + e_s (e_0..e_6 = (1,0,0), (0,1,0), (0,0,1),
+ * (1,1,0), (1,0,1), (0,1,1), (1,1,1); e_7..e_13 their negations; in 2D
+ * e_0..e_2 = (1,0), (0,1), (1,1) and e_3..e_5 their negations) and 15 is v
+ * itself (a maximum, resp. minimum). */
+int msz_directions(const void* field_dev, int ndim, const int64_t dims[3], int dtype,
+                   uint8_t* dir_dev, void* stream);
+
+const char* msz_strerror(int status);
+
+/* Library version string. */
+const char* msz_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSZ_H_ */

@@ -413,10 +413,10 @@ int fix_impl(int ndim, const int64_t* dims, const T* f, const T* fhat, double xi
   F.lb.resize(n);
   for (int64_t v = 0; v < n; ++v) {
     F.lb[v] = lower_bound_of(f[v], xi);
-    const T ub = upper_bound_of(f[v], xi);
-    if (!std::isfinite(F.lb[v])) return ST_ARG;
-    if (fhat[v] < F.lb[v] || fhat[v] > ub) return ST_BOUND;
+    if (!std::isfinite(F.lb[v])) return ST_ARG;  // f - xi overflows
   }
+  for (int64_t v = 0; v < n; ++v)
+    if (fhat[v] < F.lb[v] || fhat[v] > upper_bound_of(f[v], xi)) return ST_BOUND;
   for (int64_t v = 0; v < n; ++v) g_out[v] = fhat[v];  // g^(0) = fhat, Eq. (1)
   F.up_f.resize(n); F.dn_f.resize(n); F.up_g.resize(n); F.dn_g.resize(n);
   F.M.resize(n); F.m.resize(n); F.Mg.resize(n); F.mg.resize(n);

@@ -1,0 +1,135 @@
+"""GB300-native MSz: preserves the piecewise-linear Morse-Smale segmentation
+of a scalar field through error-bounded lossy compression by editing the
+decompressed field (Li et al., MSz, Sec. 4-5).
+
+The correction loop runs entirely in libmsz.so (hand-written CUDA for
+sm_103a, C ABI in include/msz.h). This package only moves torch tensors in
+and out of that library:
+
+    import torch, paper_2406_09423_gb300 as msz
+    res = msz.fix(f, fhat, xi)           # f, fhat: CUDA tensors (ny, nx) or (nz, ny, nx)
+    g = fhat.clone(); msz.apply(g, res.edit_idx, res.edit_val)
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+from . import native
+
+__all__ = ["Plan", "FixResult", "fix", "apply", "directions", "native"]
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+class _DeviceArray:
+    """__cuda_array_interface__ view of plan-owned device memory."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {
+            "shape": (n,), "typestr": typestr, "data": (int(ptr), False), "version": 3, "strides": None,
+        }
+
+
+def _view(torch, ptr, n, dtype):
+    typestr = {torch.float32: "<f4", torch.float64: "<f8", torch.int32: "<i4", torch.uint32: "<u4"}[dtype]
+    if n == 0 or not ptr:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    return torch.as_tensor(_DeviceArray(ptr, n, typestr), device="cuda")
+
+
+@dataclass
+class FixResult:
+    edit_idx: "object"     # int64 tensor (ascending vertex indices)
+    edit_val: "object"     # new values, field dtype
+    label_max: "object"    # int32 tensor, field shape
+    label_min: "object"
+    counts: dict
+    status: int
+    device_ms: float
+    launches: int = 0
+    kernel_ms: dict = None
+
+    @property
+    def n_edits(self) -> int:
+        return int(self.edit_idx.numel())
+
+
+class Plan:
+    """Device state for fields of one shape and dtype (msz_plan_create)."""
+
+    def __init__(self, shape, dtype, max_rounds: int = 0, use_tma: bool = True, time_kernels: bool = False):
+        self.shape = tuple(int(s) for s in shape)
+        self.dtype = dtype
+        flags = (0 if use_tma else native.MSZ_OPT_NO_TMA) | (native.MSZ_OPT_TIME_KERNELS if time_kernels else 0)
+        self._p = native.msz_plan_create(self.shape, dtype, max_rounds, flags)
+
+    def fix(self, f, fhat, xi: float, copy: bool = True, check: bool = True) -> FixResult:
+        torch = _torch()
+        if f.shape != fhat.shape or tuple(f.shape) != self.shape or f.dtype != fhat.dtype:
+            raise ValueError("f and fhat must match the plan's shape and dtype")
+        if not (f.is_cuda and fhat.is_cuda):
+            raise ValueError("f and fhat must be CUDA tensors")
+        f = f.contiguous()
+        fhat = fhat.contiguous()
+        stream = torch.cuda.current_stream().cuda_stream
+        r = native.msz_fix(self._p, f.data_ptr(), fhat.data_ptr(), xi, stream)
+        if check:
+            native.check(r.status, "msz_fix")
+        n = f.numel()
+        ne = int(r.n_edits) if r.status == 0 else 0
+        idx = _view(torch, r.edit_idx, ne, torch.int32)
+        val = _view(torch, r.edit_val, ne, f.dtype)
+        lmax = _view(torch, r.label_max, n if r.status == 0 else 0, torch.int32)
+        lmin = _view(torch, r.label_min, n if r.status == 0 else 0, torch.int32)
+        if copy:
+            idx, val, lmax, lmin = idx.long(), val.clone(), lmax.clone(), lmin.clone()
+        if r.status == 0:
+            lmax = lmax.view(self.shape)
+            lmin = lmin.view(self.shape)
+        kms = {k: float(v) for k, v in zip(native.KERNEL_KINDS, r.kernel_ms)}
+        return FixResult(idx, val, lmax, lmin, r.counts.as_dict(), int(r.status), float(r.device_ms),
+                         int(r.launches), kms)
+
+    def close(self):
+        if self._p:
+            native.msz_plan_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fix(f, fhat, xi: float, max_rounds: int = 0) -> FixResult:
+    """One-shot correction loop (plan + msz_fix + copy of the results)."""
+    plan = Plan(tuple(f.shape), f.dtype, max_rounds)
+    try:
+        return plan.fix(f, fhat, xi)
+    finally:
+        plan.close()
+
+
+def apply(decomp, edit_idx, edit_val) -> None:
+    """Writes the edits into ``decomp`` in place (msz_apply)."""
+    torch = _torch()
+    idx = edit_idx.to(device=decomp.device, dtype=torch.int32).contiguous()
+    val = edit_val.to(device=decomp.device, dtype=decomp.dtype).contiguous()
+    st = native.msz_apply(decomp.data_ptr(), tuple(decomp.shape), decomp.dtype, idx.data_ptr(),
+                          val.data_ptr(), int(idx.numel()), torch.cuda.current_stream().cuda_stream)
+    native.check(st, "msz_apply")
+
+
+def directions(field):
+    """Direction byte per vertex (ascending slot | descending slot << 4)."""
+    torch = _torch()
+    out = torch.empty(field.shape, dtype=torch.uint8, device=field.device)
+    st = native.msz_directions(field.contiguous().data_ptr(), tuple(field.shape), field.dtype,
+                               out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    native.check(st, "msz_directions")
+    return out

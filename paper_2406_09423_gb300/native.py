@@ -1,0 +1,192 @@
+"""Thin ctypes binding of libmsz.so (include/msz.h). Argument marshalling only:
+every step of the correction loop runs in the CUDA library.
+
+The library is loaded from the package's ``_build`` directory; it must have
+been built (``python -c "import __graft_entry__ as g; g.build()"``). There is
+no CPU fallback: importing a function of this module on a machine without
+the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmsz.so")
+
+MSZ_F32, MSZ_F64 = 0, 1
+MSZ_OPT_NO_TMA = 1
+MSZ_OPT_TIME_KERNELS = 2
+KERNEL_KINDS = ("csweep", "labels", "rcheck", "mark_apply")
+STATUS = {
+    0: "MSZ_OK", -1: "MSZ_ERR_ARG", -2: "MSZ_ERR_DTYPE", -3: "MSZ_ERR_NONFINITE",
+    -4: "MSZ_ERR_BOUND", -5: "MSZ_ERR_OOM", -6: "MSZ_ERR_NOCONVERGE", -7: "MSZ_ERR_TIMEOUT",
+    -8: "MSZ_ERR_CUDA", -9: "MSZ_ERR_BUSY",
+}
+
+COUNT_FIELDS = (
+    "sweeps",
+    "c_rounds_fpmax", "c_rounds_fpmin", "c_rounds_fnmax", "c_rounds_fnmin",
+    "c_cases_fpmax", "c_cases_fpmin", "c_cases_fnmax", "c_cases_fnmin",
+    "c_passes", "r_rounds", "r_cases_asc", "r_cases_desc", "label_evals",
+    "mismatch_max", "mismatch_min", "dec_edits", "freezes", "edits",
+)
+
+
+class MszCounts(ctypes.Structure):
+    _fields_ = [
+        ("sweeps", ctypes.c_uint64),
+        ("c_rounds", ctypes.c_uint64 * 4),
+        ("c_cases", ctypes.c_uint64 * 4),
+        ("c_passes", ctypes.c_uint64),
+        ("r_rounds", ctypes.c_uint64),
+        ("r_cases", ctypes.c_uint64 * 2),
+        ("label_evals", ctypes.c_uint64),
+        ("mismatch", ctypes.c_uint64 * 2),
+        ("dec_edits", ctypes.c_uint64),
+        ("freezes", ctypes.c_uint64),
+        ("edits", ctypes.c_uint64),
+    ]
+
+    def as_dict(self) -> dict:
+        flat = [self.sweeps, *self.c_rounds, *self.c_cases, self.c_passes, self.r_rounds,
+                *self.r_cases, self.label_evals, *self.mismatch, self.dec_edits, self.freezes,
+                self.edits]
+        return {k: int(v) for k, v in zip(COUNT_FIELDS, flat)}
+
+
+class MszOptions(ctypes.Structure):
+    _fields_ = [("max_rounds", ctypes.c_uint64), ("label_tile", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class MszResult(ctypes.Structure):
+    _fields_ = [
+        ("edit_idx", ctypes.c_void_p),
+        ("edit_val", ctypes.c_void_p),
+        ("n_edits", ctypes.c_uint64),
+        ("label_max", ctypes.c_void_p),
+        ("label_min", ctypes.c_void_p),
+        ("counts", MszCounts),
+        ("status", ctypes.c_int32),
+        ("device_ms", ctypes.c_float),
+        ("launches", ctypes.c_uint64),
+        ("kernel_ms", ctypes.c_float * 4),
+    ]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libmsz.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, I64, U64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        L.msz_plan_create.argtypes = [ctypes.POINTER(P), I, P, I, P]
+        L.msz_plan_create.restype = I
+        L.msz_plan_bytes.argtypes = [I, P, I]
+        L.msz_plan_bytes.restype = I64
+        L.msz_plan_destroy.argtypes = [P]
+        L.msz_plan_destroy.restype = I
+        L.msz_fix.argtypes = [P, P, P, D, P, ctypes.POINTER(MszResult)]
+        L.msz_fix.restype = I
+        L.msz_fix_host.argtypes = [P, P, P, D, P, P, P, P, P, ctypes.POINTER(MszResult)]
+        L.msz_fix_host.restype = I
+        L.msz_apply.argtypes = [P, I, P, I, P, P, U64, P]
+        L.msz_apply.restype = I
+        L.msz_directions.argtypes = [P, I, P, I, P, P]
+        L.msz_directions.restype = I
+        L.msz_strerror.argtypes = [I]
+        L.msz_strerror.restype = ctypes.c_char_p
+        L.msz_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def dims_of(shape):
+    """numpy/torch shape (ny, nx) or (nz, ny, nx) -> (ndim, int64[3] dims, x fastest)."""
+    ndim = len(shape)
+    if ndim not in (2, 3):
+        raise ValueError("fields are 2D or 3D")
+    d = [1, 1, 1]
+    d[:ndim] = list(shape)[::-1]
+    return ndim, (ctypes.c_int64 * 3)(*d)
+
+
+def dtype_code(dtype) -> int:
+    s = str(dtype)
+    if s.endswith("float32"):
+        return MSZ_F32
+    if s.endswith("float64"):
+        return MSZ_F64
+    raise TypeError("float32 or float64 fields only")
+
+
+def check(status: int, what: str = "msz"):
+    if status != 0:
+        raise RuntimeError(f"{what}: {STATUS.get(status, status)} ({lib().msz_strerror(status).decode()})")
+
+
+# Same names as the C ABI ---------------------------------------------------
+
+def msz_plan_create(shape, dtype, max_rounds: int = 0, flags: int = 0):
+    ndim, d = dims_of(shape)
+    opt = MszOptions()
+    opt.max_rounds = max_rounds
+    opt.flags = flags
+    p = ctypes.c_void_p()
+    st = lib().msz_plan_create(ctypes.byref(p), ndim, d, dtype_code(dtype), ctypes.byref(opt))
+    check(st, "msz_plan_create")
+    return p
+
+
+def msz_plan_bytes(shape, dtype) -> int:
+    ndim, d = dims_of(shape)
+    return int(lib().msz_plan_bytes(ndim, d, dtype_code(dtype)))
+
+
+def msz_plan_destroy(plan):
+    check(lib().msz_plan_destroy(plan), "msz_plan_destroy")
+
+
+def msz_fix(plan, orig_ptr: int, decomp_ptr: int, xi: float, stream: int = 0) -> MszResult:
+    r = MszResult()
+    lib().msz_fix(plan, ctypes.c_void_p(orig_ptr), ctypes.c_void_p(decomp_ptr), float(xi),
+                  ctypes.c_void_p(stream), ctypes.byref(r))
+    return r
+
+
+def msz_fix_host(plan, orig_ptr: int, decomp_ptr: int, xi: float, edit_idx_ptr: int, edit_val_ptr: int,
+                 label_max_ptr: int = 0, label_min_ptr: int = 0, stream: int = 0) -> MszResult:
+    r = MszResult()
+    lib().msz_fix_host(plan, ctypes.c_void_p(orig_ptr), ctypes.c_void_p(decomp_ptr), float(xi),
+                       ctypes.c_void_p(edit_idx_ptr), ctypes.c_void_p(edit_val_ptr),
+                       ctypes.c_void_p(label_max_ptr or None), ctypes.c_void_p(label_min_ptr or None),
+                       ctypes.c_void_p(stream), ctypes.byref(r))
+    return r
+
+
+def msz_apply(decomp_ptr: int, shape, dtype, edit_idx_ptr: int, edit_val_ptr: int, n_edits: int,
+              stream: int = 0) -> int:
+    ndim, d = dims_of(shape)
+    return lib().msz_apply(ctypes.c_void_p(decomp_ptr), ndim, d, dtype_code(dtype),
+                           ctypes.c_void_p(edit_idx_ptr), ctypes.c_void_p(edit_val_ptr),
+                           int(n_edits), ctypes.c_void_p(stream))
+
+
+def msz_directions(field_ptr: int, shape, dtype, dir_ptr: int, stream: int = 0) -> int:
+    ndim, d = dims_of(shape)
+    return lib().msz_directions(ctypes.c_void_p(field_ptr), ndim, d, dtype_code(dtype),
+                                ctypes.c_void_p(dir_ptr), ctypes.c_void_p(stream))
+
+
+def msz_strerror(status: int) -> str:
+    return lib().msz_strerror(status).decode()
+
+
+def msz_version() -> str:
+    return lib().msz_version().decode()

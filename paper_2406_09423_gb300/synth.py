@@ -61,7 +61,7 @@ def lognormal3d(n=256, seed=1, dtype=np.float32, shape=None):
     k = np.sqrt(kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2)
     with np.errstate(divide="ignore"):
         filt = np.where(k > 0, k ** -1.5, 0.0)
-    g = np.fft.irfftn(F * filt, s=shape)
+    g = np.fft.irfftn(F * filt, s=shape, axes=(0, 1, 2))
     g = (g - g.mean()) / g.std()
     return np.exp(g).astype(dtype)
 

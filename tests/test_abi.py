@@ -1,0 +1,57 @@
+"""The C-ABI library loads and exports every function include/msz.h declares
+(no GPU needed: nothing is called)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(msz_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("msz_plan_create", "msz_plan_destroy", "msz_fix", "msz_apply", "msz_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2406_09423_gb300 import build
+
+    lib_path = build.build()
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_without_gpu():
+    from paper_2406_09423_gb300 import native
+
+    assert native.msz_strerror(-4) == "decompressed value outside the error bound"
+    assert native.msz_version().startswith("msz-gb300")
+
+
+def test_plan_bytes_and_argument_checks_without_gpu():
+    from paper_2406_09423_gb300 import native
+
+    assert native.msz_plan_bytes((512, 512, 512), "float32") > 512 ** 3 * 20
+    L = native.lib()
+    d = (ctypes.c_int64 * 3)(0, 4, 4)
+    assert L.msz_plan_bytes(3, d, 0) == -1
+    d = (ctypes.c_int64 * 3)(4, 4, 4)
+    assert L.msz_plan_bytes(3, d, 7) == -2
+    assert L.msz_plan_bytes(4, d, 0) == -1
+    d = (ctypes.c_int64 * 3)(1 << 16, 1 << 16, 1)
+    assert L.msz_plan_bytes(2, d, 0) == -1  # 2^32 vertices: too many
