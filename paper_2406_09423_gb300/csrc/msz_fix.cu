@@ -231,11 +231,38 @@ __device__ void ctrl_after_sweep(DevState* st) {
 // planes stream through a ring of TMA stages, otherwise through one stage
 // filled by plain loads.
 // ---------------------------------------------------------------------------
+// Cursor over the (tile, plane) sequence of one block: tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...; planes 0 .. chunk+1 of each. Divisions only
+// happen when a new tile starts.
+struct PlaneCursor {
+  int tile, p, x0, y0, c0;
+  __device__ __forceinline__ void origin(const SweepTiling& TL, int tx_, int ty_) {
+    const int bx = tile % TL.tiles_x;
+    const int r = tile / TL.tiles_x;
+    x0 = bx * tx_;
+    y0 = (r % TL.tiles_y) * ty_;
+    c0 = (r / TL.tiles_y) * TL.chunk;
+  }
+  __device__ __forceinline__ void start(const SweepTiling& TL, int tx_, int ty_) {
+    tile = (int)blockIdx.x;
+    p = 0;
+    origin(TL, tx_, ty_);
+  }
+  __device__ __forceinline__ void next(const SweepTiling& TL, int tx_, int ty_) {
+    if (++p == TL.chunk + 2) {
+      p = 0;
+      tile += (int)gridDim.x;
+      origin(TL, tx_, ty_);
+    }
+  }
+};
+
 template <class T, int ND, bool kTMA>
 __global__ void __launch_bounds__(SweepGeom<T, ND>::NT)
     k_csweep(Field<T> F, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap dmap,
              SweepTiling TL) {
   using SG = SweepGeom<T, ND>;
+  static_assert((SG::STAGES & (SG::STAGES - 1)) == 0, "power-of-two stages");
   DevState* st = F.st;
   if (st->phase != PH_C) return;
   __shared__ alignas(128) unsigned char smem[(kTMA ? SG::STAGES : 1) * SG::STAGE_BYTES];
@@ -248,32 +275,22 @@ __global__ void __launch_bounds__(SweepGeom<T, ND>::NT)
       (blockIdx.x < (unsigned)TL.ntiles) ? (TL.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int total = my_tiles * ppt;
   const Geom G = F.G;
+  constexpr int SM1 = SG::STAGES - 1;
 
-  auto tile_origin = [&](int q, int& x0, int& y0, int& c0) {
-    const int tile = (int)blockIdx.x + (q / ppt) * (int)gridDim.x;
-    const int bx = tile % TL.tiles_x;
-    const int r = tile / TL.tiles_x;
-    const int by = r % TL.tiles_y;
-    const int bc = r / TL.tiles_y;
-    x0 = bx * SG::TX;
-    y0 = by * SG::TY;
-    c0 = bc * TL.chunk;
-  };
-  auto stage_ptr = [&](int q) -> unsigned char* { return smem + (kTMA ? (q % SG::STAGES) : 0) * SG::STAGE_BYTES; };
+  PlaneCursor pc_issue{};  // producer cursor (thread 0 only)
   auto issue = [&](int q) {
-    int x0, y0, c0;
-    tile_origin(q, x0, y0, c0);
-    const int pc = c0 - 1 + q % ppt;
-    uint64_t* bar = &bars[q % SG::STAGES];
-    unsigned char* sp = stage_ptr(q);
+    const int pc = pc_issue.c0 - 1 + pc_issue.p;
+    uint64_t* bar = &bars[q & SM1];
+    unsigned char* sp = smem + (q & SM1) * SG::STAGE_BYTES;
     mbar_expect_tx(bar, (uint32_t)(SG::STAGE_ELEMS * sizeof(T) + SG::NT));
     if (ND == 3) {
-      tma_load_3d(sp, &tmap, bar, x0 - SG::PADX, y0 - 1, pc);
-      tma_load_3d(sp + SG::G_BYTES, &dmap, bar, x0, y0, pc);
+      tma_load_3d(sp, &tmap, bar, pc_issue.x0 - SG::PADX, pc_issue.y0 - 1, pc);
+      tma_load_3d(sp + SG::G_BYTES, &dmap, bar, pc_issue.x0, pc_issue.y0, pc);
     } else {
-      tma_load_2d(sp, &tmap, bar, x0 - SG::PADX, pc);
-      tma_load_2d(sp + SG::G_BYTES, &dmap, bar, x0, pc);
+      tma_load_2d(sp, &tmap, bar, pc_issue.x0 - SG::PADX, pc);
+      tma_load_2d(sp + SG::G_BYTES, &dmap, bar, pc_issue.x0, pc);
     }
+    pc_issue.next(TL, SG::TX, SG::TY);
   };
 
   if (kTMA) {
@@ -282,8 +299,10 @@ __global__ void __launch_bounds__(SweepGeom<T, ND>::NT)
       mbar_fence_init();
     }
     __syncthreads();
-    if (tid == 0)
+    if (tid == 0) {
+      pc_issue.start(TL, SG::TX, SG::TY);
       for (int q = 0; q < SG::STAGES && q < total; ++q) issue(q);
+    }
   }
 
   uint32_t cnt[4] = {0, 0, 0, 0};
@@ -291,15 +310,15 @@ __global__ void __launch_bounds__(SweepGeom<T, ND>::NT)
   int waited = 0;  // TMA stages consumed
   PlaneVals<T> C{}, A{}, B{};
   uint8_t fdA = 0, fdB = 0;  // f's direction byte of this thread's vertex in planes A, B
-  for (int q = 0; q < total && ok; ++q) {
-    int x0, y0, c0;
-    tile_origin(q, x0, y0, c0);
-    const int p = q % ppt;
-    const int pc = c0 - 1 + p;  // plane coordinate (z in 3D, y in 2D)
-    unsigned char* sp = stage_ptr(q);
+  PlaneCursor cur;
+  cur.start(TL, SG::TX, SG::TY);
+  for (int q = 0; q < total; ++q, cur.next(TL, SG::TX, SG::TY)) {
+    const int p = cur.p;
+    const int pcoord = cur.c0 - 1 + p;  // plane coordinate (z in 3D, y in 2D)
+    unsigned char* sp = smem + (kTMA ? (q & SM1) * SG::STAGE_BYTES : 0);
     const T* stage = reinterpret_cast<const T*>(sp);
     if (kTMA) {
-      const bool got = mbar_wait(&bars[q % SG::STAGES], (uint32_t)((q / SG::STAGES) & 1));
+      const bool got = mbar_wait(&bars[q & SM1], (uint32_t)((q / SG::STAGES) & 1));
       waited = q + 1;
       B = plane_vals<T, ND>(stage, tx, ty);
       fdB = sp[SG::G_BYTES + tid];
@@ -311,44 +330,42 @@ __global__ void __launch_bounds__(SweepGeom<T, ND>::NT)
       T* wst = reinterpret_cast<T*>(sp);
       for (int i = tid; i < SG::STAGE_ELEMS; i += SG::NT) {
         const int col = i % SG::BX, row = i / SG::BX;
-        const int gx = x0 - SG::PADX + col;
-        const int gy = (ND == 3) ? y0 - 1 + row : pc;
-        const int gz = (ND == 3) ? pc : 0;
+        const int gx = cur.x0 - SG::PADX + col;
+        const int gy = (ND == 3) ? cur.y0 - 1 + row : pcoord;
+        const int gz = (ND == 3) ? pcoord : 0;
         const bool in = gx >= 0 && gx < G.nx && gy >= 0 && gy < G.ny && gz >= 0 && gz < G.nz;
         wst[i] = in ? F.g[gx + G.nx * (gy + G.ny * gz)] : qnan<T>();
       }
       __syncthreads();
       B = plane_vals<T, ND>(stage, tx, ty);
-      const int vx = x0 + tx, vy = (ND == 3) ? y0 + ty : pc, vz = (ND == 3) ? pc : 0;
+      const int vx = cur.x0 + tx, vy = (ND == 3) ? cur.y0 + ty : pcoord, vz = (ND == 3) ? pcoord : 0;
       fdB = (vx < G.nx && vy >= 0 && vy < G.ny && vz >= 0 && vz < G.nz) ? F.fdir[vx + G.nx * (vy + G.ny * vz)]
                                                                         : (uint8_t)0;
     }
     if (p >= 2) {
-      const int x = x0 + tx;
-      const int y = (ND == 3) ? y0 + ty : c0 + p - 2;
-      const int z = (ND == 3) ? c0 + p - 2 : 0;
+      const int x = cur.x0 + tx;
+      const int y = (ND == 3) ? cur.y0 + ty : pcoord - 1;
+      const int z = (ND == 3) ? pcoord - 1 : 0;
       const bool valid = x < G.nx && y < G.ny && z < G.nz && (p - 2) < TL.chunk;
       unsigned bits = 0;
-      int v = 0;
       if (valid) {
-        v = x + G.nx * (y + G.ny * z);
         const unsigned e = extremum_bits<T, ND>(C, A, B);
         const unsigned fmx = (fdA & 15) == kSelf, fmn = (fdA >> 4) == kSelf;
         const unsigned gmx = e & 1u, gmn = (e >> 1) & 1u;
         bits = (gmx & ~fmx) | ((gmn & ~fmn) << 1) | ((fmx & ~gmx) << 2) | ((fmn & ~gmn) << 3);
       }
+      if (__any_sync(kFull, bits != 0)) {
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const uint32_t b = __ballot_sync(kFull, (bits >> t) & 1u);
-        if (lane == 0) cnt[t] += __popc(b);
-      }
-      const uint32_t mask = __ballot_sync(kFull, bits != 0);
-      if (mask) {
+        for (int t = 0; t < 4; ++t) {
+          const uint32_t b = __ballot_sync(kFull, (bits >> t) & 1u);
+          if (lane == 0) cnt[t] += __popc(b);
+        }
+        const uint32_t mask = __ballot_sync(kFull, bits != 0);
         const int leader = __ffs(mask) - 1;
         uint32_t b0 = 0;
         if (lane == leader) b0 = atomicAdd(&st->ncase, (uint32_t)__popc(mask));
         b0 = __shfl_sync(kFull, b0, leader);
-        if (bits) F.cases[b0 + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)v;
+        if (bits) F.cases[b0 + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)(x + G.nx * (y + G.ny * z));
       }
     }
     C = A;
@@ -360,7 +377,7 @@ __global__ void __launch_bounds__(SweepGeom<T, ND>::NT)
     if (tid == 0) {
       atomicOr(&st->err_bits, E_TIMEOUT);
       const int issued = (total < waited + SG::STAGES) ? total : waited + SG::STAGES;
-      for (int q = waited; q < issued; ++q) mbar_wait(&bars[q % SG::STAGES], (uint32_t)((q / SG::STAGES) & 1));
+      for (int q = waited; q < issued; ++q) mbar_wait(&bars[q & SM1], (uint32_t)((q / SG::STAGES) & 1));
     }
     __syncthreads();
   }
@@ -409,10 +426,10 @@ struct LabelGeom {
   static constexpr int TZ = (ND == 3) ? 8 : 1;
   static constexpr int TV = TX * TY * TZ;  // 2048 vertices
   static constexpr int SX = TX + 2, SY = TY + 2, SZ = (ND == 3) ? TZ + 2 : 1;
-  static constexpr int HALO = SX * SY * SZ;
+  static constexpr int HALO = SX * SY * SZ;  // < 65536: pointers fit in 16 bits
   static constexpr int PER_THREAD = TV / kThreads;
+  static constexpr int ROWS = SY * SZ;
 };
-constexpr uint32_t kTerm = 0x80000000u;  // pointer word: terminal (global index in low 31 bits)
 
 template <class T, int ND>
 __global__ void __launch_bounds__(kThreads) k_label_tile(Field<T> F) {
@@ -421,8 +438,10 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(Field<T> F) {
   if (st->action != ACT_LABELS || st->lstate != L_INIT) return;
   extern __shared__ __align__(16) unsigned char lsm[];
   T* val = reinterpret_cast<T*>(lsm);
-  uint32_t* Pu = reinterpret_cast<uint32_t*>(lsm + ((LG::HALO * sizeof(T) + 15) / 16) * 16);
-  uint32_t* Pd = Pu + LG::TV;
+  // Pointers live in halo coordinates: a halo cell or an extremum points to
+  // itself (terminal); an interior cell points to its steepest neighbour.
+  uint16_t* Pu = reinterpret_cast<uint16_t*>(lsm + ((LG::HALO * sizeof(T) + 15) / 16) * 16);
+  uint16_t* Pd = Pu + ((LG::HALO + 7) / 8) * 8;
   const bool job = st->ljob != 0;
   const T* src = job ? F.g : F.f;
   uint8_t* dir = job ? F.gdir : F.fdir;
@@ -433,18 +452,28 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(Field<T> F) {
   const int tiles_y = (G.ny + LG::TY - 1) / LG::TY;
   const int tiles_z = (G.nz + LG::TZ - 1) / LG::TZ;
   const int ntiles = tiles_x * tiles_y * tiles_z;
-  // candidate order: ascending linear index = ascending (dz, dy, dx)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // halo-space offset of every stencil slot (slots 0..13, 15 = self)
+  constexpr int HS = LG::SX, HSS = LG::SX * LG::SY;
   constexpr int NC = (ND == 3) ? 15 : 7;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int x0 = (tile % tiles_x) * LG::TX;
     const int y0 = ((tile / tiles_x) % tiles_y) * LG::TY;
     const int z0 = (tile / (tiles_x * tiles_y)) * LG::TZ;
     __syncthreads();
-    for (int i = threadIdx.x; i < LG::HALO; i += kThreads) {
-      const int hx = i % LG::SX, hy = (i / LG::SX) % LG::SY, hz = i / (LG::SX * LG::SY);
-      const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = (ND == 3) ? z0 - 1 + hz : 0;
-      const bool in = gx >= 0 && gx < G.nx && gy >= 0 && gy < G.ny && gz >= 0 && gz < G.nz;
-      val[i] = in ? src[gx + G.nx * (gy + G.ny * gz)] : qnan<T>();
+    // halo load, one row (fixed hy, hz) per warp iteration; NaN outside the grid
+    for (int row = warp; row < LG::ROWS; row += kThreads / 32) {
+      const int hy = row % LG::SY, hz = row / LG::SY;
+      const int gy = y0 - 1 + hy, gz = (ND == 3) ? z0 - 1 + hz : 0;
+      const bool rin = gy >= 0 && gy < G.ny && gz >= 0 && gz < G.nz;
+      const T* srow = src + (size_t)G.nx * ((size_t)gy + (size_t)G.ny * gz);
+      for (int hx = lane; hx < LG::SX; hx += 32) {
+        const int gx = x0 - 1 + hx;
+        const int h = hx + HS * row;
+        val[h] = (rin && gx >= 0 && gx < G.nx) ? srow[gx] : qnan<T>();
+        Pu[h] = (uint16_t)h;
+        Pd[h] = (uint16_t)h;
+      }
     }
     __syncthreads();
     uint8_t dbyte[LG::PER_THREAD];
@@ -452,60 +481,49 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(Field<T> F) {
     for (int k = 0; k < LG::PER_THREAD; ++k) {
       const int i = threadIdx.x + k * kThreads;
       const int lx = i % LG::TX, ly = (i / LG::TX) % LG::TY, lz = i / (LG::TX * LG::TY);
-      const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-      const int c = (lx + 1) + LG::SX * ((ly + 1) + LG::SY * ((ND == 3) ? lz + 1 : 0));
+      const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
+      // candidates in ascending linear index = ascending (dz, dy, dx); ties go
+      // to the larger index for the maximum and to the smaller for the minimum
       T hv = -INFINITY, lv = INFINITY;
-      int hs = kSelf, ls = kSelf;
+      int hs = kSelf, ls = kSelf, ho = 0, lo = 0;
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
-        // j-th candidate: (dz, dy, dx) in lexicographic order over {-1,0,1}^d
-        // restricted to the Freudenthal ring (e or -e with e in {0,1}^d).
-        int dx, dy, dz, slot;
+        int o, slot;
         if (ND == 3) {
-          constexpr int tab[15][4] = {{-1, -1, -1, 13}, {0, -1, -1, 12}, {-1, 0, -1, 11}, {0, 0, -1, 9},
-                                      {-1, -1, 0, 10},  {0, -1, 0, 8},   {-1, 0, 0, 7},   {0, 0, 0, kSelf},
-                                      {1, 0, 0, 0},     {0, 1, 0, 1},    {1, 1, 0, 3},    {0, 0, 1, 2},
-                                      {1, 0, 1, 4},     {0, 1, 1, 5},    {1, 1, 1, 6}};
-          dx = tab[j][0]; dy = tab[j][1]; dz = tab[j][2]; slot = tab[j][3];
+          constexpr int tab[15][2] = {{-1 - HS - HSS, 13}, {-HS - HSS, 12}, {-1 - HSS, 11}, {-HSS, 9},
+                                      {-1 - HS, 10},       {-HS, 8},        {-1, 7},        {0, kSelf},
+                                      {1, 0},              {HS, 1},         {1 + HS, 3},    {HSS, 2},
+                                      {1 + HSS, 4},        {HS + HSS, 5},   {1 + HS + HSS, 6}};
+          o = tab[j][0]; slot = tab[j][1];
         } else {
-          constexpr int tab[7][3] = {{-1, -1, 5}, {0, -1, 4}, {-1, 0, 3}, {0, 0, kSelf},
-                                     {1, 0, 0},   {0, 1, 1},  {1, 1, 2}};
-          dx = tab[j][0]; dy = tab[j][1]; dz = 0; slot = tab[j][2];
+          constexpr int tab[7][2] = {{-1 - HS, 5}, {-HS, 4}, {-1, 3}, {0, kSelf}, {1, 0}, {HS, 1}, {1 + HS, 2}};
+          o = tab[j][0]; slot = tab[j][1];
         }
-        const T u = val[c + dx + LG::SX * (dy + LG::SY * dz)];
-        if (u >= hv) { hv = u; hs = slot; }
-        if (u < lv) { lv = u; ls = slot; }
+        const T u = val[c + o];
+        if (u >= hv) { hv = u; hs = slot; ho = o; }
+        if (u < lv) { lv = u; ls = slot; lo = o; }
       }
-      const bool valid = x < G.nx && y < G.ny && z < G.nz;
       dbyte[k] = (uint8_t)(hs | (ls << 4));
-      // pointer words: local index inside the tile, else terminal global index
-      auto word = [&](int s) -> uint32_t {
-        if (s == kSelf) return kTerm | (uint32_t)(x + G.nx * (y + G.ny * z));
-        const int npos = (ND == 3) ? 7 : 3;
-        const bool neg = s >= npos;
-        const int m = slot_mask(ND, neg ? s - npos : s);
-        const int sg = neg ? -1 : 1;
-        const int ex = sg * (m & 1), ey = sg * ((m >> 1) & 1), ez = sg * ((m >> 2) & 1);
-        const int tx_ = lx + ex, ty_ = ly + ey, tz_ = lz + ez;
-        if (tx_ >= 0 && tx_ < LG::TX && ty_ >= 0 && ty_ < LG::TY && tz_ >= 0 && tz_ < LG::TZ)
-          return (uint32_t)(tx_ + LG::TX * (ty_ + LG::TY * tz_));
-        return kTerm | (uint32_t)((x + ex) + G.nx * ((y + ey) + G.ny * (z + ez)));
-      };
-      // out-of-grid tile cells are terminal and never referenced by valid ones
-      Pu[i] = valid ? word(hs) : kTerm;
-      Pd[i] = valid ? word(ls) : kTerm;
+      // cells outside the grid are NaN: they keep self pointers and are never
+      // chosen by a valid cell
+      if (val[c] == val[c]) {
+        Pu[c] = (uint16_t)(c + ho);
+        Pd[c] = (uint16_t)(c + lo);
+      }
     }
     __syncthreads();
-    // in-tile pointer doubling: P[i] <- P[P[i]] until every pointer is terminal
+    // pointer doubling inside the tile: P[c] <- P[P[c]] until all are terminal
     for (int round = 0; round < 2 * LG::TV; ++round) {
       int changed = 0;
 #pragma unroll
       for (int k = 0; k < LG::PER_THREAD; ++k) {
         const int i = threadIdx.x + k * kThreads;
-        const uint32_t a = Pu[i];
-        if (!(a & kTerm)) { Pu[i] = Pu[a]; changed = 1; }
-        const uint32_t b = Pd[i];
-        if (!(b & kTerm)) { Pd[i] = Pd[b]; changed = 1; }
+        const int lx = i % LG::TX, ly = (i / LG::TX) % LG::TY, lz = i / (LG::TX * LG::TY);
+        const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
+        const int a = Pu[c], a2 = Pu[a];
+        if (a2 != a) { Pu[c] = (uint16_t)a2; changed = 1; }
+        const int b = Pd[c], b2 = Pd[b];
+        if (b2 != b) { Pd[c] = (uint16_t)b2; changed = 1; }
       }
       if (!__syncthreads_or(changed)) break;
     }
@@ -516,9 +534,15 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(Field<T> F) {
       const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
       if (x < G.nx && y < G.ny && z < G.nz) {
         const int v = x + G.nx * (y + G.ny * z);
+        const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
+        // terminal halo cell -> global index (same offset from v as from c)
+        auto global_of = [&](int h) -> int {
+          const int hx = h % LG::SX, hy = (h / LG::SX) % LG::SY, hz = h / HSS;
+          return (x0 - 1 + hx) + G.nx * ((y0 - 1 + hy) + G.ny * ((ND == 3) ? (z0 - 1 + hz) : 0));
+        };
         dir[v] = dbyte[k];
-        A[v] = (int32_t)(Pu[i] & ~kTerm);
-        B[v] = (int32_t)(Pd[i] & ~kTerm);
+        A[v] = global_of(Pu[c]);
+        B[v] = global_of(Pd[c]);
       }
     }
   }
@@ -1046,7 +1070,7 @@ template <class T, int ND>
 int setup_labels_t(msz_plan_s* p) {
   using LG = LabelGeom<ND>;
   const Geom& G = p->G;
-  p->label_smem = (int)(((LG::HALO * sizeof(T) + 15) / 16) * 16 + 2 * LG::TV * sizeof(uint32_t));
+  p->label_smem = (int)(((LG::HALO * sizeof(T) + 15) / 16) * 16 + 2 * ((LG::HALO + 7) / 8) * 8 * sizeof(uint16_t));
   if (cudaFuncSetAttribute(k_label_tile<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, p->label_smem) !=
       cudaSuccess)
     return MSZ_ERR_CUDA;
