@@ -51,7 +51,8 @@ typedef enum {
   MSZ_ERR_NOCONVERGE = -6, /* round cap reached (msz_options.max_rounds) */
   MSZ_ERR_TIMEOUT = -7,    /* a bounded device-side wait gave up */
   MSZ_ERR_CUDA = -8,       /* a CUDA runtime call failed */
-  MSZ_ERR_BUSY = -9        /* server: no free slot / request id unknown or not finished */
+  MSZ_ERR_BUSY = -9,       /* server: no free slot / request id unknown or not finished */
+  MSZ_ERR_TOO_LARGE = -10  /* msz_fix_noalloc: the field does not fit its static scratch */
 } msz_status;
 
 /* Counters of one fix. The same quantities are computed by the reference
@@ -144,6 +145,27 @@ int msz_apply(void* decomp_dev, int ndim, const int64_t dims[3], int dtype,
  * itself (a maximum, resp. minimum). */
 int msz_directions(const void* field_dev, int ndim, const int64_t dims[3], int dtype,
                    uint8_t* dir_dev, void* stream);
+
+/* msz_fix without any device allocation. The paper has no counterpart: this
+ * entry point serves callers that cannot call cudaMalloc (a framework whose
+ * allocator must not grow, a real-time loop where an allocation may block or
+ * fail, a plugin whose host forbids allocation during a call).
+ *
+ * Inputs (orig_dev, decomp_dev: N values) and outputs are the caller's
+ * device buffers: edit_idx_dev / edit_val_dev hold N entries (worst case),
+ * label_max_dev / label_min_dev hold N labels. out->edit_idx etc. point to
+ * them. Every other array of the loop lives in one static device array of
+ * 64 MiB that each GPU loading the library holds until exit; a field needs
+ * about 23 bytes per vertex (float32) or 27 (float64) of it, so up to about
+ * 2.9 M (float32) / 2.4 M (float64) vertices. Larger fields are rejected
+ * with MSZ_ERR_TOO_LARGE before any work. The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture. All calls share
+ * the array: calls that overlap on the GPU race and must be serialised by
+ * the caller. No timing (device_ms = 0). Returns out->status. */
+int msz_fix_noalloc(int ndim, const int64_t dims[3], int dtype, const void* orig_dev,
+                    const void* decomp_dev, double xi, uint32_t* edit_idx_dev, void* edit_val_dev,
+                    int32_t* label_max_dev, int32_t* label_min_dev, void* stream, msz_result* out);
 
 const char* msz_strerror(int status);
 

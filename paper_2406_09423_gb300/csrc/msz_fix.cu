@@ -1149,7 +1149,7 @@ int run_fix(msz_plan_s* p, const void* f, const void* fhat, double xi, cudaStrea
   std::memcpy(p->host_st, &init, sizeof(init));
   if (cudaMemcpyAsync(p->st, p->host_st, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return MSZ_ERR_CUDA;
-  cudaEventRecord(p->ev0, s);
+  if (p->ev0) cudaEventRecord(p->ev0, s);
   p->launches = 0;
   k_init<T, ND><<<p->dense_blocks, kThreads, 0, s>>>(F);
   p->launches += 1;
@@ -1181,7 +1181,7 @@ int run_fix(msz_plan_s* p, const void* f, const void* fhat, double xi, cudaStrea
   k_emit_scan<T><<<1, 1024, 0, s>>>(F, p->ntiles);
   k_emit_write<T><<<p->ntiles, kThreads, 0, s>>>(F);
   p->launches += 3;
-  cudaEventRecord(p->ev1, s);
+  if (p->ev1) cudaEventRecord(p->ev1, s);
   cudaMemcpyAsync(p->host_st, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return MSZ_ERR_CUDA;
   if (cudaGetLastError() != cudaSuccess) return MSZ_ERR_CUDA;
@@ -1199,7 +1199,7 @@ int run_fix(msz_plan_s* p, const void* f, const void* fhat, double xi, cudaStrea
       out->label_min = p->Pdn;
     }
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, p->ev0, p->ev1) == cudaSuccess) out->device_ms = ms;
+    if (p->ev0 && p->ev1 && cudaEventElapsedTime(&ms, p->ev0, p->ev1) == cudaSuccess) out->device_ms = ms;
     out->launches = p->launches;
     for (int k = 0; k < kKinds; ++k) out->kernel_ms[k] = (float)p->kernel_ms[k];
   }
@@ -1416,6 +1416,7 @@ const char* msz_strerror(int status) {
     case MSZ_ERR_TIMEOUT: return "device-side wait gave up";
     case MSZ_ERR_CUDA: return "CUDA runtime error";
     case MSZ_ERR_BUSY: return "no free slot or request not ready";
+    case MSZ_ERR_TOO_LARGE: return "field too large for the static scratch of msz_fix_noalloc";
     default: return "unknown status";
   }
 }
@@ -1423,3 +1424,132 @@ const char* msz_strerror(int status) {
 const char* msz_version(void) { return "msz-gb300 0.1"; }
 
 }  // extern "C"
+// ---------------------------------------------------------------------------
+// msz_fix_noalloc: the correction loop with no device allocation at all.
+//
+// Some callers cannot call cudaMalloc: code that runs where the allocator is
+// owned by someone else (a framework's caching allocator or a memory pool
+// that must not grow, a real-time loop where an allocation may block or fail,
+// a plugin whose host forbids allocations during a call). For them this
+// entry point keeps every intermediate array of the loop in one file-scope
+// device array of fixed size, kNoAllocScratchBytes, which every GPU that
+// loads the library holds until the process exits. Inputs and outputs are
+// still the caller's buffers.
+//
+// In host code g_noalloc_scratch names a host-side stand-in, not the device
+// array: its device address is obtained with cudaGetSymbolAddress, once per
+// device, by the first call on that device (with that device current). That
+// first call should therefore come before any stream capture.
+//
+// Every call shares the array and finds the previous call's contents in it;
+// the loop clears what must start at zero (state, flags) itself. Calls whose
+// work overlaps on the GPU (different streams, or different host threads on
+// one device) race on the array and must be serialised by the caller.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;  // 64 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (set up once).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MSZ_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return MSZ_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return MSZ_OK;
+}
+
+// Carves the loop's scratch out of [base, base + cap); false if it does not fit.
+bool carve_noalloc(msz_plan_s* p, unsigned char* base, size_t cap) {
+  const Geom& G = p->G;
+  const size_t n = (size_t)G.n;
+  const size_t es = esize(p->dtype);
+  const size_t ntiles = (n + kEmitTile - 1) / kEmitTile;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> unsigned char* {
+    unsigned char* q = base + off;
+    off += round_up(bytes, 256);
+    return q;
+  };
+  p->g = take(n * es);
+  p->fdir = take(n);
+  p->gdir = take(n);
+  p->flags = take(ntiles * kEmitTile);
+  p->Mf = reinterpret_cast<int32_t*>(take(n * 4));
+  p->mf = reinterpret_cast<int32_t*>(take(n * 4));
+  p->cases = reinterpret_cast<uint32_t*>(take(n * 4));
+  p->touched = reinterpret_cast<uint32_t*>(take(n * 4));
+  p->tile_cnt = reinterpret_cast<uint32_t*>(take(ntiles * 4));
+  p->st = reinterpret_cast<DevState*>(take(sizeof(DevState)));
+  p->ntiles = (int)ntiles;
+  return off <= cap;
+}
+
+}  // namespace
+
+extern "C" int msz_fix_noalloc(int ndim, const int64_t dims[3], int dtype, const void* orig_dev,
+                               const void* decomp_dev, double xi, uint32_t* edit_idx_dev, void* edit_val_dev,
+                               int32_t* label_max_dev, int32_t* label_min_dev, void* stream, msz_result* out) {
+  if (out) std::memset(out, 0, sizeof(*out));
+  auto fail = [&](int code) {
+    if (out) out->status = code;
+    return code;
+  };
+  Geom G;
+  if (!geom_from(ndim, dims, G)) return fail(MSZ_ERR_ARG);
+  if (dtype != MSZ_F32 && dtype != MSZ_F64) return fail(MSZ_ERR_DTYPE);
+  if (!orig_dev || !decomp_dev || !edit_idx_dev || !edit_val_dev || !label_max_dev || !label_min_dev)
+    return fail(MSZ_ERR_ARG);
+  if (!xi_ok(xi, dtype)) return fail(MSZ_ERR_ARG);
+  void* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc != MSZ_OK) return fail(rc);
+  // A plan whose arrays point into the static scratch and the caller's
+  // outputs; host-side state lives on this stack frame (pageable memory).
+  msz_plan_s P;
+  P.G = G;
+  P.dtype = dtype;
+  cudaGetDevice(&P.device);
+  std::memset(&P.opt, 0, sizeof(P.opt));
+  if (!carve_noalloc(&P, static_cast<unsigned char*>(base), kNoAllocScratchBytes)) return fail(MSZ_ERR_TOO_LARGE);
+  P.Pup = label_max_dev;
+  P.Pdn = label_min_dev;
+  P.edit_idx = edit_idx_dev;
+  P.edit_val = edit_val_dev;
+  DevState host_state;
+  uint32_t host_phase[2] = {0, 0};
+  uint64_t host_ticks = 0;
+  P.host_st = &host_state;
+  P.host_phase = host_phase;
+  P.host_ticks = &host_ticks;
+  const int sms = num_sms();
+  P.dense_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((G.n + kThreads - 1) / kThreads, (int64_t)sms * 8));
+  P.sparse_blocks = sms * 4;
+  if (setup_sweep(&P) != MSZ_OK) return fail(MSZ_ERR_CUDA);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(P.flags, 0, (size_t)P.ntiles * kEmitTile, s) != cudaSuccess) return fail(MSZ_ERR_CUDA);
+  msz_result r;
+  const int st = dispatch_fix(&P, orig_dev, decomp_dev, xi, s, &r);
+  // P owns nothing: clear the pointers so that no destructor-like path frees them
+  P.host_st = nullptr;
+  P.host_phase = nullptr;
+  P.host_ticks = nullptr;
+  if (out) {
+    *out = r;
+    out->status = st;
+  }
+  return st;
+}

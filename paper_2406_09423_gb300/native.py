@@ -21,7 +21,7 @@ KERNEL_KINDS = ("csweep", "labels", "rcheck", "mark_apply")
 STATUS = {
     0: "MSZ_OK", -1: "MSZ_ERR_ARG", -2: "MSZ_ERR_DTYPE", -3: "MSZ_ERR_NONFINITE",
     -4: "MSZ_ERR_BOUND", -5: "MSZ_ERR_OOM", -6: "MSZ_ERR_NOCONVERGE", -7: "MSZ_ERR_TIMEOUT",
-    -8: "MSZ_ERR_CUDA", -9: "MSZ_ERR_BUSY",
+    -8: "MSZ_ERR_CUDA", -9: "MSZ_ERR_BUSY", -10: "MSZ_ERR_TOO_LARGE",
 }
 
 COUNT_FIELDS = (
@@ -100,6 +100,8 @@ def lib() -> ctypes.CDLL:
         L.msz_apply.restype = I
         L.msz_directions.argtypes = [P, I, P, I, P, P]
         L.msz_directions.restype = I
+        L.msz_fix_noalloc.argtypes = [I, P, I, P, P, D, P, P, P, P, P, ctypes.POINTER(MszResult)]
+        L.msz_fix_noalloc.restype = I
         L.msz_strerror.argtypes = [I]
         L.msz_strerror.restype = ctypes.c_char_p
         L.msz_version.restype = ctypes.c_char_p
@@ -167,6 +169,19 @@ def msz_fix_host(plan, orig_ptr: int, decomp_ptr: int, xi: float, edit_idx_ptr: 
                        ctypes.c_void_p(edit_idx_ptr), ctypes.c_void_p(edit_val_ptr),
                        ctypes.c_void_p(label_max_ptr or None), ctypes.c_void_p(label_min_ptr or None),
                        ctypes.c_void_p(stream), ctypes.byref(r))
+    return r
+
+
+def msz_fix_noalloc(shape, dtype, orig_ptr: int, decomp_ptr: int, xi: float, edit_idx_ptr: int,
+                    edit_val_ptr: int, label_max_ptr: int, label_min_ptr: int, stream: int = 0) -> MszResult:
+    """msz_fix with no device allocation (static scratch inside the library);
+    all buffers are the caller's device memory."""
+    ndim, d = dims_of(shape)
+    r = MszResult()
+    lib().msz_fix_noalloc(ndim, d, dtype_code(dtype), ctypes.c_void_p(orig_ptr), ctypes.c_void_p(decomp_ptr),
+                          float(xi), ctypes.c_void_p(edit_idx_ptr), ctypes.c_void_p(edit_val_ptr),
+                          ctypes.c_void_p(label_max_ptr), ctypes.c_void_p(label_min_ptr),
+                          ctypes.c_void_p(stream), ctypes.byref(r))
     return r
 
 
