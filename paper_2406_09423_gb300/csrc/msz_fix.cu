@@ -262,15 +262,17 @@ __global__ void __launch_bounds__(SweepGeom<T, ND>::NT)
     k_csweep(Field<T> F, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap dmap,
              SweepTiling TL) {
   using SG = SweepGeom<T, ND>;
+  constexpr int RPT = SG::RPT;
+  using PV = PlaneVals<T, RPT>;
   static_assert((SG::STAGES & (SG::STAGES - 1)) == 0, "power-of-two stages");
   DevState* st = F.st;
   if (st->phase != PH_C) return;
   __shared__ alignas(128) unsigned char smem[(kTMA ? SG::STAGES : 1) * SG::STAGE_BYTES];
   __shared__ alignas(8) uint64_t bars[SG::STAGES];
   const int tid = threadIdx.x;
-  const int tx = tid % SG::TX, ty = tid / SG::TX;
+  const int tx = tid % SG::TX, w = tid / SG::TX;  // 3D: warp w owns rows 2w, 2w+1
   const int lane = tid & 31;
-  const int ppt = TL.chunk + 2;
+  const int ppt = TL.chunk + 2;  // planes per tile, a multiple of 3
   const int my_tiles =
       (blockIdx.x < (unsigned)TL.ntiles) ? (TL.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int total = my_tiles * ppt;
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(SweepGeom<T, ND>::NT)
     const int pc = pc_issue.c0 - 1 + pc_issue.p;
     uint64_t* bar = &bars[q & SM1];
     unsigned char* sp = smem + (q & SM1) * SG::STAGE_BYTES;
-    mbar_expect_tx(bar, (uint32_t)(SG::STAGE_ELEMS * sizeof(T) + SG::NT));
+    mbar_expect_tx(bar, (uint32_t)(SG::STAGE_ELEMS * sizeof(T) + SG::TX * SG::TY));
     if (ND == 3) {
       tma_load_3d(sp, &tmap, bar, pc_issue.x0 - SG::PADX, pc_issue.y0 - 1, pc);
       tma_load_3d(sp + SG::G_BYTES, &dmap, bar, pc_issue.x0, pc_issue.y0, pc);
@@ -308,11 +310,12 @@ __global__ void __launch_bounds__(SweepGeom<T, ND>::NT)
   uint32_t cnt[4] = {0, 0, 0, 0};
   bool ok = true;
   int waited = 0;  // TMA stages consumed
-  PlaneVals<T> C{}, A{}, B{};
-  uint8_t fdA = 0, fdB = 0;  // f's direction byte of this thread's vertex in planes A, B
   PlaneCursor cur;
   cur.start(TL, SG::TX, SG::TY);
-  for (int q = 0; q < total; ++q, cur.next(TL, SG::TX, SG::TY)) {
+
+  // One plane: stage it, derive its quantities into dst (role B), then
+  // classify the vertices of plane A using C (previous) and dst (next).
+  auto step = [&](int q, PV& dst, uint16_t& fd_dst, const PV& Cv, const PV& Av, uint16_t fdA) -> bool {
     const int p = cur.p;
     const int pcoord = cur.c0 - 1 + p;  // plane coordinate (z in 3D, y in 2D)
     unsigned char* sp = smem + (kTMA ? (q & SM1) * SG::STAGE_BYTES : 0);
@@ -320,10 +323,11 @@ __global__ void __launch_bounds__(SweepGeom<T, ND>::NT)
     if (kTMA) {
       const bool got = mbar_wait(&bars[q & SM1], (uint32_t)((q / SG::STAGES) & 1));
       waited = q + 1;
-      B = plane_vals<T, ND>(stage, tx, ty);
-      fdB = sp[SG::G_BYTES + tid];
-      ok = __syncthreads_and(got) != 0;
-      if (!ok) break;
+      dst = plane_vals<T, ND>(stage, tx, w);
+      if (ND == 3) fd_dst = (uint16_t)(sp[SG::G_BYTES + (2 * w) * SG::TX + tx] |
+                                       (sp[SG::G_BYTES + (2 * w + 1) * SG::TX + tx] << 8));
+      else fd_dst = sp[SG::G_BYTES + tx];
+      if (!__syncthreads_and(got)) return false;
       if (tid == 0 && q + SG::STAGES < total) issue(q + SG::STAGES);
     } else {
       __syncthreads();
@@ -337,40 +341,56 @@ __global__ void __launch_bounds__(SweepGeom<T, ND>::NT)
         wst[i] = in ? F.g[gx + G.nx * (gy + G.ny * gz)] : qnan<T>();
       }
       __syncthreads();
-      B = plane_vals<T, ND>(stage, tx, ty);
-      const int vx = cur.x0 + tx, vy = (ND == 3) ? cur.y0 + ty : pcoord, vz = (ND == 3) ? pcoord : 0;
-      fdB = (vx < G.nx && vy >= 0 && vy < G.ny && vz >= 0 && vz < G.nz) ? F.fdir[vx + G.nx * (vy + G.ny * vz)]
-                                                                        : (uint8_t)0;
+      dst = plane_vals<T, ND>(stage, tx, w);
+      uint16_t fd = 0;
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int vx = cur.x0 + tx, vy = (ND == 3) ? cur.y0 + RPT * w + k : pcoord, vz = (ND == 3) ? pcoord : 0;
+        if (vx < G.nx && vy >= 0 && vy < G.ny && vz >= 0 && vz < G.nz)
+          fd |= (uint16_t)(F.fdir[vx + G.nx * (vy + G.ny * vz)] << (8 * k));
+      }
+      fd_dst = fd;
     }
     if (p >= 2) {
       const int x = cur.x0 + tx;
-      const int y = (ND == 3) ? cur.y0 + ty : pcoord - 1;
       const int z = (ND == 3) ? pcoord - 1 : 0;
-      const bool valid = x < G.nx && y < G.ny && z < G.nz && (p - 2) < TL.chunk;
-      unsigned bits = 0;
-      if (valid) {
-        const unsigned e = extremum_bits<T, ND>(C, A, B);
-        const unsigned fmx = (fdA & 15) == kSelf, fmn = (fdA >> 4) == kSelf;
-        const unsigned gmx = e & 1u, gmn = (e >> 1) & 1u;
-        bits = (gmx & ~fmx) | ((gmn & ~fmn) << 1) | ((fmx & ~gmx) << 2) | ((fmn & ~gmn) << 3);
-      }
-      if (__any_sync(kFull, bits != 0)) {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const uint32_t b = __ballot_sync(kFull, (bits >> t) & 1u);
-          if (lane == 0) cnt[t] += __popc(b);
+      for (int k = 0; k < RPT; ++k) {
+        const int y = (ND == 3) ? cur.y0 + RPT * w + k : pcoord - 1;
+        const bool valid = x < G.nx && y < G.ny && z < G.nz && (p - 2) < TL.chunk;
+        unsigned bits = 0;
+        if (valid) {
+          const unsigned e = extremum_bits<T, ND, RPT>(Cv, Av, dst, k);
+          const unsigned fdk = (fdA >> (8 * k)) & 0xffu;
+          const unsigned fmx = (fdk & 15) == kSelf, fmn = (fdk >> 4) == kSelf;
+          const unsigned gmx = e & 1u, gmn = (e >> 1) & 1u;
+          bits = (gmx & ~fmx) | ((gmn & ~fmn) << 1) | ((fmx & ~gmx) << 2) | ((fmn & ~gmn) << 3);
         }
-        const uint32_t mask = __ballot_sync(kFull, bits != 0);
-        const int leader = __ffs(mask) - 1;
-        uint32_t b0 = 0;
-        if (lane == leader) b0 = atomicAdd(&st->ncase, (uint32_t)__popc(mask));
-        b0 = __shfl_sync(kFull, b0, leader);
-        if (bits) F.cases[b0 + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)(x + G.nx * (y + G.ny * z));
+        if (__any_sync(kFull, bits != 0)) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const uint32_t b = __ballot_sync(kFull, (bits >> t) & 1u);
+            if (lane == 0) cnt[t] += __popc(b);
+          }
+          const uint32_t mask = __ballot_sync(kFull, bits != 0);
+          const int leader = __ffs(mask) - 1;
+          uint32_t b0 = 0;
+          if (lane == leader) b0 = atomicAdd(&st->ncase, (uint32_t)__popc(mask));
+          b0 = __shfl_sync(kFull, b0, leader);
+          if (bits) F.cases[b0 + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)(x + G.nx * (y + G.ny * z));
+        }
       }
     }
-    C = A;
-    A = B;
-    fdA = fdB;
+    cur.next(TL, SG::TX, SG::TY);
+    return true;
+  };
+
+  PV P0{}, P1{}, P2{};
+  uint16_t f0 = 0, f1 = 0, f2 = 0;
+  for (int q = 0; q < total; q += 3) {  // planes rotate through P0, P1, P2
+    if (!step(q, P0, f0, P1, P2, f2)) { ok = false; break; }
+    if (!step(q + 1, P1, f1, P2, P0, f0)) { ok = false; break; }
+    if (!step(q + 2, P2, f2, P0, P1, f1)) { ok = false; break; }
   }
   if (kTMA && !ok) {
     // give up: record the timeout, then wait (bounded) for loads still in flight
@@ -1026,6 +1046,7 @@ void sweep_tiling(msz_plan_s* p) {
   const int axis = (ND == 3) ? G.nz : G.ny;  // marching axis
   const int nchunks = (axis + 63) / 64;
   TL.chunk = (axis + nchunks - 1) / nchunks;
+  TL.chunk += (4 - TL.chunk % 3) % 3;  // chunk + 2 planes per tile must be a multiple of 3
   TL.chunks = (axis + TL.chunk - 1) / TL.chunk;
   TL.tiles_x = (G.nx + SG::TX - 1) / SG::TX;
   TL.tiles_y = (ND == 3) ? (G.ny + SG::TY - 1) / SG::TY : 1;
@@ -1424,6 +1445,7 @@ const char* msz_strerror(int status) {
 const char* msz_version(void) { return "msz-gb300 0.1"; }
 
 }  // extern "C"
+
 // ---------------------------------------------------------------------------
 // msz_fix_noalloc: the correction loop with no device allocation at all.
 //

@@ -42,19 +42,23 @@ template <>
 __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000ll); }
 
 // Tile geometry. PADX keeps the TMA box start and width 16-byte aligned.
+// 3D: a block of 256 threads covers 32 x 16 vertices of a plane, two rows per
+// thread (rows 2w, 2w+1 for warp w). 2D: 128 threads cover 128 vertices of a
+// row, one per thread.
 template <class T, int ND>
 struct SweepGeom {
   static constexpr int PADX = 16 / (int)sizeof(T);
   static constexpr int TX = (ND == 3) ? 32 : 128;
-  static constexpr int TY = (ND == 3) ? 8 : 1;
-  static constexpr int NT = TX * TY;
+  static constexpr int RPT = (ND == 3) ? 2 : 1;   // rows per thread
+  static constexpr int TY = (ND == 3) ? 16 : 1;
+  static constexpr int NT = (ND == 3) ? 256 : 128;
   static constexpr int BX = TX + 2 * PADX;
   static constexpr int BY = (ND == 3) ? TY + 2 : 1;
   static constexpr int STAGE_ELEMS = BX * BY;
   static constexpr int G_BYTES = ((STAGE_ELEMS * (int)sizeof(T) + 127) / 128) * 128;
-  static constexpr int D_BYTES = ((NT + 127) / 128) * 128;  // f's direction bytes of the tile plane
+  static constexpr int D_BYTES = ((TX * TY + 127) / 128) * 128;  // f's direction bytes of the tile plane
   static constexpr int STAGE_BYTES = G_BYTES + D_BYTES;
-  static constexpr int STAGES = 4;
+  static constexpr int STAGES = (ND == 3) ? 8 : 4;
 };
 
 struct SweepTiling {
@@ -110,71 +114,91 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// Per-plane quantities of one thread's column (see the header comment).
-template <class T>
+// Per-plane quantities of one thread's vertices (RPT rows, see the header
+// comment): the values the plane contributes when it is the vertex's own
+// plane (A), the next plane (B) or the previous plane (C).
+template <class T, int RPT>
 struct PlaneVals {
-  T a0, am, ap;          // g at (x, y), (x-1, y), (x+1, y)
-  T rup_max, rup_min;    // row y+1, columns x..x+1          (3D only)
-  T rdn_max, rdn_min;    // row y-1, columns x-1..x          (3D only)
-  T sup_max, sup_min;    // square x..x+1 by y..y+1 (3D); x..x+1 (2D)
-  T sdn_max, sdn_min;    // square x-1..x by y-1..y (3D); x-1..x (2D)
+  T a0[RPT], am[RPT], ap[RPT];   // g at (x, y), (x-1, y), (x+1, y)
+  T rupM[RPT], rupm[RPT];        // max/min of row y+1, columns x..x+1     (3D only)
+  T rdnM[RPT], rdnm[RPT];        // max/min of row y-1, columns x-1..x     (3D only)
+  T supM[RPT], supm[RPT];        // max/min of square x..x+1 by y..y+1 (3D); x..x+1 (2D)
+  T sdnM[RPT], sdnm[RPT];        // max/min of square x-1..x by y-1..y (3D); x-1..x (2D)
 };
 
+// Reads the thread's neighbourhood from a staged plane and derives the
+// row-pair and square extrema. 3D: rows 2w-1 .. 2w+2 (stage rows 2w .. 2w+3)
+// at columns x-1, x, x+1; each row pair is computed once for both vertices.
 template <class T, int ND>
-__device__ __forceinline__ PlaneVals<T> plane_vals(const T* s, int tx, int ty) {
+__device__ __forceinline__ PlaneVals<T, SweepGeom<T, ND>::RPT> plane_vals(const T* s, int tx, int w) {
   using SG = SweepGeom<T, ND>;
-  PlaneVals<T> P;
+  PlaneVals<T, SG::RPT> P;
   const int c = tx + SG::PADX;
-  if (ND == 3) {
-    const int r = ty + 1;
-    const T* m1 = s + (r - 1) * SG::BX + c;
-    const T* m0 = s + r * SG::BX + c;
-    const T* p1 = s + (r + 1) * SG::BX + c;
-    P.a0 = m0[0];
-    P.am = m0[-1];
-    P.ap = m0[1];
-    const T u0 = p1[0], u1 = p1[1], d0 = m1[-1], d1 = m1[0];
-    P.rup_max = vmax(u0, u1);
-    P.rup_min = vmin(u0, u1);
-    P.rdn_max = vmax(d0, d1);
-    P.rdn_min = vmin(d0, d1);
-    P.sup_max = vmax(vmax(P.a0, P.ap), P.rup_max);
-    P.sup_min = vmin(vmin(P.a0, P.ap), P.rup_min);
-    P.sdn_max = vmax(vmax(P.am, P.a0), P.rdn_max);
-    P.sdn_min = vmin(vmin(P.am, P.a0), P.rdn_min);
+  if constexpr (ND == 3) {
+    const T* r0 = s + (2 * w) * SG::BX + c;  // row y-1
+    T a[4][3];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      a[r][0] = r0[r * SG::BX - 1];
+      a[r][1] = r0[r * SG::BX];
+      a[r][2] = r0[r * SG::BX + 1];
+    }
+    // hi pair: columns x..x+1; lo pair: columns x-1..x
+    T hiM[4], him[4], loM[4], lom[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      hiM[r] = vmax(a[r][1], a[r][2]);
+      him[r] = vmin(a[r][1], a[r][2]);
+      loM[r] = vmax(a[r][0], a[r][1]);
+      lom[r] = vmin(a[r][0], a[r][1]);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {  // vertex row = r k+1
+      P.a0[k] = a[k + 1][1];
+      P.am[k] = a[k + 1][0];
+      P.ap[k] = a[k + 1][2];
+      P.rupM[k] = hiM[k + 2];
+      P.rupm[k] = him[k + 2];
+      P.rdnM[k] = loM[k];
+      P.rdnm[k] = lom[k];
+      P.supM[k] = vmax(hiM[k + 1], hiM[k + 2]);
+      P.supm[k] = vmin(him[k + 1], him[k + 2]);
+      P.sdnM[k] = vmax(loM[k], loM[k + 1]);
+      P.sdnm[k] = vmin(lom[k], lom[k + 1]);
+    }
   } else {
     const T* m0 = s + c;
-    P.a0 = m0[0];
-    P.am = m0[-1];
-    P.ap = m0[1];
-    P.rup_max = P.rup_min = P.rdn_max = P.rdn_min = P.a0;  // unused in 2D
-    P.sup_max = vmax(P.a0, P.ap);
-    P.sup_min = vmin(P.a0, P.ap);
-    P.sdn_max = vmax(P.am, P.a0);
-    P.sdn_min = vmin(P.am, P.a0);
+    P.a0[0] = m0[0];
+    P.am[0] = m0[-1];
+    P.ap[0] = m0[1];
+    P.rupM[0] = P.rupm[0] = P.rdnM[0] = P.rdnm[0] = P.a0[0];  // unused in 2D
+    P.supM[0] = vmax(P.a0[0], P.ap[0]);
+    P.supm[0] = vmin(P.a0[0], P.ap[0]);
+    P.sdnM[0] = vmax(P.am[0], P.a0[0]);
+    P.sdnm[0] = vmin(P.am[0], P.a0[0]);
   }
   return P;
 }
 
-// Extremum flags of the vertex at the centre of plane A, with B the next
+// Extremum flags of the thread's k-th vertex of plane A, with B the next
 // plane (larger indices) and C the previous one. Bit 0: maximum, bit 1:
 // minimum (closed-ring order with ties to the larger index).
-template <class T, int ND>
-__device__ __forceinline__ unsigned extremum_bits(const PlaneVals<T>& C, const PlaneVals<T>& A,
-                                                  const PlaneVals<T>& B) {
+template <class T, int ND, int RPT>
+__device__ __forceinline__ unsigned extremum_bits(const PlaneVals<T, RPT>& C, const PlaneVals<T, RPT>& A,
+                                                  const PlaneVals<T, RPT>& B, int k) {
   T maxU, maxL, minU, minL;
-  if (ND == 3) {
-    maxU = vmax(A.ap, vmax(A.rup_max, B.sup_max));
-    maxL = vmax(A.am, vmax(A.rdn_max, C.sdn_max));
-    minU = vmin(A.ap, vmin(A.rup_min, B.sup_min));
-    minL = vmin(A.am, vmin(A.rdn_min, C.sdn_min));
+  if constexpr (ND == 3) {
+    maxU = vmax(A.ap[k], vmax(A.rupM[k], B.supM[k]));
+    maxL = vmax(A.am[k], vmax(A.rdnM[k], C.sdnM[k]));
+    minU = vmin(A.ap[k], vmin(A.rupm[k], B.supm[k]));
+    minL = vmin(A.am[k], vmin(A.rdnm[k], C.sdnm[k]));
   } else {
-    maxU = vmax(A.ap, B.sup_max);
-    maxL = vmax(A.am, C.sdn_max);
-    minU = vmin(A.ap, B.sup_min);
-    minL = vmin(A.am, C.sdn_min);
+    maxU = vmax(A.ap[k], B.supM[k]);
+    maxL = vmax(A.am[k], C.sdnM[k]);
+    minU = vmin(A.ap[k], B.supm[k]);
+    minL = vmin(A.am[k], C.sdnm[k]);
   }
-  const T g = A.a0;
+  const T g = A.a0[k];
   const bool is_max = !(maxU >= g) && !(maxL > g);
   const bool is_min = !(minU < g) && !(minL <= g);
   return (unsigned)is_max | ((unsigned)is_min << 1);
