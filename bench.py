@@ -184,6 +184,27 @@ def _cpu_workload(size):
     return f, cases
 
 
+def profile_fix(args):
+    """One warm-up-free fix of the workload at one bound (for profiler runs)."""
+    import torch
+
+    import paper_2406_09423_gb300 as msz
+    from paper_2406_09423_gb300 import synth
+
+    dev = torch.device("cuda", 0)
+    f = synth.turbulence3d(args.size, 3, device=dev)
+    xi = synth.xi_for(f, args.profile_fix)
+    fh = synth.quantise_torch(f, xi)
+    plan = msz.Plan(tuple(f.shape), f.dtype)
+    r = plan.fix(f, fh, xi, copy=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"size": args.size, "rel": args.profile_fix, "sweeps": r.counts["sweeps"],
+                      "label_evals": r.counts["label_evals"], "launches": r.launches,
+                      "n_edits": r.n_edits}), flush=True)
+    plan.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -194,7 +215,11 @@ def main():
     ap.add_argument("--crop", type=int, default=64, help="oracle sample block edge")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-fix", type=float, default=None, metavar="REL",
+                    help="run one fix of the --size workload at xi = REL * range and exit (for ncu captures)")
     args = ap.parse_args()
+    if args.profile_fix is not None:
+        return profile_fix(args)
     if args.impl == "reference":
         return run_reference(args)
 

@@ -258,19 +258,23 @@ struct PlaneCursor {
 };
 
 template <class T, int ND, bool kTMA>
-__global__ void __launch_bounds__(SweepGeom<T, ND>::NT)
+__global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND>::NT)
     k_csweep(Field<T> F, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap dmap,
              SweepTiling TL) {
   using SG = SweepGeom<T, ND>;
   constexpr int RPT = SG::RPT;
+  constexpr int NCW = SG::NT / 32;  // consumer warps
   using PV = PlaneVals<T, RPT>;
   static_assert((SG::STAGES & (SG::STAGES - 1)) == 0, "power-of-two stages");
   DevState* st = F.st;
   if (st->phase != PH_C) return;
   __shared__ alignas(128) unsigned char smem[(kTMA ? SG::STAGES : 1) * SG::STAGE_BYTES];
-  __shared__ alignas(8) uint64_t bars[SG::STAGES];
+  __shared__ alignas(8) uint64_t full[SG::STAGES];
+  __shared__ alignas(8) uint64_t empty[SG::STAGES];
+  __shared__ int s_abort;
   const int tid = threadIdx.x;
-  const int tx = tid % SG::TX, w = tid / SG::TX;  // 3D: warp w owns rows 2w, 2w+1
+  const bool producer = kTMA && tid >= SG::NT;
+  const int tx = tid % SG::TX, w = (tid / SG::TX) % (SG::NT / SG::TX);  // 3D: consumer warp w owns rows 2w, 2w+1
   const int lane = tid & 31;
   const int ppt = TL.chunk + 2;  // planes per tile, a multiple of 3
   const int my_tiles =
@@ -278,128 +282,164 @@ __global__ void __launch_bounds__(SweepGeom<T, ND>::NT)
   const int total = my_tiles * ppt;
   const Geom G = F.G;
   constexpr int SM1 = SG::STAGES - 1;
-
-  PlaneCursor pc_issue{};  // producer cursor (thread 0 only)
-  auto issue = [&](int q) {
-    const int pc = pc_issue.c0 - 1 + pc_issue.p;
-    uint64_t* bar = &bars[q & SM1];
-    unsigned char* sp = smem + (q & SM1) * SG::STAGE_BYTES;
-    mbar_expect_tx(bar, (uint32_t)(SG::STAGE_ELEMS * sizeof(T) + SG::TX * SG::TY));
-    if (ND == 3) {
-      tma_load_3d(sp, &tmap, bar, pc_issue.x0 - SG::PADX, pc_issue.y0 - 1, pc);
-      tma_load_3d(sp + SG::G_BYTES, &dmap, bar, pc_issue.x0, pc_issue.y0, pc);
-    } else {
-      tma_load_2d(sp, &tmap, bar, pc_issue.x0 - SG::PADX, pc);
-      tma_load_2d(sp + SG::G_BYTES, &dmap, bar, pc_issue.x0, pc);
-    }
-    pc_issue.next(TL, SG::TX, SG::TY);
-  };
+  uint32_t cnt[4] = {0, 0, 0, 0};
 
   if (kTMA) {
     if (tid == 0) {
-      for (int s = 0; s < SG::STAGES; ++s) mbar_init(&bars[s], 1);
+      for (int s = 0; s < SG::STAGES; ++s) {
+        mbar_init(&full[s], 1);
+        mbar_init(&empty[s], NCW);
+      }
+      s_abort = 0;
       mbar_fence_init();
     }
     __syncthreads();
-    if (tid == 0) {
-      pc_issue.start(TL, SG::TX, SG::TY);
-      for (int q = 0; q < SG::STAGES && q < total; ++q) issue(q);
-    }
   }
 
-  uint32_t cnt[4] = {0, 0, 0, 0};
-  bool ok = true;
-  int waited = 0;  // TMA stages consumed
-  PlaneCursor cur;
-  cur.start(TL, SG::TX, SG::TY);
-
-  // One plane: stage it, derive its quantities into dst (role B), then
-  // classify the vertices of plane A using C (previous) and dst (next).
-  auto step = [&](int q, PV& dst, uint16_t& fd_dst, const PV& Cv, const PV& Av, uint16_t fdA) -> bool {
-    const int p = cur.p;
-    const int pcoord = cur.c0 - 1 + p;  // plane coordinate (z in 3D, y in 2D)
-    unsigned char* sp = smem + (kTMA ? (q & SM1) * SG::STAGE_BYTES : 0);
-    const T* stage = reinterpret_cast<const T*>(sp);
-    if (kTMA) {
-      const bool got = mbar_wait(&bars[q & SM1], (uint32_t)((q / SG::STAGES) & 1));
-      waited = q + 1;
-      dst = plane_vals<T, ND>(stage, tx, w);
-      if (ND == 3) fd_dst = (uint16_t)(sp[SG::G_BYTES + (2 * w) * SG::TX + tx] |
-                                       (sp[SG::G_BYTES + (2 * w + 1) * SG::TX + tx] << 8));
-      else fd_dst = sp[SG::G_BYTES + tx];
-      if (!__syncthreads_and(got)) return false;
-      if (tid == 0 && q + SG::STAGES < total) issue(q + SG::STAGES);
-    } else {
-      __syncthreads();
-      T* wst = reinterpret_cast<T*>(sp);
-      for (int i = tid; i < SG::STAGE_ELEMS; i += SG::NT) {
-        const int col = i % SG::BX, row = i / SG::BX;
-        const int gx = cur.x0 - SG::PADX + col;
-        const int gy = (ND == 3) ? cur.y0 - 1 + row : pcoord;
-        const int gz = (ND == 3) ? pcoord : 0;
-        const bool in = gx >= 0 && gx < G.nx && gy >= 0 && gy < G.ny && gz >= 0 && gz < G.nz;
-        wst[i] = in ? F.g[gx + G.nx * (gy + G.ny * gz)] : qnan<T>();
-      }
-      __syncthreads();
-      dst = plane_vals<T, ND>(stage, tx, w);
-      uint16_t fd = 0;
-#pragma unroll
-      for (int k = 0; k < RPT; ++k) {
-        const int vx = cur.x0 + tx, vy = (ND == 3) ? cur.y0 + RPT * w + k : pcoord, vz = (ND == 3) ? pcoord : 0;
-        if (vx < G.nx && vy >= 0 && vy < G.ny && vz >= 0 && vz < G.nz)
-          fd |= (uint16_t)(F.fdir[vx + G.nx * (vy + G.ny * vz)] << (8 * k));
-      }
-      fd_dst = fd;
-    }
-    if (p >= 2) {
-      const int x = cur.x0 + tx;
-      const int z = (ND == 3) ? pcoord - 1 : 0;
-#pragma unroll
-      for (int k = 0; k < RPT; ++k) {
-        const int y = (ND == 3) ? cur.y0 + RPT * w + k : pcoord - 1;
-        const bool valid = x < G.nx && y < G.ny && z < G.nz && (p - 2) < TL.chunk;
-        unsigned bits = 0;
-        if (valid) {
-          const unsigned e = extremum_bits<T, ND, RPT>(Cv, Av, dst, k);
-          const unsigned fdk = (fdA >> (8 * k)) & 0xffu;
-          const unsigned fmx = (fdk & 15) == kSelf, fmn = (fdk >> 4) == kSelf;
-          const unsigned gmx = e & 1u, gmn = (e >> 1) & 1u;
-          bits = (gmx & ~fmx) | ((gmn & ~fmn) << 1) | ((fmx & ~gmx) << 2) | ((fmn & ~gmn) << 3);
-        }
-        if (__any_sync(kFull, bits != 0)) {
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            const uint32_t b = __ballot_sync(kFull, (bits >> t) & 1u);
-            if (lane == 0) cnt[t] += __popc(b);
+  if (producer) {
+    // Producer warp (lane 0): streams planes into the stage ring. Before it
+    // refills a stage it waits until every consumer warp has released it.
+    if (lane == 0) {
+      PlaneCursor pc{};
+      pc.start(TL, SG::TX, SG::TY);
+      int issued = 0;
+      for (int q = 0; q < total; ++q) {
+        const int s = q & SM1;
+        if (q >= SG::STAGES) {
+          if (!mbar_wait_or_abort(&empty[s], (uint32_t)(((q - SG::STAGES) / SG::STAGES) & 1), &s_abort)) {
+            atomicExch(&s_abort, 1);
+            break;
           }
-          const uint32_t mask = __ballot_sync(kFull, bits != 0);
-          const int leader = __ffs(mask) - 1;
-          uint32_t b0 = 0;
-          if (lane == leader) b0 = atomicAdd(&st->ncase, (uint32_t)__popc(mask));
-          b0 = __shfl_sync(kFull, b0, leader);
-          if (bits) F.cases[b0 + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)(x + G.nx * (y + G.ny * z));
         }
+        const int pcoord = pc.c0 - 1 + pc.p;
+        unsigned char* sp = smem + s * SG::STAGE_BYTES;
+        mbar_expect_tx(&full[s], (uint32_t)(SG::STAGE_ELEMS * sizeof(T) + SG::TX * SG::TY));
+        if (ND == 3) {
+          tma_load_3d(sp, &tmap, &full[s], pc.x0 - SG::PADX, pc.y0 - 1, pcoord);
+          tma_load_3d(sp + SG::G_BYTES, &dmap, &full[s], pc.x0, pc.y0, pcoord);
+        } else {
+          tma_load_2d(sp, &tmap, &full[s], pc.x0 - SG::PADX, pcoord);
+          tma_load_2d(sp + SG::G_BYTES, &dmap, &full[s], pc.x0, pcoord);
+        }
+        pc.next(TL, SG::TX, SG::TY);
+        issued = q + 1;
+      }
+      if (*(volatile int*)&s_abort) {
+        // wait (bounded) for the loads still in flight before leaving
+        const int first = (issued > SG::STAGES) ? issued - SG::STAGES : 0;
+        for (int q = first; q < issued; ++q) mbar_wait(&full[q & SM1], (uint32_t)((q / SG::STAGES) & 1));
+        atomicOr(&st->err_bits, E_TIMEOUT);
       }
     }
-    cur.next(TL, SG::TX, SG::TY);
-    return true;
-  };
+  } else {
+    PlaneCursor cur;
+    cur.start(TL, SG::TX, SG::TY);
+    // vertices of this thread inside the grid in x and y (bits 8k, 8k+4)
+    auto xy_mask = [&]() -> uint32_t {
+      uint32_t m = 0;
+      const int x = cur.x0 + tx;
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int y = (ND == 3) ? cur.y0 + RPT * w + k : 0;
+        if (x < G.nx && y < G.ny) m |= 0x11u << (8 * k);
+      }
+      return m;
+    };
+    uint32_t vmask = xy_mask();
+    // One plane: stage it, derive its quantities into dst (role B), then
+    // classify the vertices of plane A using C (previous) and dst (next).
+    auto step = [&](int q, PV& dst, uint16_t& fd_dst, const PV& Cv, const PV& Av, uint16_t fdA) -> bool {
+      const int p = cur.p;
+      const int pcoord = cur.c0 - 1 + p;  // plane coordinate (z in 3D, y in 2D)
+      unsigned char* sp = smem + (kTMA ? (q & SM1) * SG::STAGE_BYTES : 0);
+      const T* stage = reinterpret_cast<const T*>(sp);
+      if (kTMA) {
+        const bool got = mbar_wait_or_abort(&full[q & SM1], (uint32_t)((q / SG::STAGES) & 1), &s_abort);
+        if (!__all_sync(kFull, got)) {
+          if (lane == 0) atomicExch(&s_abort, 1);
+          return false;
+        }
+        dst = plane_vals<T, ND>(stage, tx, w);
+        if (ND == 3) fd_dst = (uint16_t)(sp[SG::G_BYTES + (2 * w) * SG::TX + tx] |
+                                         (sp[SG::G_BYTES + (2 * w + 1) * SG::TX + tx] << 8));
+        else fd_dst = sp[SG::G_BYTES + tx];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[q & SM1]);
+      } else {
+        __syncthreads();
+        T* wst = reinterpret_cast<T*>(sp);
+        for (int i = tid; i < SG::STAGE_ELEMS; i += SG::NT) {
+          const int col = i % SG::BX, row = i / SG::BX;
+          const int gx = cur.x0 - SG::PADX + col;
+          const int gy = (ND == 3) ? cur.y0 - 1 + row : pcoord;
+          const int gz = (ND == 3) ? pcoord : 0;
+          const bool in = gx >= 0 && gx < G.nx && gy >= 0 && gy < G.ny && gz >= 0 && gz < G.nz;
+          wst[i] = in ? F.g[gx + G.nx * (gy + G.ny * gz)] : qnan<T>();
+        }
+        __syncthreads();
+        dst = plane_vals<T, ND>(stage, tx, w);
+        uint16_t fd = 0;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+          const int vx = cur.x0 + tx, vy = (ND == 3) ? cur.y0 + RPT * w + k : pcoord, vz = (ND == 3) ? pcoord : 0;
+          if (vx < G.nx && vy >= 0 && vy < G.ny && vz >= 0 && vz < G.nz)
+            fd |= (uint16_t)(F.fdir[vx + G.nx * (vy + G.ny * vz)] << (8 * k));
+        }
+        fd_dst = fd;
+      }
+      if (p >= 2) {
+        // g's extremum flags and f's, both packed at bits 8k (max) and 8k+4
+        // (min) for vertex k; a vertex is a case when they differ.
+        uint32_t gb = 0;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+          gb |= ((uint32_t)is_max_at<T, RPT>(Cv, Av, dst, k) << (8 * k)) |
+                ((uint32_t)is_min_at<T, RPT>(Cv, Av, dst, k) << (8 * k + 4));
+        const uint32_t fa = fdA;
+        const uint32_t fb = fa & (fa >> 1) & (fa >> 2) & (fa >> 3) & 0x1111u;  // nibble == 15
+        uint32_t diff = (gb ^ fb) & vmask;
+        if (!(p - 2 < TL.chunk && pcoord - 1 < ((ND == 3) ? G.nz : G.ny))) diff = 0;
+        if (__any_sync(kFull, diff != 0)) {
+          const int x = cur.x0 + tx;
+          const int z = (ND == 3) ? pcoord - 1 : 0;
+#pragma unroll
+          for (int k = 0; k < RPT; ++k) {
+            const int y = (ND == 3) ? cur.y0 + RPT * w + k : pcoord - 1;
+            const uint32_t gk = gb >> (8 * k), fk = fb >> (8 * k), dk = diff >> (8 * k);
+            unsigned bits = 0;
+            if (dk & 0x11u) {
+              const unsigned gmx = gk & 1u, gmn = (gk >> 4) & 1u, fmx = fk & 1u, fmn = (fk >> 4) & 1u;
+              bits = (gmx & ~fmx) | ((gmn & ~fmn) << 1) | ((fmx & ~gmx) << 2) | ((fmn & ~gmn) << 3);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const uint32_t b = __ballot_sync(kFull, (bits >> t) & 1u);
+              if (lane == 0) cnt[t] += __popc(b);
+            }
+            const uint32_t mask = __ballot_sync(kFull, bits != 0);
+            if (mask) {
+              const int leader = __ffs(mask) - 1;
+              uint32_t b0 = 0;
+              if (lane == leader) b0 = atomicAdd(&st->ncase, (uint32_t)__popc(mask));
+              b0 = __shfl_sync(kFull, b0, leader);
+              if (bits) F.cases[b0 + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)(x + G.nx * (y + G.ny * z));
+            }
+          }
+        }
+      }
+      const int tile_before = cur.tile;
+      cur.next(TL, SG::TX, SG::TY);
+      if (cur.tile != tile_before) vmask = xy_mask();
+      return true;
+    };
 
-  PV P0{}, P1{}, P2{};
-  uint16_t f0 = 0, f1 = 0, f2 = 0;
-  for (int q = 0; q < total; q += 3) {  // planes rotate through P0, P1, P2
-    if (!step(q, P0, f0, P1, P2, f2)) { ok = false; break; }
-    if (!step(q + 1, P1, f1, P2, P0, f0)) { ok = false; break; }
-    if (!step(q + 2, P2, f2, P0, P1, f1)) { ok = false; break; }
-  }
-  if (kTMA && !ok) {
-    // give up: record the timeout, then wait (bounded) for loads still in flight
-    if (tid == 0) {
-      atomicOr(&st->err_bits, E_TIMEOUT);
-      const int issued = (total < waited + SG::STAGES) ? total : waited + SG::STAGES;
-      for (int q = waited; q < issued; ++q) mbar_wait(&bars[q & SM1], (uint32_t)((q / SG::STAGES) & 1));
+    PV P0{}, P1{}, P2{};
+    uint16_t f0 = 0, f1 = 0, f2 = 0;
+    for (int q = 0; q < total; q += 3) {  // planes rotate through P0, P1, P2
+      if (!step(q, P0, f0, P1, P2, f2)) break;
+      if (!step(q + 1, P1, f1, P2, P0, f0)) break;
+      if (!step(q + 2, P2, f2, P0, P1, f1)) break;
     }
-    __syncthreads();
   }
   block_add<4>(cnt, st->counts);
   if (last_block(st) && threadIdx.x == 0) {
@@ -1053,7 +1093,7 @@ void sweep_tiling(msz_plan_s* p) {
   TL.ntiles = TL.tiles_x * TL.tiles_y * TL.chunks;
   int occ = 0;
   if (p->use_tma)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_csweep<T, ND, true>, SG::NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_csweep<T, ND, true>, SG::NTP, 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_csweep<T, ND, false>, SG::NT, 0);
   if (occ < 1) occ = 1;
@@ -1122,9 +1162,10 @@ template <class T, int ND>
 void launch_step(msz_plan_s* p, const Field<T>& F, cudaStream_t s, int slot) {
   const int db = p->dense_blocks, sb = p->sparse_blocks;
   constexpr int NT = SweepGeom<T, ND>::NT;
+  constexpr int NTP = SweepGeom<T, ND>::NTP;
   cudaEvent_t* e = (slot >= 0) ? p->tev[slot] : nullptr;
   if (e) cudaEventRecord(e[0], s);
-  if (p->use_tma) k_csweep<T, ND, true><<<p->csweep_blocks, NT, 0, s>>>(F, p->tmap, p->dmap, p->tiling);
+  if (p->use_tma) k_csweep<T, ND, true><<<p->csweep_blocks, NTP, 0, s>>>(F, p->tmap, p->dmap, p->tiling);
   else k_csweep<T, ND, false><<<p->csweep_blocks, NT, 0, s>>>(F, p->tmap, p->dmap, p->tiling);
   if (e) cudaEventRecord(e[1], s);
   if (e) cudaEventRecord(e[6], s);

@@ -6,21 +6,27 @@
 //   g_v > max(U*(v))  and  g_v >= max(L*(v)),
 // where U*(v) = v + ({0,1}^d \ 0) holds the neighbours of larger index and
 // L*(v) = v - ({0,1}^d \ 0) those of smaller index (ties go to the larger
-// index); symmetrically for the least. Both sets are unit cubes minus a corner,
-// so their max/min are built separably from row pairs and 2x2 squares of each
-// plane: about twenty FMNMX per vertex instead of a 14-way argmax with index
-// tie-breaks. Out-of-grid vertices are NaN, which fmax/fmin ignore, and an
-// empty set gives NaN, which the negated comparisons treat as "no neighbour".
+// index); symmetrically for the least. With A the plane of v, B the next and
+// C the previous plane, and the "L" corners
+//   LUR_P(x,y) = {P(x+1,y), P(x,y+1), P(x+1,y+1)},
+//   LLL_P(x,y) = {P(x-1,y), P(x,y-1), P(x-1,y-1)}
+// (in 2D, where planes are rows: LUR_P(x) = {P(x+1)}, LLL_P(x) = {P(x-1)}),
+//   U*(v) = LUR_A u {B(x,y)} u LUR_B,   L*(v) = LLL_A u {C(x,y)} u LLL_C,
+// so each plane contributes one three-input max and min per vertex and the
+// test costs about a dozen FMNMX/FSETP per vertex. Out-of-grid vertices are
+// NaN, which max/min ignore; an empty set gives NaN, which the negated
+// comparisons treat as "no neighbour".
 //
 // Data movement: a block owns an x-y tile and marches along z (3D; rows
 // along y in 2D). Each plane of the tile plus a one-vertex halo (widened in x
 // to a 16-byte multiple) is fetched by TMA (cp.async.bulk.tensor) into a
-// ring of shared-memory stages guarded by mbarriers; the tensor map's
-// out-of-bounds fill supplies the NaN halo. Grids whose row pitch is not a
-// multiple of 16 bytes use the same kernel with plain coalesced loads.
-// The original field's extremum flags come from its direction bytes, fetched
-// through the same stages (a second tensor map), so the sweep reads 5 bytes
-// per float32 vertex and writes only the (sparse) case list.
+// ring of shared-memory stages guarded by full/empty mbarriers; a producer
+// warp issues the copies and the tensor map's out-of-bounds fill supplies
+// the NaN halo. Grids whose row pitch is not a multiple of 16 bytes use the
+// same kernel with plain coalesced loads. The original field's extremum
+// flags come from its direction bytes, fetched through the same stages (a
+// second tensor map), so the sweep reads 5 bytes per float32 vertex and
+// writes only the (sparse) case list.
 #pragma once
 
 #include <cuda.h>
@@ -33,6 +39,20 @@ __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+// Three-input max / min (a single instruction for float32 on sm_100+; NaN
+// operands are ignored like in the two-input form).
+__device__ __forceinline__ float vmax3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float vmin3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ double vmax3(double a, double b, double c) { return fmax(fmax(a, b), c); }
+__device__ __forceinline__ double vmin3(double a, double b, double c) { return fmin(fmin(a, b), c); }
 
 template <class T>
 __device__ __forceinline__ T qnan();
@@ -51,7 +71,8 @@ struct SweepGeom {
   static constexpr int TX = (ND == 3) ? 32 : 128;
   static constexpr int RPT = (ND == 3) ? 2 : 1;   // rows per thread
   static constexpr int TY = (ND == 3) ? 16 : 1;
-  static constexpr int NT = (ND == 3) ? 256 : 128;
+  static constexpr int NT = (ND == 3) ? 256 : 128;  // consumer threads
+  static constexpr int NTP = NT + 32;               // + one producer warp (TMA path)
   static constexpr int BX = TX + 2 * PADX;
   static constexpr int BY = (ND == 3) ? TY + 2 : 1;
   static constexpr int STAGE_ELEMS = BX * BY;
@@ -81,6 +102,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -94,8 +118,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait: false if the phase did not complete within the limit.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < (1u << 26); ++i)
+  for (uint32_t i = 0; i < (1u << 24); ++i)
     if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// Bounded wait that also gives up as soon as *abort is set by another warp.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, const int* abort) {
+  for (uint32_t i = 0; i < (1u << 24); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 63u && *(const volatile int*)abort) return false;
+  }
   return false;
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -114,21 +146,18 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// Per-plane quantities of one thread's vertices (RPT rows, see the header
-// comment): the values the plane contributes when it is the vertex's own
-// plane (A), the next plane (B) or the previous plane (C).
+// Per-plane quantities of one thread's vertices (RPT rows): the centre value
+// and the extrema of the two "L" corners (see the header comment).
 template <class T, int RPT>
 struct PlaneVals {
-  T a0[RPT], am[RPT], ap[RPT];   // g at (x, y), (x-1, y), (x+1, y)
-  T rupM[RPT], rupm[RPT];        // max/min of row y+1, columns x..x+1     (3D only)
-  T rdnM[RPT], rdnm[RPT];        // max/min of row y-1, columns x-1..x     (3D only)
-  T supM[RPT], supm[RPT];        // max/min of square x..x+1 by y..y+1 (3D); x..x+1 (2D)
-  T sdnM[RPT], sdnm[RPT];        // max/min of square x-1..x by y-1..y (3D); x-1..x (2D)
+  T a0[RPT];                 // g at (x, y)
+  T lurM[RPT], lurm[RPT];    // max / min of LUR
+  T lllM[RPT], lllm[RPT];    // max / min of LLL
 };
 
-// Reads the thread's neighbourhood from a staged plane and derives the
-// row-pair and square extrema. 3D: rows 2w-1 .. 2w+2 (stage rows 2w .. 2w+3)
-// at columns x-1, x, x+1; each row pair is computed once for both vertices.
+// Reads the thread's neighbourhood from a staged plane. 3D: rows y-1 .. y+2
+// (stage rows 2w .. 2w+3) at columns x-1, x, x+1 for the two vertices of
+// rows y = 2w, 2w+1 (tile-local).
 template <class T, int ND>
 __device__ __forceinline__ PlaneVals<T, SweepGeom<T, ND>::RPT> plane_vals(const T* s, int tx, int w) {
   using SG = SweepGeom<T, ND>;
@@ -143,65 +172,41 @@ __device__ __forceinline__ PlaneVals<T, SweepGeom<T, ND>::RPT> plane_vals(const 
       a[r][1] = r0[r * SG::BX];
       a[r][2] = r0[r * SG::BX + 1];
     }
-    // hi pair: columns x..x+1; lo pair: columns x-1..x
-    T hiM[4], him[4], loM[4], lom[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      hiM[r] = vmax(a[r][1], a[r][2]);
-      him[r] = vmin(a[r][1], a[r][2]);
-      loM[r] = vmax(a[r][0], a[r][1]);
-      lom[r] = vmin(a[r][0], a[r][1]);
-    }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {  // vertex row = r k+1
       P.a0[k] = a[k + 1][1];
-      P.am[k] = a[k + 1][0];
-      P.ap[k] = a[k + 1][2];
-      P.rupM[k] = hiM[k + 2];
-      P.rupm[k] = him[k + 2];
-      P.rdnM[k] = loM[k];
-      P.rdnm[k] = lom[k];
-      P.supM[k] = vmax(hiM[k + 1], hiM[k + 2]);
-      P.supm[k] = vmin(him[k + 1], him[k + 2]);
-      P.sdnM[k] = vmax(loM[k], loM[k + 1]);
-      P.sdnm[k] = vmin(lom[k], lom[k + 1]);
+      P.lurM[k] = vmax3(a[k + 1][2], a[k + 2][1], a[k + 2][2]);
+      P.lurm[k] = vmin3(a[k + 1][2], a[k + 2][1], a[k + 2][2]);
+      P.lllM[k] = vmax3(a[k + 1][0], a[k][0], a[k][1]);
+      P.lllm[k] = vmin3(a[k + 1][0], a[k][0], a[k][1]);
     }
   } else {
     const T* m0 = s + c;
     P.a0[0] = m0[0];
-    P.am[0] = m0[-1];
-    P.ap[0] = m0[1];
-    P.rupM[0] = P.rupm[0] = P.rdnM[0] = P.rdnm[0] = P.a0[0];  // unused in 2D
-    P.supM[0] = vmax(P.a0[0], P.ap[0]);
-    P.supm[0] = vmin(P.a0[0], P.ap[0]);
-    P.sdnM[0] = vmax(P.am[0], P.a0[0]);
-    P.sdnm[0] = vmin(P.am[0], P.a0[0]);
+    P.lurM[0] = P.lurm[0] = m0[1];
+    P.lllM[0] = P.lllm[0] = m0[-1];
   }
   return P;
 }
 
-// Extremum flags of the thread's k-th vertex of plane A, with B the next
-// plane (larger indices) and C the previous one. Bit 0: maximum, bit 1:
-// minimum (closed-ring order with ties to the larger index).
-template <class T, int ND, int RPT>
-__device__ __forceinline__ unsigned extremum_bits(const PlaneVals<T, RPT>& C, const PlaneVals<T, RPT>& A,
-                                                  const PlaneVals<T, RPT>& B, int k) {
-  T maxU, maxL, minU, minL;
-  if constexpr (ND == 3) {
-    maxU = vmax(A.ap[k], vmax(A.rupM[k], B.supM[k]));
-    maxL = vmax(A.am[k], vmax(A.rdnM[k], C.sdnM[k]));
-    minU = vmin(A.ap[k], vmin(A.rupm[k], B.supm[k]));
-    minL = vmin(A.am[k], vmin(A.rdnm[k], C.sdnm[k]));
-  } else {
-    maxU = vmax(A.ap[k], B.supM[k]);
-    maxL = vmax(A.am[k], C.sdnM[k]);
-    minU = vmin(A.ap[k], B.supm[k]);
-    minL = vmin(A.am[k], C.sdnm[k]);
-  }
+// Extremum flags of the thread's vertices of plane A (B next, C previous),
+// packed two bits per vertex: bit 4k maximum, bit 4k+2 minimum... see
+// kBitMax / kBitMin.
+template <class T, int RPT>
+__device__ __forceinline__ bool is_max_at(const PlaneVals<T, RPT>& C, const PlaneVals<T, RPT>& A,
+                                          const PlaneVals<T, RPT>& B, int k) {
+  const T maxU = vmax3(A.lurM[k], B.a0[k], B.lurM[k]);
+  const T maxL = vmax3(A.lllM[k], C.a0[k], C.lllM[k]);
   const T g = A.a0[k];
-  const bool is_max = !(maxU >= g) && !(maxL > g);
-  const bool is_min = !(minU < g) && !(minL <= g);
-  return (unsigned)is_max | ((unsigned)is_min << 1);
+  return !(maxU >= g) && !(maxL > g);
+}
+template <class T, int RPT>
+__device__ __forceinline__ bool is_min_at(const PlaneVals<T, RPT>& C, const PlaneVals<T, RPT>& A,
+                                          const PlaneVals<T, RPT>& B, int k) {
+  const T minU = vmin3(A.lurm[k], B.a0[k], B.lurm[k]);
+  const T minL = vmin3(A.lllm[k], C.a0[k], C.lllm[k]);
+  const T g = A.a0[k];
+  return !(minU < g) && !(minL <= g);
 }
 
 }  // namespace msz
