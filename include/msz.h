@@ -129,6 +129,26 @@ int msz_fix_host(msz_plan p, const void* orig_host, const void* decomp_host, dou
                  uint32_t* edit_idx_host, void* edit_val_host, int32_t* label_max_host,
                  int32_t* label_min_host, void* stream, msz_result* out);
 
+/* Batched form: many independent fields of uneven shapes and mixed
+ * float32 / float64 corrected together (Sec. 5's per-vertex parallelism
+ * applied across fields). Every kernel of a step works on all fields of a
+ * (dtype, dimension) group at once; each field keeps its own state machine
+ * and drops out when it converges, so the results are bit-identical to
+ * msz_fix on each field alone. The step sequence is captured once in a CUDA
+ * graph and replayed.
+ *   n fields; ndim[i], dims[3*i .. 3*i+2], dtype[i] as for msz_plan_create.
+ *   msz_batch_fix: orig_dev[i], decomp_dev[i], xi[i] per field; results[i]
+ *   receives field i's result (device arrays owned by the batch, valid until
+ *   the next msz_batch_fix or msz_batch_destroy). Returns MSZ_OK when every
+ *   field succeeded, else the first failing field's status. */
+typedef struct msz_batch_s* msz_batch;
+int64_t msz_batch_bytes(int n, const int* ndim, const int64_t* dims, const int* dtype);
+int msz_batch_create(msz_batch* out, int n, const int* ndim, const int64_t* dims, const int* dtype,
+                     const msz_options* opt);
+int msz_batch_fix(msz_batch b, const void* const* orig_dev, const void* const* decomp_dev, const double* xi,
+                  void* stream, msz_result* results);
+int msz_batch_destroy(msz_batch b);
+
 /* Decompression side (Fig. 3 bottom; g_i = fhat_i + delta_i, Sec. 3):
  * writes edit_val[k] into decomp_dev[edit_idx[k]] for k < n_edits. Indices
  * must be < N (checked on the device: out-of-range entries are skipped and

@@ -16,7 +16,7 @@ from dataclasses import dataclass
 
 from . import native
 
-__all__ = ["Plan", "FixResult", "fix", "apply", "directions", "native"]
+__all__ = ["Plan", "Batch", "FixResult", "fix", "apply", "directions", "native"]
 
 
 def _torch():
@@ -58,6 +58,63 @@ class FixResult:
         return int(self.edit_idx.numel())
 
 
+def _result(torch, r, shape, dtype, copy):
+    n = 1
+    for s_ in shape:
+        n *= int(s_)
+    ok = r.status == 0
+    ne = int(r.n_edits) if ok else 0
+    idx = _view(torch, r.edit_idx, ne, torch.int32)
+    val = _view(torch, r.edit_val, ne, dtype)
+    lmax = _view(torch, r.label_max, n if ok else 0, torch.int32)
+    lmin = _view(torch, r.label_min, n if ok else 0, torch.int32)
+    if copy:
+        idx, val, lmax, lmin = idx.long(), val.clone(), lmax.clone(), lmin.clone()
+    if ok:
+        lmax = lmax.view(tuple(shape))
+        lmin = lmin.view(tuple(shape))
+    kms = {k: float(v) for k, v in zip(native.KERNEL_KINDS, r.kernel_ms)}
+    return FixResult(idx, val, lmax, lmin, r.counts.as_dict(), int(r.status), float(r.device_ms),
+                     int(r.launches), kms)
+
+
+class Batch:
+    """Many fields of uneven shapes and mixed float32 / float64, corrected
+    together (msz_batch_create / msz_batch_fix); each result equals msz_fix
+    on that field alone."""
+
+    def __init__(self, shapes, dtypes, max_rounds: int = 0, use_tma: bool = True):
+        self.shapes = [tuple(int(v) for v in s_) for s_ in shapes]
+        self.dtypes = list(dtypes)
+        flags = 0 if use_tma else native.MSZ_OPT_NO_TMA
+        self._b = native.msz_batch_create(self.shapes, self.dtypes, max_rounds, flags)
+
+    def fix(self, fs, fhats, xis, copy: bool = True):
+        torch = _torch()
+        if not (len(fs) == len(fhats) == len(xis) == len(self.shapes)):
+            raise ValueError("one f, fhat and xi per field")
+        fs = [f.contiguous() for f in fs]
+        fhats = [h.contiguous() for h in fhats]
+        for f, h, shp, dt in zip(fs, fhats, self.shapes, self.dtypes):
+            if tuple(f.shape) != shp or tuple(h.shape) != shp or f.dtype != dt or h.dtype != dt or not f.is_cuda:
+                raise ValueError("fields must match the batch's shapes and dtypes (CUDA tensors)")
+        stream = torch.cuda.current_stream().cuda_stream
+        st, res = native.msz_batch_fix(self._b, [f.data_ptr() for f in fs], [h.data_ptr() for h in fhats], xis,
+                                       stream)
+        return st, [_result(torch, r, shp, dt, copy) for r, shp, dt in zip(res, self.shapes, self.dtypes)]
+
+    def close(self):
+        if self._b:
+            native.msz_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Plan:
     """Device state for fields of one shape and dtype (msz_plan_create)."""
 
@@ -79,20 +136,7 @@ class Plan:
         r = native.msz_fix(self._p, f.data_ptr(), fhat.data_ptr(), xi, stream)
         if check:
             native.check(r.status, "msz_fix")
-        n = f.numel()
-        ne = int(r.n_edits) if r.status == 0 else 0
-        idx = _view(torch, r.edit_idx, ne, torch.int32)
-        val = _view(torch, r.edit_val, ne, f.dtype)
-        lmax = _view(torch, r.label_max, n if r.status == 0 else 0, torch.int32)
-        lmin = _view(torch, r.label_min, n if r.status == 0 else 0, torch.int32)
-        if copy:
-            idx, val, lmax, lmin = idx.long(), val.clone(), lmax.clone(), lmin.clone()
-        if r.status == 0:
-            lmax = lmax.view(self.shape)
-            lmin = lmin.view(self.shape)
-        kms = {k: float(v) for k, v in zip(native.KERNEL_KINDS, r.kernel_ms)}
-        return FixResult(idx, val, lmax, lmin, r.counts.as_dict(), int(r.status), float(r.device_ms),
-                         int(r.launches), kms)
+        return _result(torch, r, self.shape, f.dtype, copy)
 
     def close(self):
         if self._p:

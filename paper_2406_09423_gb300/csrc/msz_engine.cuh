@@ -1,0 +1,295 @@
+// Multi-field engine of the MSz correction loop: per-field state machine,
+// work-unit kernels and the host-side group/engine machinery. One engine runs
+// one field (msz_fix, msz_fix_noalloc) or many of uneven sizes and mixed
+// float32 / float64 (msz_batch_*, msz_server_*) through the same kernels.
+//
+// Every kernel walks "units" (vertex chunks, sweep tiles, label tiles, list
+// slices) of all fields of a (dtype, dimension) group; a unit finds its field
+// through prefix sums, checks that field's state and skips it when the field
+// has nothing to do in this kernel (per-field convergence mask). The unit that
+// completes a field's work in a kernel advances that field's state machine.
+// The host launches a fixed sequence of kernels per step (captured once in a
+// CUDA graph) and reads the fields' states once per chunk of steps.
+//
+// Paper references (Li et al., MSz): Sec. 3 (PL field, critical points,
+// integral lines, labels), Sec. 4.1 (false critical points, Eqs. 1-5),
+// Sec. 4.2 (troublemaker, Eq. 6), Sec. 5 (parallel C-loop / R-loop, lock-free
+// lists, deterministic conflict resolution), Sec. 5.3 (edit list).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <stdint.h>
+
+#include "msz.h"
+#include "msz_device.cuh"
+#include "msz_sweep.cuh"
+
+namespace msz {
+
+enum : uint32_t { PH_INIT = 0, PH_FLABELS = 1, PH_C = 2, PH_R = 3, PH_DONE = 4, PH_ERR = 5 };
+enum : uint32_t { ACT_NONE = 0, ACT_MARK_C = 1, ACT_LABELS = 2, ACT_APPLY_R = 3 };
+enum : uint32_t { L_INIT = 0, L_JUMP = 1, L_DONE = 2 };
+enum : uint32_t { E_NONFINITE = 1, E_ARG = 2, E_BOUND = 4, E_TIMEOUT = 8 };
+
+// Work-unit kinds.
+enum { K_DENSE = 0, K_SWEEP = 1, K_LABEL = 2, K_SPARSE = 3, K_EMIT = 4, NKIND = 5 };
+constexpr int kDenseChunk = 8192;  // vertices per dense unit
+constexpr int kEmitItems = 16;
+constexpr int kEmitTile = kThreads * kEmitItems;  // vertices per emission unit
+
+// Per-field device state (one contiguous array per engine).
+struct DevState {
+  uint32_t phase, action, T, lstate, ljob, units_done, err_bits;
+  int32_t status;
+  uint32_t counts[4];
+  uint32_t ncase, ntouch;
+  uint32_t acc_changed;
+  uint32_t acc_ap[2];  // apply: decreases, freezes
+  uint32_t acc_r[4];   // rcheck: wrong max, wrong min, asc troublemakers, desc troublemakers
+  uint32_t jump_rounds, emitted;
+  uint64_t rounds, max_rounds, n_edits;
+  uint64_t ticks;  // advanced by every state transition (stall detection)
+  msz_counts cnt;
+};
+
+// Per-field descriptor (device array per group).
+template <class T>
+struct Field {
+  const T* f;
+  const T* fhat;
+  T* g;
+  uint8_t* fdir;
+  uint8_t* gdir;
+  uint8_t* flags;
+  int32_t* Mf;
+  int32_t* mf;
+  int32_t* Pup;
+  int32_t* Pdn;
+  uint32_t* cases;
+  uint32_t* touched;
+  uint32_t* tile_cnt;
+  uint32_t* edit_idx;
+  T* edit_val;
+  DevState* st;
+  T xi;
+  Geom G;
+  SweepTiling TL;
+  int units[NKIND];
+};
+
+// Kernel argument: one (dtype, dimension) group of fields.
+template <class T>
+struct GroupArgs {
+  const Field<T>* fields;
+  const int* prefix;        // [NKIND][nf + 1]
+  const CUtensorMap* maps;  // [2 * nf]: g (halo box, NaN fill), f's direction bytes
+  int nf;
+  int total[NKIND];
+};
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t vload(const uint32_t* p) { return *(volatile const uint32_t*)p; }
+
+// Field owning global unit u of a kind: pre[i] <= u < pre[i + 1].
+__device__ __forceinline__ int field_of_unit(const int* pre, int nf, int u) {
+  int lo = 0, hi = nf;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(pre + mid) <= u) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Completion of one unit of a field by the whole block: true in the block
+// that completes the field's last unit (all other units' writes visible).
+__device__ __forceinline__ bool unit_done(DevState* st, int units) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&st->units_done, 1u) == (uint32_t)(units - 1);
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last;
+}
+
+template <int NW>
+__device__ __forceinline__ void block_add(uint32_t (&v)[NW], uint32_t* dst) {
+  __shared__ uint32_t s[NW];
+  __syncthreads();
+  if (threadIdx.x < NW) s[threadIdx.x] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NW; ++k) {
+    uint32_t x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s[k], x);
+  }
+  __syncthreads();
+  if (threadIdx.x < NW && s[threadIdx.x]) atomicAdd(&dst[threadIdx.x], s[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// State transitions (run by one thread of the block completing the field)
+// ---------------------------------------------------------------------------
+__device__ void ctrl_after_init(DevState* st) {
+  const uint32_t e = vload(&st->err_bits);
+  if (e) {
+    st->phase = PH_ERR;
+    st->status = (e & E_NONFINITE) ? MSZ_ERR_NONFINITE : (e & E_ARG) ? MSZ_ERR_ARG : MSZ_ERR_BOUND;
+  } else {
+    st->phase = PH_FLABELS;
+    st->action = ACT_LABELS;
+    st->lstate = L_INIT;
+    st->ljob = 0;
+  }
+  st->ticks++;
+}
+
+// C-loop control after a sweep (Sec. 4.1): the next sub-loop with cases, the
+// end of a pass after FNmin, or the R-loop when a whole pass is clean.
+__device__ void ctrl_after_sweep(DevState* st) {
+  uint32_t c[4];
+  for (int t = 0; t < 4; ++t) c[t] = vload(&st->counts[t]);
+  if (vload(&st->err_bits) & E_TIMEOUT) {
+    st->phase = PH_ERR;
+    st->status = MSZ_ERR_TIMEOUT;
+    st->ticks++;
+    return;
+  }
+  st->cnt.sweeps++;
+  uint32_t T_ = st->T;
+  for (;;) {
+    if (c[T_]) { st->action = ACT_MARK_C; break; }
+    if (T_ < 3) { ++T_; continue; }
+    st->cnt.c_passes++;
+    if ((c[0] | c[1] | c[2] | c[3]) == 0) {
+      st->phase = PH_R;
+      st->action = ACT_LABELS;
+      st->lstate = L_INIT;
+      st->ljob = 1;
+      break;
+    }
+    T_ = 0;
+  }
+  st->T = T_;
+  st->ticks++;
+}
+
+__device__ void ctrl_after_jump(DevState* st) {
+  const uint32_t c = vload(&st->acc_changed);
+  st->acc_changed = 0;
+  st->jump_rounds++;
+  st->ticks++;
+  if (c == 0) {
+    if (st->ljob == 0) {
+      st->phase = PH_C;
+      st->action = ACT_NONE;
+      st->T = 0;
+    } else {
+      st->lstate = L_DONE;
+    }
+  } else if (st->jump_rounds > 64) {
+    st->phase = PH_ERR;
+    st->status = MSZ_ERR_TIMEOUT;
+  }
+}
+
+__device__ void ctrl_after_rcheck(DevState* st) {
+  const uint32_t wM = vload(&st->acc_r[0]), wm = vload(&st->acc_r[1]);
+  const uint32_t ta = vload(&st->acc_r[2]), td = vload(&st->acc_r[3]);
+  st->cnt.label_evals++;
+  st->cnt.mismatch[0] += wM;
+  st->cnt.mismatch[1] += wm;
+  st->acc_r[0] = st->acc_r[1] = 0;
+  st->lstate = L_INIT;
+  st->ticks++;
+  if (wM + wm == 0) {
+    st->phase = PH_DONE;
+    st->action = ACT_NONE;
+  } else if (ta + td == 0) {
+    st->phase = PH_ERR;  // cannot happen once the extremum sets agree
+    st->status = MSZ_ERR_NOCONVERGE;
+  } else {
+    st->action = ACT_APPLY_R;
+  }
+}
+
+__device__ void ctrl_after_apply(DevState* st, uint32_t act) {
+  st->cnt.dec_edits += vload(&st->acc_ap[0]);
+  st->cnt.freezes += vload(&st->acc_ap[1]);
+  st->ticks++;
+  if (act == ACT_MARK_C) {
+    const uint32_t t = st->T;
+    st->cnt.c_rounds[t]++;
+    st->cnt.c_cases[t] += st->counts[t];
+  } else {
+    st->cnt.r_rounds++;
+    st->cnt.r_cases[0] += st->acc_r[2];
+    st->cnt.r_cases[1] += st->acc_r[3];
+    st->phase = PH_C;
+    st->T = 0;
+  }
+  st->rounds++;
+  if (st->rounds > st->max_rounds) {
+    st->phase = PH_ERR;
+    st->status = MSZ_ERR_NOCONVERGE;
+  }
+  st->action = ACT_NONE;
+  st->ncase = st->ntouch = 0;
+  st->counts[0] = st->counts[1] = st->counts[2] = st->counts[3] = 0;
+  st->acc_ap[0] = st->acc_ap[1] = 0;
+  st->acc_r[2] = st->acc_r[3] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Edit requests (Sec. 5.1 deterministic mode): idempotent flags collected
+// from one snapshot of g, applied afterwards; a freeze overrides a decrease.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void mark(const Field<T>& F, int u, uint8_t bit) {
+  uint32_t* w = reinterpret_cast<uint32_t*>(F.flags) + (u >> 2);
+  const int sh = (u & 3) * 8;
+  const uint32_t old = atomicOr(w, (uint32_t)bit << sh);
+  if (((old >> sh) & (FL_DEC | FL_FREEZE)) == 0) {
+    const uint32_t k = atomicAdd(&F.st->ntouch, 1u);
+    F.touched[k] = (uint32_t)u;
+  }
+}
+
+// A false case anchored at a asks for a decreasing edit of t. If t is frozen
+// or already at its lower bound, the non-frozen part of a's closed 1-ring is
+// frozen instead (termination guard; the paper argues convergence in the
+// reals, Sec. 4.3).
+template <class T, int ND>
+__device__ void request(const Field<T>& F, int a, int t) {
+  const uint8_t ft = F.flags[t];
+  if (!(ft & FL_FROZEN) && F.g[t] > lower_bound_of(F.f[t], F.xi)) {
+    mark(F, t, FL_DEC);
+    return;
+  }
+  int x, y, z;
+  coords(F.G, a, x, y, z);
+  if (!(F.flags[a] & FL_FROZEN)) mark(F, a, FL_FREEZE);
+  constexpr int NPOS = Slots<ND>::NPOS;
+#pragma unroll
+  for (int s = 0; s < 2 * NPOS; ++s) {
+    const int sg = (s < NPOS) ? 1 : -1;
+    const int m = (int)((Slots<ND>::MASKS >> (4 * (s < NPOS ? s : s - NPOS))) & 7u);
+    const int dx = sg * (m & 1), dy = sg * ((m >> 1) & 1), dz = sg * ((m >> 2) & 1);
+    const int X = x + dx, Y = y + dy, Z = z + dz;
+    bool in = X >= 0 && X < F.G.nx && Y >= 0 && Y < F.G.ny;
+    if (ND == 3) in = in && Z >= 0 && Z < F.G.nz;
+    if (in) {
+      const int u = a + dx + dy * F.G.nx + dz * F.G.nxny;
+      if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE);
+    }
+  }
+}
+
+}  // namespace msz

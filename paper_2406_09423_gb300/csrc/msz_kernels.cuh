@@ -1,0 +1,727 @@
+// Work-unit kernels of the MSz correction loop (see msz_engine.cuh).
+#pragma once
+
+#include "msz_engine.cuh"
+
+namespace msz {
+
+#define MSZ_UNIT_LOOP(A, KIND)                                                  \
+  for (int u_ = blockIdx.x; u_ < (A).total[KIND]; u_ += gridDim.x)
+
+// ---------------------------------------------------------------------------
+// Init (Sec. 3 constraint): validate f and fhat (finite, |fhat - f| <= xi via
+// the tightest representable bounds), g = fhat, clear flags.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_init(GroupArgs<T> A) {
+  const int* pre = A.prefix + K_DENSE * (A.nf + 1);
+  MSZ_UNIT_LOOP(A, K_DENSE) {
+    const int i = field_of_unit(pre, A.nf, u_);
+    const Field<T>& F = A.fields[i];
+    DevState* st = F.st;
+    if (st->phase != PH_INIT) continue;
+    const int v0 = (u_ - pre[i]) * kDenseChunk;
+    const int v1 = min(F.G.n, v0 + kDenseChunk);
+    uint32_t err = 0;
+    for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+      const T fv = F.f[v], hv = F.fhat[v];
+      if (!finite(fv) || !finite(hv)) {
+        err |= E_NONFINITE;
+      } else {
+        const T lb = lower_bound_of(fv, F.xi);
+        const T ub = upper_bound_of(fv, F.xi);
+        if (!finite(lb)) err |= E_ARG;
+        else if (hv < lb || hv > ub) err |= E_BOUND;
+      }
+      F.g[v] = hv;
+      F.flags[v] = 0;
+    }
+    if (err) atomicOr(&st->err_bits, err);
+    if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
+      ctrl_after_init(st);
+      st->units_done = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// C-loop sweep (msz_sweep.cuh): extremum flags of g per vertex, false critical
+// points of every type counted with warp ballots and appended to the field's
+// case list. Units are tiles (x-y tile by a chunk of planes). With kTMA a
+// producer warp streams the planes of the block's active tiles through a
+// ring of TMA stages (full/empty mbarriers, bounded waits); otherwise the
+// consumers fill one stage with plain loads.
+// ---------------------------------------------------------------------------
+template <class T, int ND, bool kTMA>
+__global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND>::NT)
+    k_csweep(GroupArgs<T> A) {
+  using SG = SweepGeom<T, ND>;
+  constexpr int RPT = SG::RPT;
+  constexpr int NCW = SG::NT / 32;  // consumer warps
+  using PV = PlaneVals<T, RPT>;
+  static_assert((SG::STAGES & (SG::STAGES - 1)) == 0, "power-of-two stages");
+  constexpr int SM1 = SG::STAGES - 1;
+  __shared__ alignas(128) unsigned char smem[(kTMA ? SG::STAGES : 1) * SG::STAGE_BYTES];
+  __shared__ alignas(8) uint64_t full[SG::STAGES];
+  __shared__ alignas(8) uint64_t empty[SG::STAGES];
+  __shared__ int s_abort;
+  __shared__ unsigned s_tiles;
+  const int* pre = A.prefix + K_SWEEP * (A.nf + 1);
+  const int tid = threadIdx.x;
+  const bool producer = kTMA && tid >= SG::NT;
+  const int tx = tid % SG::TX, w = (tid / SG::TX) % (SG::NT / SG::TX);
+  const int lane = tid & 31;
+
+  // Next active tile of this block at or after global unit u: field index,
+  // tile origin and planes per tile; false when the block's units are done.
+  struct Tile {
+    int u, i, x0, y0, c0, ppt;
+  };
+  auto next_tile = [&](Tile& t, int u) -> bool {
+    for (; u < A.total[K_SWEEP]; u += gridDim.x) {
+      const int i = field_of_unit(pre, A.nf, u);
+      const Field<T>& F = A.fields[i];
+      if (F.st->phase != PH_C) continue;
+      const SweepTiling& TL = F.TL;
+      const int lt = u - pre[i];
+      const int bx = lt % TL.tiles_x;
+      const int r = lt / TL.tiles_x;
+      t.u = u;
+      t.i = i;
+      t.x0 = bx * SG::TX;
+      t.y0 = (r % TL.tiles_y) * SG::TY;
+      t.c0 = (r / TL.tiles_y) * TL.chunk;
+      t.ppt = TL.chunk + 2;
+      return true;
+    }
+    return false;
+  };
+
+  if (tid == 0) {
+    if (kTMA) {
+      for (int s = 0; s < SG::STAGES; ++s) {
+        mbar_init(&full[s], 1);
+        mbar_init(&empty[s], NCW);
+      }
+      mbar_fence_init();
+    }
+    s_abort = 0;
+    s_tiles = 0;
+  }
+  __syncthreads();
+
+  if (producer) {
+    if (lane == 0) {
+      int q = 0;
+      Tile t;
+      bool more = next_tile(t, blockIdx.x);
+      while (more && !*(volatile int*)&s_abort) {
+        const CUtensorMap* gm = A.maps + 2 * t.i;
+        for (int p = 0; p < t.ppt; ++p, ++q) {
+          const int s = q & SM1;
+          if (q >= SG::STAGES &&
+              !mbar_wait_or_abort(&empty[s], (uint32_t)(((q - SG::STAGES) / SG::STAGES) & 1), &s_abort)) {
+            atomicExch(&s_abort, 1);
+            break;
+          }
+          const int pc = t.c0 - 1 + p;
+          unsigned char* sp = smem + s * SG::STAGE_BYTES;
+          mbar_expect_tx(&full[s], (uint32_t)(SG::STAGE_ELEMS * sizeof(T) + SG::TX * SG::TY));
+          if (ND == 3) {
+            tma_load_3d(sp, gm, &full[s], t.x0 - SG::PADX, t.y0 - 1, pc);
+            tma_load_3d(sp + SG::G_BYTES, gm + 1, &full[s], t.x0, t.y0, pc);
+          } else {
+            tma_load_2d(sp, gm, &full[s], t.x0 - SG::PADX, pc);
+            tma_load_2d(sp + SG::G_BYTES, gm + 1, &full[s], t.x0, pc);
+          }
+        }
+        more = next_tile(t, t.u + gridDim.x);
+      }
+      if (*(volatile int*)&s_abort) {
+        // wait (bounded) for the copies still in flight before leaving
+        const int first = (q > SG::STAGES) ? q - SG::STAGES : 0;
+        for (int k = first; k < q; ++k) mbar_wait(&full[k & SM1], (uint32_t)((k / SG::STAGES) & 1));
+      }
+    }
+  } else {
+    int q = 0;
+    Tile t;
+    bool more = next_tile(t, blockIdx.x);
+    bool ok = true;
+    while (more && ok) {
+      const Field<T>& F = A.fields[t.i];
+      DevState* st = F.st;
+      const Geom G = F.G;
+      const int chunk = t.ppt - 2;
+      const int axis_n = (ND == 3) ? G.nz : G.ny;
+      uint32_t vmask = 0;  // this thread's vertices inside the grid in x and y
+      {
+        const int x = t.x0 + tx;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+          const int y = (ND == 3) ? t.y0 + RPT * w + k : 0;
+          if (x < G.nx && y < G.ny) vmask |= 0x11u << (8 * k);
+        }
+      }
+      uint32_t cnt[4] = {0, 0, 0, 0};
+
+      // One plane p of the tile: stage it, derive its quantities into dst
+      // (role B), then classify the vertices of plane A (Cv previous).
+      auto step = [&](int qq, int p, PV& dst, uint16_t& fd_dst, const PV& Cv, const PV& Av, uint16_t fdA) -> bool {
+        const int pcoord = t.c0 - 1 + p;  // plane coordinate (z in 3D, y in 2D)
+        unsigned char* sp = smem + (kTMA ? (qq & SM1) * SG::STAGE_BYTES : 0);
+        const T* stage = reinterpret_cast<const T*>(sp);
+        if (kTMA) {
+          const bool got = mbar_wait_or_abort(&full[qq & SM1], (uint32_t)((qq / SG::STAGES) & 1), &s_abort);
+          if (!__all_sync(kFull, got)) {
+            if (lane == 0) atomicExch(&s_abort, 1);
+            return false;
+          }
+          dst = plane_vals<T, ND>(stage, tx, w);
+          if (ND == 3)
+            fd_dst = (uint16_t)(sp[SG::G_BYTES + (2 * w) * SG::TX + tx] |
+                                (sp[SG::G_BYTES + (2 * w + 1) * SG::TX + tx] << 8));
+          else
+            fd_dst = sp[SG::G_BYTES + tx];
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[qq & SM1]);
+        } else {
+          __syncthreads();
+          T* wst = reinterpret_cast<T*>(sp);
+          for (int k = tid; k < SG::STAGE_ELEMS; k += SG::NT) {
+            const int col = k % SG::BX, row = k / SG::BX;
+            const int gx = t.x0 - SG::PADX + col;
+            const int gy = (ND == 3) ? t.y0 - 1 + row : pcoord;
+            const int gz = (ND == 3) ? pcoord : 0;
+            const bool in = gx >= 0 && gx < G.nx && gy >= 0 && gy < G.ny && gz >= 0 && gz < G.nz;
+            wst[k] = in ? F.g[gx + G.nx * (gy + G.ny * gz)] : qnan<T>();
+          }
+          __syncthreads();
+          dst = plane_vals<T, ND>(stage, tx, w);
+          uint16_t fd = 0;
+#pragma unroll
+          for (int k = 0; k < RPT; ++k) {
+            const int vx = t.x0 + tx, vy = (ND == 3) ? t.y0 + RPT * w + k : pcoord, vz = (ND == 3) ? pcoord : 0;
+            if (vx < G.nx && vy >= 0 && vy < G.ny && vz >= 0 && vz < G.nz)
+              fd |= (uint16_t)(F.fdir[vx + G.nx * (vy + G.ny * vz)] << (8 * k));
+          }
+          fd_dst = fd;
+        }
+        if (p >= 2) {
+          // g's extremum flags and f's, packed at bits 8k (max) and 8k+4
+          // (min) for vertex k; a vertex is a case when they differ.
+          uint32_t gb = 0;
+#pragma unroll
+          for (int k = 0; k < RPT; ++k)
+            gb |= ((uint32_t)is_max_at<T, RPT>(Cv, Av, dst, k) << (8 * k)) |
+                  ((uint32_t)is_min_at<T, RPT>(Cv, Av, dst, k) << (8 * k + 4));
+          const uint32_t fa = fdA;
+          const uint32_t fb = fa & (fa >> 1) & (fa >> 2) & (fa >> 3) & 0x1111u;  // nibble == 15
+          uint32_t diff = (gb ^ fb) & vmask;
+          if (!(p - 2 < chunk && pcoord - 1 < axis_n)) diff = 0;
+          if (__any_sync(kFull, diff != 0)) {
+            const int x = t.x0 + tx;
+            const int z = (ND == 3) ? pcoord - 1 : 0;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+              const int y = (ND == 3) ? t.y0 + RPT * w + k : pcoord - 1;
+              const uint32_t gk = gb >> (8 * k), fk = fb >> (8 * k), dk = diff >> (8 * k);
+              unsigned bits = 0;
+              if (dk & 0x11u) {
+                const unsigned gmx = gk & 1u, gmn = (gk >> 4) & 1u, fmx = fk & 1u, fmn = (fk >> 4) & 1u;
+                bits = (gmx & ~fmx) | ((gmn & ~fmn) << 1) | ((fmx & ~gmx) << 2) | ((fmn & ~gmn) << 3);
+              }
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const uint32_t b = __ballot_sync(kFull, (bits >> c) & 1u);
+                if (lane == 0) cnt[c] += __popc(b);
+              }
+              const uint32_t mask = __ballot_sync(kFull, bits != 0);
+              if (mask) {
+                const int leader = __ffs(mask) - 1;
+                uint32_t b0 = 0;
+                if (lane == leader) b0 = atomicAdd(&st->ncase, (uint32_t)__popc(mask));
+                b0 = __shfl_sync(kFull, b0, leader);
+                if (bits) F.cases[b0 + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)(x + G.nx * (y + G.ny * z));
+              }
+            }
+          }
+        }
+        return true;
+      };
+
+      PV P0{}, P1{}, P2{};
+      uint16_t f0 = 0, f1 = 0, f2 = 0;
+      for (int p = 0; p < t.ppt && ok; p += 3, q += 3) {  // planes rotate through P0, P1, P2
+        ok = step(q, p, P0, f0, P1, P2, f2) && step(q + 1, p + 1, P1, f1, P2, P0, f0) &&
+             step(q + 2, p + 2, P2, f2, P0, P1, f1);
+      }
+      if (!ok) break;
+      // Tile done by this warp: flush its counts; the last consumer warp to
+      // finish the tile counts the unit for the field.
+      if (lane == 0) {
+        for (int c = 0; c < 4; ++c)
+          if (cnt[c]) atomicAdd(&st->counts[c], cnt[c]);
+        __threadfence();
+        const unsigned old = atomicAdd(&s_tiles, 1u);
+        if ((old + 1) % NCW == 0) {
+          __threadfence();
+          if (atomicAdd(&st->units_done, 1u) == (uint32_t)(F.units[K_SWEEP] - 1)) {
+            __threadfence();
+            ctrl_after_sweep(st);
+            st->units_done = 0;
+          }
+        }
+      }
+      __syncwarp();
+      more = next_tile(t, t.u + gridDim.x);
+    }
+    if (!ok && lane == 0) {
+      // gave up on a bounded wait: the tile is not counted, so the field's
+      // state machine stalls and the host reports MSZ_ERR_TIMEOUT
+      atomicOr(&A.fields[t.i].st->err_bits, E_TIMEOUT);
+    }
+  }
+}
+
+// C-loop requests for the field's current type (Eqs. 2-5): FPmax and FNmin
+// edit the false vertex itself; FPmin and FNmax edit its neighbour that is
+// maximal in g, which is its steepest ascent since it is not a maximum of
+// g's ring. Units are slices of the case list.
+template <class T, int ND>
+__global__ void __launch_bounds__(kThreads) k_mark_c(GroupArgs<T> A) {
+  const int* pre = A.prefix + K_SPARSE * (A.nf + 1);
+  MSZ_UNIT_LOOP(A, K_SPARSE) {
+    const int i = field_of_unit(pre, A.nf, u_);
+    const Field<T>& F = A.fields[i];
+    DevState* st = F.st;
+    if (st->action != ACT_MARK_C) continue;
+    const uint32_t type = st->T, nc = st->ncase;
+    const int S = F.units[K_SPARSE], k = u_ - pre[i];
+    const uint32_t b = (uint32_t)(((uint64_t)nc * k) / S), e = (uint32_t)(((uint64_t)nc * (k + 1)) / S);
+    for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) {
+      const int v = (int)F.cases[j];
+      int x, y, z;
+      coords(F.G, v, x, y, z);
+      const uint8_t d = direction_of<T, ND>(F.g, F.G, v, x, y, z);
+      if (!((case_bits(d, F.fdir[v]) >> type) & 1u)) continue;
+      const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny);
+      request<T, ND>(F, v, t);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Labels, first level (Sec. 5.2 path compression): a block loads a tile plus
+// a one-vertex halo into shared memory, computes every tile vertex's
+// steepest ascending / descending neighbour (candidates in ascending index
+// order: ties go to the larger index for the maximum and to the smaller for
+// the minimum; NaN halo cells never win), and follows the pointers inside the
+// tile by pointer doubling. Each vertex leaves with a pointer to the first
+// vertex outside the tile on its integral line, or to the extremum it reaches
+// inside. Job 0: f (fdir, Mf, mf). Job 1: g (gdir, Pup, Pdn).
+// ---------------------------------------------------------------------------
+template <int ND>
+struct LabelGeom {
+  static constexpr int TX = (ND == 3) ? 32 : 64;
+  static constexpr int TY = (ND == 3) ? 8 : 32;
+  static constexpr int TZ = (ND == 3) ? 8 : 1;
+  static constexpr int TV = TX * TY * TZ;  // 2048 vertices
+  static constexpr int SX = TX + 2, SY = TY + 2, SZ = (ND == 3) ? TZ + 2 : 1;
+  static constexpr int HALO = SX * SY * SZ;  // < 65536: pointers fit in 16 bits
+  static constexpr int PER_THREAD = TV / kThreads;
+  static constexpr int ROWS = SY * SZ;
+};
+
+template <class T, int ND>
+size_t label_smem_bytes() {
+  using LG = LabelGeom<ND>;
+  return ((LG::HALO * sizeof(T) + 15) / 16) * 16 + 2 * ((LG::HALO + 7) / 8) * 8 * sizeof(uint16_t);
+}
+
+template <class T, int ND>
+__global__ void __launch_bounds__(kThreads) k_label_tile(GroupArgs<T> A) {
+  using LG = LabelGeom<ND>;
+  extern __shared__ __align__(16) unsigned char lsm[];
+  T* val = reinterpret_cast<T*>(lsm);
+  // Pointers in halo coordinates: halo cells and extrema point to themselves
+  // (terminal); interior cells to their steepest neighbour.
+  uint16_t* Pu = reinterpret_cast<uint16_t*>(lsm + ((LG::HALO * sizeof(T) + 15) / 16) * 16);
+  uint16_t* Pd = Pu + ((LG::HALO + 7) / 8) * 8;
+  const int* pre = A.prefix + K_LABEL * (A.nf + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int HS = LG::SX, HSS = LG::SX * LG::SY;
+  constexpr int NC = (ND == 3) ? 15 : 7;
+  MSZ_UNIT_LOOP(A, K_LABEL) {
+    const int fi = field_of_unit(pre, A.nf, u_);
+    const Field<T>& F = A.fields[fi];
+    DevState* st = F.st;
+    if (st->action != ACT_LABELS || st->lstate != L_INIT) continue;
+    const bool job = st->ljob != 0;
+    const T* src = job ? F.g : F.f;
+    uint8_t* dir = job ? F.gdir : F.fdir;
+    int32_t* OA = job ? F.Pup : F.Mf;
+    int32_t* OB = job ? F.Pdn : F.mf;
+    const Geom G = F.G;
+    const int tiles_x = (G.nx + LG::TX - 1) / LG::TX;
+    const int tiles_y = (G.ny + LG::TY - 1) / LG::TY;
+    const int tile = u_ - pre[fi];
+    const int x0 = (tile % tiles_x) * LG::TX;
+    const int y0 = ((tile / tiles_x) % tiles_y) * LG::TY;
+    const int z0 = (tile / (tiles_x * tiles_y)) * LG::TZ;
+    __syncthreads();
+    for (int row = warp; row < LG::ROWS; row += kThreads / 32) {
+      const int hy = row % LG::SY, hz = row / LG::SY;
+      const int gy = y0 - 1 + hy, gz = (ND == 3) ? z0 - 1 + hz : 0;
+      const bool rin = gy >= 0 && gy < G.ny && gz >= 0 && gz < G.nz;
+      const size_t rbase = rin ? (size_t)G.nx * ((size_t)gy + (size_t)G.ny * gz) : 0;
+      for (int hx = lane; hx < LG::SX; hx += 32) {
+        const int gx = x0 - 1 + hx;
+        const int h = hx + HS * row;
+        val[h] = (rin && gx >= 0 && gx < G.nx) ? src[rbase + gx] : qnan<T>();
+        Pu[h] = (uint16_t)h;
+        Pd[h] = (uint16_t)h;
+      }
+    }
+    __syncthreads();
+    uint8_t dbyte[LG::PER_THREAD];
+#pragma unroll
+    for (int k = 0; k < LG::PER_THREAD; ++k) {
+      const int i = threadIdx.x + k * kThreads;
+      const int lx = i % LG::TX, ly = (i / LG::TX) % LG::TY, lz = i / (LG::TX * LG::TY);
+      const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
+      T hv = -INFINITY, lv = INFINITY;
+      int hs = kSelf, ls = kSelf, ho = 0, lo = 0;
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        int o, slot;
+        if (ND == 3) {
+          constexpr int tab[15][2] = {{-1 - HS - HSS, 13}, {-HS - HSS, 12}, {-1 - HSS, 11}, {-HSS, 9},
+                                      {-1 - HS, 10},       {-HS, 8},        {-1, 7},        {0, kSelf},
+                                      {1, 0},              {HS, 1},         {1 + HS, 3},    {HSS, 2},
+                                      {1 + HSS, 4},        {HS + HSS, 5},   {1 + HS + HSS, 6}};
+          o = tab[j][0];
+          slot = tab[j][1];
+        } else {
+          constexpr int tab[7][2] = {{-1 - HS, 5}, {-HS, 4}, {-1, 3}, {0, kSelf}, {1, 0}, {HS, 1}, {1 + HS, 2}};
+          o = tab[j][0];
+          slot = tab[j][1];
+        }
+        const T uval = val[c + o];
+        if (uval >= hv) { hv = uval; hs = slot; ho = o; }
+        if (uval < lv) { lv = uval; ls = slot; lo = o; }
+      }
+      dbyte[k] = (uint8_t)(hs | (ls << 4));
+      if (val[c] == val[c]) {  // cells outside the grid are NaN and keep self pointers
+        Pu[c] = (uint16_t)(c + ho);
+        Pd[c] = (uint16_t)(c + lo);
+      }
+    }
+    __syncthreads();
+    for (int round = 0; round < 2 * LG::TV; ++round) {
+      int changed = 0;
+#pragma unroll
+      for (int k = 0; k < LG::PER_THREAD; ++k) {
+        const int i = threadIdx.x + k * kThreads;
+        const int lx = i % LG::TX, ly = (i / LG::TX) % LG::TY, lz = i / (LG::TX * LG::TY);
+        const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
+        const int a = Pu[c], a2 = Pu[a];
+        if (a2 != a) { Pu[c] = (uint16_t)a2; changed = 1; }
+        const int b = Pd[c], b2 = Pd[b];
+        if (b2 != b) { Pd[c] = (uint16_t)b2; changed = 1; }
+      }
+      if (!__syncthreads_or(changed)) break;
+    }
+#pragma unroll
+    for (int k = 0; k < LG::PER_THREAD; ++k) {
+      const int i = threadIdx.x + k * kThreads;
+      const int lx = i % LG::TX, ly = (i / LG::TX) % LG::TY, lz = i / (LG::TX * LG::TY);
+      const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+      if (x < G.nx && y < G.ny && z < G.nz) {
+        const int v = x + G.nx * (y + G.ny * z);
+        const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
+        auto global_of = [&](int h) -> int {  // terminal halo cell -> global index
+          const int hx = h % LG::SX, hy = (h / LG::SX) % LG::SY, hz = h / HSS;
+          return (x0 - 1 + hx) + G.nx * ((y0 - 1 + hy) + G.ny * ((ND == 3) ? (z0 - 1 + hz) : 0));
+        };
+        dir[v] = dbyte[k];
+        OA[v] = global_of(Pu[c]);
+        OB[v] = global_of(Pd[c]);
+      }
+    }
+    if (unit_done(st, F.units[K_LABEL]) && threadIdx.x == 0) {
+      st->lstate = L_JUMP;
+      st->jump_rounds = 0;
+      st->ticks++;
+      st->units_done = 0;
+    }
+  }
+}
+
+// One pointer-jumping round, in place: P[v] <- P[P[v]]. A round that changes
+// nothing means every pointer is a root (an extremum).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
+  const int* pre = A.prefix + K_DENSE * (A.nf + 1);
+  MSZ_UNIT_LOOP(A, K_DENSE) {
+    const int i = field_of_unit(pre, A.nf, u_);
+    const Field<T>& F = A.fields[i];
+    DevState* st = F.st;
+    if (st->action != ACT_LABELS || st->lstate != L_JUMP) continue;
+    const bool job = st->ljob != 0;
+    int32_t* PA = job ? F.Pup : F.Mf;
+    int32_t* PB = job ? F.Pdn : F.mf;
+    const int v0 = (u_ - pre[i]) * kDenseChunk;
+    const int v1 = min(F.G.n, v0 + kDenseChunk);
+    uint32_t changed[1] = {0};
+    for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+      const int p = PA[v], q = PA[p];
+      if (q != p) { PA[v] = q; ++changed[0]; }
+      const int r = PB[v], s = PB[r];
+      if (s != r) { PB[v] = s; ++changed[0]; }
+    }
+    block_add<1>(changed, &st->acc_changed);
+    if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
+      ctrl_after_jump(st);
+      st->units_done = 0;
+    }
+  }
+}
+
+// R-loop check (Sec. 4.2): count wrong labels; a wrongly labelled vertex whose
+// steepest neighbour in g differs from f's is a troublemaker. Wrong max label:
+// decrease its ascending neighbour in g (Eq. 6). Wrong min label: decrease the
+// descending neighbour that f prescribes.
+template <class T, int ND>
+__global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
+  const int* pre = A.prefix + K_DENSE * (A.nf + 1);
+  MSZ_UNIT_LOOP(A, K_DENSE) {
+    const int i = field_of_unit(pre, A.nf, u_);
+    const Field<T>& F = A.fields[i];
+    DevState* st = F.st;
+    if (st->action != ACT_LABELS || st->lstate != L_DONE || st->ljob != 1) continue;
+    const int v0 = (u_ - pre[i]) * kDenseChunk;
+    const int v1 = min(F.G.n, v0 + kDenseChunk);
+    uint32_t acc[4] = {0, 0, 0, 0};
+    for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+      const bool wM = F.Pup[v] != F.Mf[v];
+      const bool wm = F.Pdn[v] != F.mf[v];
+      acc[0] += wM;
+      acc[1] += wm;
+      if (wM || wm) {
+        const uint8_t d = F.gdir[v], fd = F.fdir[v];
+        if (wM && (d & 15) != (fd & 15)) {
+          ++acc[2];
+          request<T, ND>(F, v, v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny));
+        }
+        if (wm && (d >> 4) != (fd >> 4)) {
+          ++acc[3];
+          request<T, ND>(F, v, v + slot_offset(fd >> 4, ND, F.G.nx, F.G.nxny));
+        }
+      }
+    }
+    block_add<4>(acc, st->acc_r);
+    if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
+      ctrl_after_rcheck(st);
+      st->units_done = 0;
+    }
+  }
+}
+
+// Applies a round's requests to the touched vertices only. Units are slices
+// of the touched list.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
+  const int* pre = A.prefix + K_SPARSE * (A.nf + 1);
+  MSZ_UNIT_LOOP(A, K_SPARSE) {
+    const int i = field_of_unit(pre, A.nf, u_);
+    const Field<T>& F = A.fields[i];
+    DevState* st = F.st;
+    const uint32_t act = st->action;
+    if (act != ACT_MARK_C && act != ACT_APPLY_R) continue;
+    const uint32_t nt = st->ntouch;
+    const int S = F.units[K_SPARSE], k = u_ - pre[i];
+    const uint32_t b = (uint32_t)(((uint64_t)nt * k) / S), e = (uint32_t)(((uint64_t)nt * (k + 1)) / S);
+    uint32_t acc[2] = {0, 0};
+    for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) {
+      const int u = (int)F.touched[j];
+      uint8_t bb = F.flags[u];
+      if (bb & FL_FREEZE) {
+        F.g[u] = F.f[u];
+        bb = (uint8_t)((bb & ~(FL_DEC | FL_FREEZE)) | FL_FROZEN | FL_EDITED);
+        ++acc[1];
+      } else if (bb & FL_DEC) {
+        F.g[u] = decrease(F.g[u], lower_bound_of(F.f[u], F.xi));
+        bb = (uint8_t)((bb & ~FL_DEC) | FL_EDITED);
+        ++acc[0];
+      }
+      F.flags[u] = bb;
+    }
+    block_add<2>(acc, st->acc_ap);
+    if (unit_done(st, S) && threadIdx.x == 0) {
+      ctrl_after_apply(st, act);
+      st->units_done = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Edit list (Sec. 5.3): every vertex whose final value differs bitwise from
+// fhat, ascending. Count per tile, scan per field, write.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ bool bits_differ(T a, T b);
+template <>
+__device__ __forceinline__ bool bits_differ<float>(float a, float b) {
+  return __float_as_uint(a) != __float_as_uint(b);
+}
+template <>
+__device__ __forceinline__ bool bits_differ<double>(double a, double b) {
+  return __double_as_longlong(a) != __double_as_longlong(b);
+}
+
+template <class T>
+__device__ __forceinline__ uint32_t emit_mask(const Field<T>& F, int base) {
+  const uint4 wv = *reinterpret_cast<const uint4*>(F.flags + base);
+  const uint32_t ws[4] = {wv.x, wv.y, wv.z, wv.w};
+  uint32_t m = 0;
+#pragma unroll
+  for (int k = 0; k < kEmitItems; ++k) {
+    const uint32_t byte = (ws[k >> 2] >> ((k & 3) * 8)) & 0xffu;
+    if (byte & FL_EDITED) {
+      const int v = base + k;
+      if (v < F.G.n && bits_differ(F.g[v], F.fhat[v])) m |= 1u << k;
+    }
+  }
+  return m;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_emit_count(GroupArgs<T> A) {
+  const int* pre = A.prefix + K_EMIT * (A.nf + 1);
+  __shared__ uint32_t s;
+  MSZ_UNIT_LOOP(A, K_EMIT) {
+    const int i = field_of_unit(pre, A.nf, u_);
+    const Field<T>& F = A.fields[i];
+    if (F.st->phase != PH_DONE || F.st->emitted) continue;
+    const int tile = u_ - pre[i];
+    const int base = tile * kEmitTile + threadIdx.x * kEmitItems;
+    __syncthreads();
+    if (threadIdx.x == 0) s = 0;
+    __syncthreads();
+    uint32_t x = __popc(emit_mask(F, base));
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s, x);
+    __syncthreads();
+    if (threadIdx.x == 0) F.tile_cnt[tile] = s;
+  }
+}
+
+// Exclusive scan of one field's tile counts per block (grid = nf).
+template <class T>
+__global__ void __launch_bounds__(1024) k_emit_scan(GroupArgs<T> A) {
+  const Field<T>& F = A.fields[blockIdx.x];
+  DevState* st = F.st;
+  if (st->phase != PH_DONE || st->emitted) return;
+  const int ntiles = F.units[K_EMIT];
+  __shared__ uint32_t warp_sums[32];
+  __shared__ uint32_t carry_s;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < ntiles; base += 1024) {
+    const int i = base + threadIdx.x;
+    const uint32_t x = (i < ntiles) ? F.tile_cnt[i] : 0u;
+    uint32_t incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t wsum = warp_sums[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, wsum, o);
+        if (lane >= o) wsum += y;
+      }
+      warp_sums[lane] = wsum;
+    }
+    __syncthreads();
+    const uint32_t carry = carry_s;
+    const uint32_t warp_off = wid ? warp_sums[wid - 1] : 0u;
+    if (i < ntiles) F.tile_cnt[i] = carry + warp_off + incl - x;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s = carry + warp_sums[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    st->n_edits = carry_s;
+    st->cnt.edits = carry_s;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_emit_write(GroupArgs<T> A) {
+  const int* pre = A.prefix + K_EMIT * (A.nf + 1);
+  __shared__ uint32_t ws[kThreads / 32];
+  MSZ_UNIT_LOOP(A, K_EMIT) {
+    const int fi = field_of_unit(pre, A.nf, u_);
+    const Field<T>& F = A.fields[fi];
+    DevState* st = F.st;
+    if (st->phase != PH_DONE || st->emitted) continue;
+    const int tile = u_ - pre[fi];
+    const int base = tile * kEmitTile + threadIdx.x * kEmitItems;
+    const uint32_t m = emit_mask(F, base);
+    const uint32_t c = __popc(m);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    __syncthreads();
+    if (lane == 31) ws[wid] = incl;
+    __syncthreads();
+    uint32_t off = F.tile_cnt[tile] + incl - c;
+    for (int wv = 0; wv < wid; ++wv) off += ws[wv];
+    uint32_t mm = m;
+    while (mm) {
+      const int k = __ffs(mm) - 1;
+      mm &= mm - 1;
+      const int v = base + k;
+      F.edit_idx[off] = (uint32_t)v;
+      F.edit_val[off] = F.g[v];
+      ++off;
+    }
+    if (unit_done(st, F.units[K_EMIT]) && threadIdx.x == 0) {
+      st->emitted = 1;
+      st->units_done = 0;
+    }
+  }
+}
+
+// Standalone direction kernel (msz_directions).
+template <class T, int ND>
+__global__ void __launch_bounds__(kThreads) k_directions(const T* __restrict__ g, Geom G, uint8_t* out) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < G.n; v += gridDim.x * blockDim.x) {
+    int x, y, z;
+    coords(G, v, x, y, z);
+    out[v] = direction_of<T, ND>(g, G, v, x, y, z);
+  }
+}
+
+// Decompression-side scatter (msz_apply).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_scatter(T* dst, int n, const uint32_t* idx, const T* val,
+                                                      uint64_t ne, uint32_t* bad) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < ne; k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = idx[k];
+    if (i < (uint32_t)n) dst[i] = val[k];
+    else atomicOr(bad, 1u);
+  }
+}
+
+#undef MSZ_UNIT_LOOP
+
+}  // namespace msz

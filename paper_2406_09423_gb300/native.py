@@ -100,6 +100,14 @@ def lib() -> ctypes.CDLL:
         L.msz_apply.restype = I
         L.msz_directions.argtypes = [P, I, P, I, P, P]
         L.msz_directions.restype = I
+        L.msz_batch_bytes.argtypes = [I, P, P, P]
+        L.msz_batch_bytes.restype = I64
+        L.msz_batch_create.argtypes = [ctypes.POINTER(P), I, P, P, P, P]
+        L.msz_batch_create.restype = I
+        L.msz_batch_fix.argtypes = [P, P, P, P, P, ctypes.POINTER(MszResult)]
+        L.msz_batch_fix.restype = I
+        L.msz_batch_destroy.argtypes = [P]
+        L.msz_batch_destroy.restype = I
         L.msz_fix_noalloc.argtypes = [I, P, I, P, P, D, P, P, P, P, P, ctypes.POINTER(MszResult)]
         L.msz_fix_noalloc.restype = I
         L.msz_strerror.argtypes = [I]
@@ -170,6 +178,49 @@ def msz_fix_host(plan, orig_ptr: int, decomp_ptr: int, xi: float, edit_idx_ptr: 
                        ctypes.c_void_p(label_max_ptr or None), ctypes.c_void_p(label_min_ptr or None),
                        ctypes.c_void_p(stream), ctypes.byref(r))
     return r
+
+
+def _batch_arrays(shapes, dtypes):
+    n = len(shapes)
+    nd = (ctypes.c_int * n)()
+    dims = (ctypes.c_int64 * (3 * n))()
+    dts = (ctypes.c_int * n)()
+    for i, (shp, dt) in enumerate(zip(shapes, dtypes)):
+        k, d = dims_of(shp)
+        nd[i] = k
+        dims[3 * i:3 * i + 3] = list(d)
+        dts[i] = dtype_code(dt)
+    return n, nd, dims, dts
+
+
+def msz_batch_bytes(shapes, dtypes) -> int:
+    n, nd, dims, dts = _batch_arrays(shapes, dtypes)
+    return int(lib().msz_batch_bytes(n, nd, dims, dts))
+
+
+def msz_batch_create(shapes, dtypes, max_rounds: int = 0, flags: int = 0):
+    n, nd, dims, dts = _batch_arrays(shapes, dtypes)
+    opt = MszOptions()
+    opt.max_rounds = max_rounds
+    opt.flags = flags
+    b = ctypes.c_void_p()
+    check(lib().msz_batch_create(ctypes.byref(b), n, nd, dims, dts, ctypes.byref(opt)), "msz_batch_create")
+    return b
+
+
+def msz_batch_fix(batch, orig_ptrs, decomp_ptrs, xis, stream: int = 0):
+    """Returns (status, [MszResult per field])."""
+    n = len(orig_ptrs)
+    fa = (ctypes.c_void_p * n)(*orig_ptrs)
+    ha = (ctypes.c_void_p * n)(*decomp_ptrs)
+    xa = (ctypes.c_double * n)(*[float(x) for x in xis])
+    res = (MszResult * n)()
+    st = lib().msz_batch_fix(batch, fa, ha, xa, ctypes.c_void_p(stream), res)
+    return st, list(res)
+
+
+def msz_batch_destroy(batch):
+    check(lib().msz_batch_destroy(batch), "msz_batch_destroy")
 
 
 def msz_fix_noalloc(shape, dtype, orig_ptr: int, decomp_ptr: int, xi: float, edit_idx_ptr: int,
