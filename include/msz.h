@@ -149,6 +149,30 @@ int msz_batch_fix(msz_batch b, const void* const* orig_dev, const void* const* d
                   void* stream, msz_result* results);
 int msz_batch_destroy(msz_batch b);
 
+/* Served form: continuous batching. A worker thread owned by the server
+ * admits submitted fields while slots (max_slots) and device memory
+ * (budget_bytes, counted with msz_plan_bytes) allow, and corrects all
+ * resident fields together, step by step, each with its own state machine
+ * kept on the device until it converges; fields that arrive while others are
+ * running join at the next chunk of steps. Results equal msz_fix on each
+ * field alone.
+ *   msz_server_submit: inputs must be ready on the device and stay valid and
+ *     unmodified until the request finishes; returns a request id at once.
+ *   msz_server_poll: waits up to wait_ms; MSZ_OK when finished (out filled:
+ *     out->status is the field's status, out->device_ms the submit-to-result
+ *     latency, arrays are device memory held until msz_server_release),
+ *     MSZ_ERR_BUSY while queued or running, MSZ_ERR_ARG for an unknown id.
+ *     A field larger than the whole budget finishes with MSZ_ERR_OOM.
+ *   msz_server_release: frees a finished request's memory.
+ *   msz_server_destroy: stops the worker; running requests are abandoned. */
+typedef struct msz_server_s* msz_server;
+int msz_server_create(msz_server* out, int64_t budget_bytes, int max_slots, const msz_options* opt);
+int msz_server_submit(msz_server s, int ndim, const int64_t dims[3], int dtype, const void* orig_dev,
+                      const void* decomp_dev, double xi, uint64_t* request_id);
+int msz_server_poll(msz_server s, uint64_t request_id, int wait_ms, msz_result* out);
+int msz_server_release(msz_server s, uint64_t request_id);
+int msz_server_destroy(msz_server s);
+
 /* Decompression side (Fig. 3 bottom; g_i = fhat_i + delta_i, Sec. 3):
  * writes edit_val[k] into decomp_dev[edit_idx[k]] for k < n_edits. Indices
  * must be < N (checked on the device: out-of-range entries are skipped and

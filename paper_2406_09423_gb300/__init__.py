@@ -16,7 +16,7 @@ from dataclasses import dataclass
 
 from . import native
 
-__all__ = ["Plan", "Batch", "FixResult", "fix", "apply", "directions", "native"]
+__all__ = ["Plan", "Batch", "Server", "FixResult", "fix", "apply", "directions", "native"]
 
 
 def _torch():
@@ -107,6 +107,60 @@ class Batch:
         if self._b:
             native.msz_batch_destroy(self._b)
             self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching correction service (msz_server_*): fields are
+    admitted as slots and memory allow and corrected together with the
+    fields already resident; each result equals msz_fix on that field."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 64, max_rounds: int = 0, use_tma: bool = True):
+        flags = 0 if use_tma else native.MSZ_OPT_NO_TMA
+        self._s = native.msz_server_create(budget_bytes, max_slots, max_rounds, flags)
+        self._inputs = {}
+
+    def submit(self, f, fhat, xi: float) -> int:
+        """Queues a correction; f and fhat (CUDA tensors) must stay alive and
+        unchanged until the request finishes."""
+        torch = _torch()
+        f = f.contiguous()
+        fhat = fhat.contiguous()
+        torch.cuda.current_stream().synchronize()  # inputs ready before the worker reads them
+        rid = native.msz_server_submit(self._s, tuple(f.shape), f.dtype, f.data_ptr(), fhat.data_ptr(), xi)
+        self._inputs[rid] = (f, fhat)
+        return rid
+
+    def poll(self, rid: int, wait_ms: int = 0, copy: bool = True):
+        """FixResult when finished (and released if copy), else None. The
+        result's device_ms is the submit-to-result latency."""
+        torch = _torch()
+        st, r = native.msz_server_poll(self._s, rid, wait_ms)
+        if st == -9:
+            return None
+        native.check(st, "msz_server_poll")
+        f, _ = self._inputs[rid]
+        res = _result(torch, r, tuple(f.shape), f.dtype, copy)
+        if copy:
+            torch.cuda.synchronize()
+            native.msz_server_release(self._s, rid)
+            del self._inputs[rid]
+        return res
+
+    def release(self, rid: int):
+        native.msz_server_release(self._s, rid)
+        self._inputs.pop(rid, None)
+
+    def close(self):
+        if self._s:
+            native.msz_server_destroy(self._s)
+            self._s = None
+            self._inputs.clear()
 
     def __del__(self):
         try:

@@ -24,6 +24,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "msz.h"
 #include "msz_kernels.cuh"
@@ -1037,3 +1038,409 @@ extern "C" int msz_fix_noalloc(int ndim, const int64_t dims[3], int dtype, const
   }
   return st;
 }
+
+// ---------------------------------------------------------------------------
+// Serving: continuous batching of independent fields.
+//
+// A worker thread owns a CUDA stream and a table of slots. Submitted requests
+// wait in a queue until a slot is free and their device memory fits the
+// budget; they are then admitted into the running set while other fields are
+// mid-correction: the group descriptors are rebuilt, the new field starts at
+// its init phase, and every later step advances all resident fields together
+// (each with its own state machine kept on the device until convergence).
+// After each chunk of steps, converged fields get their edit lists emitted
+// and leave the running set; their results stay in the slot until released.
+// Because every field runs its own state machine on its own buffers, a
+// field's result is the same alone and in any mix.
+// ---------------------------------------------------------------------------
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+
+namespace {
+
+uint64_t now_ns() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct SrvRequest {
+  uint64_t id;
+  int ndim;
+  int64_t dims[3];
+  int dtype;
+  const void* f;
+  const void* fhat;
+  double xi;
+  uint64_t submit_ns;
+};
+
+struct SrvSlot {
+  int state = 0;  // 0 free, 1 running, 2 finished (result held), 3 release requested
+  uint64_t id = 0;
+  void* block = nullptr;
+  size_t bytes = 0;
+  uint64_t submit_ns = 0, done_ns = 0;
+  uint64_t last_ticks = ~0ull;
+  int still = 0;  // chunks without a state transition
+  msz_result result{};
+};
+
+struct SrvDone {  // requests that finished without a slot (rejected)
+  int status;
+  uint64_t done_ns;
+};
+
+}  // namespace
+
+struct msz_server_s {
+  msz_engine_s* E = nullptr;  // nf = slots; geoms/dtypes/bufs indexed by slot
+  int slots_n = 0;
+  int64_t budget = 0, used = 0;
+  std::vector<SrvSlot> slots;
+  std::vector<const void*> f, fhat;
+  std::vector<double> xi;
+  std::deque<SrvRequest> queue;
+  std::unordered_map<uint64_t, int> where;  // id -> slot
+  std::unordered_map<uint64_t, SrvDone> rejected;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread worker;
+  bool stop = false;
+  cudaStream_t stream = nullptr;
+  uint64_t next_id = 1;
+  unsigned char* dev_block = nullptr;  // states + group descriptors
+  int steps_per_chunk = 8;
+  uint64_t launches = 0;
+};
+
+namespace {
+
+// Group membership from the running slots; re-uploads descriptors.
+int srv_rebuild(msz_server_s* S) {
+  msz_engine_s* E = S->E;
+  int k2f = 0, k3f = 0, k2d = 0, k3d = 0;
+  for (int i = 0; i < S->slots_n; ++i) {
+    if (S->slots[i].state != 1) continue;
+    const bool d3 = E->geoms[i].nd == 3;
+    if (E->dtypes[i] == MSZ_F32) {
+      if (d3) E->gf3.members[k3f++] = i;
+      else E->gf2.members[k2f++] = i;
+    } else {
+      if (d3) E->gd3.members[k3d++] = i;
+      else E->gd2.members[k2d++] = i;
+    }
+  }
+  E->gf2.nf = k2f;
+  E->gf3.nf = k3f;
+  E->gd2.nf = k2d;
+  E->gd3.nf = k3d;
+  int rc = setup_groups(E);
+  if (rc != MSZ_OK) return rc;
+  E->each_group([&](auto& g) {
+    if (rc == MSZ_OK && !g.empty()) rc = g.upload(S->f.data(), S->fhat.data(), S->xi.data(), S->stream);
+  });
+  return rc;
+}
+
+// Admits queued requests while slots and budget allow (caller holds mu).
+bool srv_admit(msz_server_s* S) {
+  msz_engine_s* E = S->E;
+  bool changed = false;
+  while (!S->queue.empty()) {
+    const SrvRequest& R = S->queue.front();
+    const int64_t need = engine_bytes(1, &R.ndim, R.dims, &R.dtype);
+    if (need < 0 || need > S->budget) {  // can never fit
+      S->rejected[R.id] = SrvDone{need < 0 ? (int)need : MSZ_ERR_OOM, now_ns()};
+      S->queue.pop_front();
+      S->cv.notify_all();
+      continue;
+    }
+    if (S->used + need > S->budget) break;
+    int slot = -1;
+    for (int i = 0; i < S->slots_n; ++i)
+      if (S->slots[i].state == 0) {
+        slot = i;
+        break;
+      }
+    if (slot < 0) break;
+    SrvSlot& sl = S->slots[slot];
+    void* block = nullptr;
+    if (cudaMallocAsync(&block, (size_t)need, S->stream) != cudaSuccess) {
+      cudaGetLastError();
+      break;  // retry after other fields leave
+    }
+    Geom G;
+    geom_from(R.ndim, R.dims, G);
+    E->geoms[slot] = G;
+    E->dtypes[slot] = R.dtype;
+    Bump b{static_cast<unsigned char*>(block), 0};
+    E->bufs[slot] = FieldBufs{};
+    carve_field(b, G, R.dtype, true, E->bufs[slot]);
+    cudaMemsetAsync(E->bufs[slot].flags, 0, (size_t)emit_tiles(G) * kEmitTile, S->stream);
+    DevState& H = E->h_states[slot];
+    std::memset(&H, 0, sizeof(DevState));
+    H.phase = PH_INIT;
+    H.max_rounds = E->opt.max_rounds ? E->opt.max_rounds : 10000000ull;
+    cudaMemcpyAsync(E->d_states + slot, &H, sizeof(DevState), cudaMemcpyHostToDevice, S->stream);
+    S->f[slot] = R.f;
+    S->fhat[slot] = R.fhat;
+    S->xi[slot] = R.xi;
+    sl.state = 1;
+    sl.id = R.id;
+    sl.block = block;
+    sl.bytes = (size_t)need;
+    sl.submit_ns = R.submit_ns;
+    sl.last_ticks = ~0ull;
+    sl.still = 0;
+    S->used += need;
+    S->where[R.id] = slot;
+    S->queue.pop_front();
+    changed = true;
+  }
+  return changed;
+}
+
+void srv_worker(msz_server_s* S) {
+  cudaSetDevice(S->E->device);
+  msz_engine_s* E = S->E;
+  bool changed = false;
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      // free released slots
+      for (int i = 0; i < S->slots_n; ++i) {
+        SrvSlot& sl = S->slots[i];
+        if (sl.state == 3) {
+          cudaFreeAsync(sl.block, S->stream);
+          S->used -= (int64_t)sl.bytes;
+          S->where.erase(sl.id);
+          sl = SrvSlot{};
+        }
+      }
+      if (srv_admit(S)) changed = true;
+      bool running = false;
+      for (int i = 0; i < S->slots_n; ++i) running = running || S->slots[i].state == 1;
+      if (!running) {
+        if (S->stop) break;
+        if (!changed) {
+          S->cv.wait_for(lk, std::chrono::milliseconds(2));
+          continue;
+        }
+      }
+      if (S->stop && !running) break;
+    }
+    if (changed) {
+      if (srv_rebuild(S) != MSZ_OK) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (int i = 0; i < S->slots_n; ++i)
+          if (S->slots[i].state == 1) {
+            S->slots[i].state = 2;
+            S->slots[i].result.status = MSZ_ERR_CUDA;
+            S->slots[i].done_ns = now_ns();
+          }
+        S->cv.notify_all();
+        changed = true;
+        continue;
+      }
+      changed = false;
+    }
+    // one chunk: init of newly admitted fields, steps, emission of converged ones
+    E->each_group([&](auto& g) { g.init(S->stream); });
+    for (int k = 0; k < S->steps_per_chunk; ++k) E->each_group([&](auto& g) { g.step(S->stream, nullptr); });
+    E->each_group([&](auto& g) { g.emit(S->stream); });
+    S->launches += (uint64_t)S->steps_per_chunk * E->launches_per_step();
+    cudaMemcpyAsync(E->h_states, E->d_states, sizeof(DevState) * S->slots_n, cudaMemcpyDeviceToHost, S->stream);
+    const bool ok = cudaStreamSynchronize(S->stream) == cudaSuccess;
+    const uint64_t t = now_ns();
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (int i = 0; i < S->slots_n; ++i) {
+      SrvSlot& sl = S->slots[i];
+      if (sl.state != 1) continue;
+      const DevState& H = E->h_states[i];
+      int st = 1;  // still running
+      if (!ok) st = MSZ_ERR_CUDA;
+      else if (H.phase == PH_DONE && H.emitted) st = MSZ_OK;
+      else if (H.phase == PH_ERR) st = H.status ? H.status : MSZ_ERR_CUDA;
+      else if (H.ticks == sl.last_ticks && ++sl.still >= 2) st = MSZ_ERR_TIMEOUT;
+      if (H.ticks != sl.last_ticks) sl.still = 0;
+      sl.last_ticks = H.ticks;
+      if (st == 1) continue;
+      msz_result& R = sl.result;
+      std::memset(&R, 0, sizeof(R));
+      R.status = st;
+      R.counts = H.cnt;
+      if (st == MSZ_OK) {
+        R.edit_idx = E->bufs[i].edit_idx;
+        R.edit_val = E->bufs[i].edit_val;
+        R.n_edits = H.n_edits;
+        R.label_max = E->bufs[i].Pup;
+        R.label_min = E->bufs[i].Pdn;
+      }
+      R.device_ms = (float)((t - sl.submit_ns) * 1e-6);  // submit-to-result latency
+      R.launches = S->launches;
+      sl.done_ns = t;
+      sl.state = 2;
+      changed = true;
+    }
+    S->cv.notify_all();
+  }
+  // shutdown: free every slot
+  for (int i = 0; i < S->slots_n; ++i)
+    if (S->slots[i].block) cudaFreeAsync(S->slots[i].block, S->stream);
+  cudaStreamSynchronize(S->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int msz_server_create(msz_server* out, int64_t budget_bytes, int max_slots, const msz_options* opt) {
+  if (!out || budget_bytes <= 0 || max_slots < 1 || max_slots > 4096) return MSZ_ERR_ARG;
+  *out = nullptr;
+  msz_server_s* S = new (std::nothrow) msz_server_s();
+  if (!S) return MSZ_ERR_OOM;
+  msz_engine_s* E = new (std::nothrow) msz_engine_s();
+  if (!E) {
+    delete S;
+    return MSZ_ERR_OOM;
+  }
+  S->E = E;
+  S->slots_n = max_slots;
+  S->budget = budget_bytes;
+  S->slots.resize(max_slots);
+  S->f.assign(max_slots, nullptr);
+  S->fhat.assign(max_slots, nullptr);
+  S->xi.assign(max_slots, 0.0);
+  cudaGetDevice(&E->device);
+  if (opt) E->opt = *opt;
+  E->opt.flags &= ~MSZ_OPT_TIME_KERNELS;
+  E->nf = max_slots;
+  // host arrays with every group sized for all slots
+  E->each_group([&](auto& g) { g.nf = max_slots; });
+  HostArena measure{nullptr, 0, 0};
+  host_layout(E, measure);
+  E->host_mem = new (std::nothrow) unsigned char[measure.off + 64];
+  int rc = E->host_mem ? MSZ_OK : MSZ_ERR_OOM;
+  if (rc == MSZ_OK) {
+    const size_t shift = (64 - (reinterpret_cast<uintptr_t>(E->host_mem) & 63)) & 63;
+    HostArena h{E->host_mem + shift, measure.off, 0};
+    host_layout(E, h);
+    for (int i = 0; i < max_slots; ++i) E->bufs[i] = FieldBufs{};
+    // device: states and group descriptor arrays for all slots
+    Bump mb{nullptr, 0};
+    mb.take(sizeof(DevState) * max_slots, 256);
+    E->each_group([&](auto& g) { g.carve(mb); });
+    if (cudaMalloc((void**)&S->dev_block, mb.off) != cudaSuccess) rc = MSZ_ERR_OOM;
+    if (rc == MSZ_OK) {
+      Bump b{S->dev_block, 0};
+      E->d_states = (DevState*)b.take(sizeof(DevState) * max_slots, 256);
+      E->each_group([&](auto& g) { g.carve(b); });
+      if (cudaMallocHost((void**)&E->h_states, sizeof(DevState) * max_slots) != cudaSuccess) rc = MSZ_ERR_OOM;
+      else E->h_states_pinned = true;
+      cudaMemset(E->d_states, 0, sizeof(DevState) * max_slots);
+    }
+    if (rc == MSZ_OK && cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) rc = MSZ_ERR_CUDA;
+  }
+  E->each_group([&](auto& g) { g.nf = 0; });
+  if (rc != MSZ_OK) {
+    cudaGetLastError();
+    if (S->dev_block) cudaFree(S->dev_block);
+    if (S->stream) cudaStreamDestroy(S->stream);
+    free_engine(E);
+    delete S;
+    return rc;
+  }
+  S->worker = std::thread(srv_worker, S);
+  *out = S;
+  return MSZ_OK;
+}
+
+int msz_server_submit(msz_server S, int ndim, const int64_t dims[3], int dtype, const void* orig_dev,
+                      const void* decomp_dev, double xi, uint64_t* request_id) {
+  if (!S || !dims || !orig_dev || !decomp_dev || !request_id) return MSZ_ERR_ARG;
+  Geom G;
+  if (!geom_from(ndim, dims, G)) return MSZ_ERR_ARG;
+  if (dtype != MSZ_F32 && dtype != MSZ_F64) return MSZ_ERR_DTYPE;
+  if (!xi_ok(xi, dtype)) return MSZ_ERR_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (S->stop) return MSZ_ERR_ARG;
+  SrvRequest R;
+  R.id = S->next_id++;
+  R.ndim = ndim;
+  R.dims[0] = dims[0];
+  R.dims[1] = dims[1];
+  R.dims[2] = (ndim == 3) ? dims[2] : 1;
+  R.dtype = dtype;
+  R.f = orig_dev;
+  R.fhat = decomp_dev;
+  R.xi = xi;
+  R.submit_ns = now_ns();
+  S->queue.push_back(R);
+  *request_id = R.id;
+  S->cv.notify_all();
+  return MSZ_OK;
+}
+
+int msz_server_poll(msz_server S, uint64_t request_id, int wait_ms, msz_result* out) {
+  if (!S || !out) return MSZ_ERR_ARG;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto ready = [&]() -> int {
+    auto rj = S->rejected.find(request_id);
+    if (rj != S->rejected.end()) return 1;
+    auto it = S->where.find(request_id);
+    if (it == S->where.end()) {
+      for (const SrvRequest& q : S->queue)
+        if (q.id == request_id) return 0;
+      return -1;
+    }
+    return S->slots[it->second].state == 2 ? 1 : 0;
+  };
+  int r = ready();
+  if (r == 0 && wait_ms > 0)
+    S->cv.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return ready() != 0; }), r = ready();
+  if (r < 0) return MSZ_ERR_ARG;
+  if (r == 0) return MSZ_ERR_BUSY;
+  auto rj = S->rejected.find(request_id);
+  if (rj != S->rejected.end()) {
+    std::memset(out, 0, sizeof(*out));
+    out->status = rj->second.status;
+    return MSZ_OK;
+  }
+  *out = S->slots[S->where[request_id]].result;
+  return MSZ_OK;
+}
+
+int msz_server_release(msz_server S, uint64_t request_id) {
+  if (!S) return MSZ_ERR_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (S->rejected.erase(request_id)) return MSZ_OK;
+  auto it = S->where.find(request_id);
+  if (it == S->where.end() || S->slots[it->second].state != 2) return MSZ_ERR_BUSY;
+  S->slots[it->second].state = 3;
+  S->cv.notify_all();
+  return MSZ_OK;
+}
+
+int msz_server_destroy(msz_server S) {
+  if (!S) return MSZ_ERR_ARG;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    S->queue.clear();
+    for (SrvSlot& sl : S->slots)
+      if (sl.state == 1) sl.state = 2;  // abandon running fields
+  }
+  S->cv.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  if (S->dev_block) cudaFree(S->dev_block);
+  if (S->stream) cudaStreamDestroy(S->stream);
+  free_engine(S->E);
+  delete S;
+  return MSZ_OK;
+}
+
+}  // extern "C"

@@ -108,6 +108,16 @@ def lib() -> ctypes.CDLL:
         L.msz_batch_fix.restype = I
         L.msz_batch_destroy.argtypes = [P]
         L.msz_batch_destroy.restype = I
+        L.msz_server_create.argtypes = [ctypes.POINTER(P), I64, I, P]
+        L.msz_server_create.restype = I
+        L.msz_server_submit.argtypes = [P, I, P, I, P, P, D, ctypes.POINTER(U64)]
+        L.msz_server_submit.restype = I
+        L.msz_server_poll.argtypes = [P, U64, I, ctypes.POINTER(MszResult)]
+        L.msz_server_poll.restype = I
+        L.msz_server_release.argtypes = [P, U64]
+        L.msz_server_release.restype = I
+        L.msz_server_destroy.argtypes = [P]
+        L.msz_server_destroy.restype = I
         L.msz_fix_noalloc.argtypes = [I, P, I, P, P, D, P, P, P, P, P, ctypes.POINTER(MszResult)]
         L.msz_fix_noalloc.restype = I
         L.msz_strerror.argtypes = [I]
@@ -221,6 +231,39 @@ def msz_batch_fix(batch, orig_ptrs, decomp_ptrs, xis, stream: int = 0):
 
 def msz_batch_destroy(batch):
     check(lib().msz_batch_destroy(batch), "msz_batch_destroy")
+
+
+def msz_server_create(budget_bytes: int, max_slots: int = 64, max_rounds: int = 0, flags: int = 0):
+    opt = MszOptions()
+    opt.max_rounds = max_rounds
+    opt.flags = flags
+    srv = ctypes.c_void_p()
+    check(lib().msz_server_create(ctypes.byref(srv), int(budget_bytes), int(max_slots), ctypes.byref(opt)),
+          "msz_server_create")
+    return srv
+
+
+def msz_server_submit(srv, shape, dtype, orig_ptr: int, decomp_ptr: int, xi: float) -> int:
+    ndim, d = dims_of(shape)
+    rid = ctypes.c_uint64()
+    check(lib().msz_server_submit(srv, ndim, d, dtype_code(dtype), ctypes.c_void_p(orig_ptr),
+                                  ctypes.c_void_p(decomp_ptr), float(xi), ctypes.byref(rid)), "msz_server_submit")
+    return int(rid.value)
+
+
+def msz_server_poll(srv, request_id: int, wait_ms: int = 0):
+    """(status, MszResult): status MSZ_OK when finished, MSZ_ERR_BUSY otherwise."""
+    r = MszResult()
+    st = lib().msz_server_poll(srv, int(request_id), int(wait_ms), ctypes.byref(r))
+    return st, r
+
+
+def msz_server_release(srv, request_id: int) -> int:
+    return lib().msz_server_release(srv, int(request_id))
+
+
+def msz_server_destroy(srv):
+    check(lib().msz_server_destroy(srv), "msz_server_destroy")
 
 
 def msz_fix_noalloc(shape, dtype, orig_ptr: int, decomp_ptr: int, xi: float, edit_idx_ptr: int,
