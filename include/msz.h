@@ -200,8 +200,8 @@ int msz_directions(const void* field_dev, int ndim, const int64_t dims[3], int d
  * label_max_dev / label_min_dev hold N labels. out->edit_idx etc. point to
  * them. Every other array of the loop lives in one static device array of
  * 64 MiB that each GPU loading the library holds until exit; a field needs
- * about 23 bytes per vertex (float32) or 27 (float64) of it, so up to about
- * 2.9 M (float32) / 2.4 M (float64) vertices. Larger fields are rejected
+ * about 40 bytes per vertex (float32) or 44 (float64) of it, so up to about
+ * 1.7 M (float32) / 1.5 M (float64) vertices. Larger fields are rejected
  * with MSZ_ERR_TOO_LARGE before any work. The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture. All calls share

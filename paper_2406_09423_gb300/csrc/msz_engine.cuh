@@ -30,7 +30,7 @@ namespace msz {
 
 enum : uint32_t { PH_INIT = 0, PH_FLABELS = 1, PH_C = 2, PH_R = 3, PH_DONE = 4, PH_ERR = 5 };
 enum : uint32_t { ACT_NONE = 0, ACT_MARK_C = 1, ACT_LABELS = 2, ACT_APPLY_R = 3 };
-enum : uint32_t { L_INIT = 0, L_JUMP = 1, L_DONE = 2 };
+enum : uint32_t { L_INIT = 0, L_EINIT = 1, L_JUMP = 2, L_DONE = 3 };
 enum : uint32_t { E_NONFINITE = 1, E_ARG = 2, E_BOUND = 4, E_TIMEOUT = 8 };
 
 // Work-unit kinds.
@@ -49,6 +49,7 @@ struct DevState {
   uint32_t acc_ap[2];  // apply: decreases, freezes
   uint32_t acc_r[4];   // rcheck: wrong max, wrong min, asc troublemakers, desc troublemakers
   uint32_t jump_rounds, emitted;
+  uint32_t f_resolved, pad1;  // f's labels resolved in place (first R-check)
   uint64_t rounds, max_rounds, n_edits;
   uint64_t ticks;  // advanced by every state transition (stall detection)
   msz_counts cnt;
@@ -63,10 +64,17 @@ struct Field {
   uint8_t* fdir;
   uint8_t* gdir;
   uint8_t* flags;
-  int32_t* Mf;
+  int32_t* Mf;    // f: tile terminals, then (after the first R-check) labels
   int32_t* mf;
-  int32_t* Pup;
+  int32_t* Pup;   // g: tile terminals, labels once the field has converged
   int32_t* Pdn;
+  int32_t* Lfu;   // resolved labels of tile exits (f, g; ascending, descending)
+  int32_t* Lfd;
+  int32_t* Lgu;
+  int32_t* Lgd;
+  uint32_t* exu;  // bitmaps of tile-exit vertices (ascending, descending lines)
+  uint32_t* exd;
+  uint8_t* tdirty;  // label tiles whose terminals must be recomputed
   uint32_t* cases;
   uint32_t* touched;
   uint32_t* tile_cnt;
@@ -208,6 +216,7 @@ __device__ void ctrl_after_rcheck(DevState* st) {
   st->cnt.mismatch[1] += wm;
   st->acc_r[0] = st->acc_r[1] = 0;
   st->lstate = L_INIT;
+  st->f_resolved = 1;
   st->ticks++;
   if (wM + wm == 0) {
     st->phase = PH_DONE;

@@ -135,6 +135,13 @@ struct FieldBufs {
   int32_t* mf = nullptr;
   int32_t* Pup = nullptr;
   int32_t* Pdn = nullptr;
+  int32_t* Lfu = nullptr;
+  int32_t* Lfd = nullptr;
+  int32_t* Lgu = nullptr;
+  int32_t* Lgd = nullptr;
+  uint32_t* exu = nullptr;
+  uint32_t* exd = nullptr;
+  uint8_t* tdirty = nullptr;
   uint32_t* cases = nullptr;
   uint32_t* touched = nullptr;
   uint32_t* tile_cnt = nullptr;
@@ -143,6 +150,15 @@ struct FieldBufs {
 };
 
 int emit_tiles(const Geom& G) { return (G.n + kEmitTile - 1) / kEmitTile; }
+
+int label_tiles(const Geom& G) {
+  if (G.nd == 3) {
+    using LG = LabelGeom<3>;
+    return ((G.nx + LG::TX - 1) / LG::TX) * ((G.ny + LG::TY - 1) / LG::TY) * ((G.nz + LG::TZ - 1) / LG::TZ);
+  }
+  using LG = LabelGeom<2>;
+  return ((G.nx + LG::TX - 1) / LG::TX) * ((G.ny + LG::TY - 1) / LG::TY);
+}
 
 // Carves a field's buffers. Outputs (labels Pup/Pdn, edit list) are carved
 // too unless the caller supplies them (with_outputs = false).
@@ -154,6 +170,14 @@ void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs
   B.flags = (uint8_t*)b.take(nt * kEmitTile);
   B.Mf = (int32_t*)b.take(n * 4);
   B.mf = (int32_t*)b.take(n * 4);
+  B.Lfu = (int32_t*)b.take(n * 4);
+  B.Lfd = (int32_t*)b.take(n * 4);
+  B.Lgu = (int32_t*)b.take(n * 4);
+  B.Lgd = (int32_t*)b.take(n * 4);
+  const size_t nw = (n + 31) / 32;
+  B.exu = (uint32_t*)b.take(nw * 4);
+  B.exd = (uint32_t*)b.take(nw * 4);
+  B.tdirty = (uint8_t*)b.take((size_t)label_tiles(G));
   B.cases = (uint32_t*)b.take(n * 4);
   B.touched = (uint32_t*)b.take(n * 4);
   B.tile_cnt = (uint32_t*)b.take(nt * 4);
@@ -258,6 +282,13 @@ struct Group {
       F.mf = B.mf;
       F.Pup = B.Pup;
       F.Pdn = B.Pdn;
+      F.Lfu = B.Lfu;
+      F.Lfd = B.Lfd;
+      F.Lgu = B.Lgu;
+      F.Lgd = B.Lgd;
+      F.exu = B.exu;
+      F.exd = B.exd;
+      F.tdirty = B.tdirty;
       F.cases = B.cases;
       F.touched = B.touched;
       F.tile_cnt = B.tile_cnt;
@@ -268,8 +299,7 @@ struct Group {
       F.TL = tiling(G);
       F.units[K_DENSE] = (G.n + kDenseChunk - 1) / kDenseChunk;
       F.units[K_SWEEP] = F.TL.ntiles;
-      F.units[K_LABEL] = ((G.nx + LG::TX - 1) / LG::TX) * ((G.ny + LG::TY - 1) / LG::TY) *
-                         ((G.nz + LG::TZ - 1) / LG::TZ);
+      F.units[K_LABEL] = label_tiles(G);
       F.units[K_SPARSE] = std::max(1, std::min(1024, (G.n + 65535) / 65536));
       F.units[K_EMIT] = emit_tiles(G);
       if (tma && !encode(&h_maps[2 * j], G, B.g, B.fdir)) tma = false;
@@ -320,7 +350,7 @@ struct Group {
     return MSZ_OK;
   }
 
-  int launches_per_step() const { return empty() ? 0 : 6 + kJumpsPerStep; }
+  int launches_per_step() const { return empty() ? 0 : 7 + kJumpsPerStep; }
 
   void init(cudaStream_t s) {
     if (empty()) return;
@@ -339,6 +369,7 @@ struct Group {
     k_mark_c<T, ND><<<grid[K_SPARSE], kThreads, 0, s>>>(args);
     if (e) cudaEventRecord(e[2], s);
     k_label_tile<T, ND><<<grid[K_LABEL], kThreads, label_smem, s>>>(args);
+    k_einit<T><<<grid[K_DENSE], kThreads, 0, s>>>(args);
     for (int j = 0; j < kJumpsPerStep; ++j) k_jump<T><<<grid[K_DENSE], kThreads, 0, s>>>(args);
     if (e) cudaEventRecord(e[3], s);
     if (e) cudaEventRecord(e[4], s);

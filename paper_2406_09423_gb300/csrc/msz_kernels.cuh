@@ -5,8 +5,66 @@
 
 namespace msz {
 
-#define MSZ_UNIT_LOOP(A, KIND)                                                  \
-  for (int u_ = blockIdx.x; u_ < (A).total[KIND]; u_ += gridDim.x)
+template <int ND>
+struct LabelGeom {
+  static constexpr int TX = (ND == 3) ? 32 : 64;
+  static constexpr int TY = (ND == 3) ? 8 : 32;
+  static constexpr int TZ = (ND == 3) ? 8 : 1;
+  static constexpr int TV = TX * TY * TZ;  // 2048 vertices
+  static constexpr int SX = TX + 2, SY = TY + 2, SZ = (ND == 3) ? TZ + 2 : 1;
+  static constexpr int HALO = SX * SY * SZ;  // < 65536: pointers fit in 16 bits
+  static constexpr int PER_THREAD = TV / kThreads;
+  static constexpr int ROWS = SY * SZ;
+};
+
+// Marks every label tile whose tile or one-vertex halo contains vertex u:
+// the tiles of u + d for d in {-1,0,1}^d (their terminals must be redone).
+template <int ND>
+__device__ __forceinline__ void mark_dirty_tiles(uint8_t* tdirty, const Geom& G, int u) {
+  using LG = LabelGeom<ND>;
+  int x, y, z;
+  coords(G, u, x, y, z);
+  const int tx = (G.nx + LG::TX - 1) / LG::TX, ty = (G.ny + LG::TY - 1) / LG::TY;
+  const int zlo = (ND == 3) ? -1 : 0, zhi = (ND == 3) ? 1 : 0;
+  for (int dz = zlo; dz <= zhi; ++dz) {
+    const int Z = z + dz;
+    if (Z < 0 || Z >= G.nz) continue;
+    if (dz != 0 && (Z / LG::TZ) == (z / LG::TZ)) continue;  // same tile row as dz = 0
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int Y = y + dy;
+      if (Y < 0 || Y >= G.ny) continue;
+      if (dy != 0 && (Y / LG::TY) == (y / LG::TY)) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int X = x + dx;
+        if (X < 0 || X >= G.nx) continue;
+        if (dx != 0 && (X / LG::TX) == (x / LG::TX)) continue;
+        tdirty[(X / LG::TX) + tx * ((Y / LG::TY) + ty * (Z / LG::TZ))] = 1;
+      }
+    }
+  }
+}
+
+// Next unit of this block (u, u + gridDim.x, ...) whose field satisfies
+// active(field); the units of an inactive field are skipped in O(1), so a
+// kernel with nothing to do costs one lookup per field and block.
+template <class T, class Pred>
+__device__ __forceinline__ int next_active_unit(const GroupArgs<T>& A, const int* pre, int total, int u, Pred active,
+                                                int& fi) {
+  while (u < total) {
+    const int i = field_of_unit(pre, A.nf, u);
+    if (active(A.fields[i])) {
+      fi = i;
+      return u;
+    }
+    const int end = __ldg(pre + i + 1);
+    u += ((end - u + (int)gridDim.x - 1) / (int)gridDim.x) * (int)gridDim.x;
+  }
+  return total;
+}
+
+#define MSZ_ACTIVE_UNITS(A, KIND, PRE, FI, PRED)                                                     \
+  for (int FI = 0, u_ = next_active_unit((A), (PRE), (A).total[KIND], (int)blockIdx.x, (PRED), FI); \
+       u_ < (A).total[KIND]; u_ = next_active_unit((A), (PRE), (A).total[KIND], u_ + (int)gridDim.x, (PRED), FI))
 
 // ---------------------------------------------------------------------------
 // Init (Sec. 3 constraint): validate f and fhat (finite, |fhat - f| <= xi via
@@ -15,11 +73,10 @@ namespace msz {
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_init(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
-  MSZ_UNIT_LOOP(A, K_DENSE) {
-    const int i = field_of_unit(pre, A.nf, u_);
+  auto active = [](const Field<T>& F) { return F.st->phase == PH_INIT; };
+  MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
-    if (st->phase != PH_INIT) continue;
     const int v0 = (u_ - pre[i]) * kDenseChunk;
     const int v1 = min(F.G.n, v0 + kDenseChunk);
     uint32_t err = 0;
@@ -37,6 +94,16 @@ __global__ void __launch_bounds__(kThreads) k_init(GroupArgs<T> A) {
       F.flags[v] = 0;
     }
     if (err) atomicOr(&st->err_bits, err);
+    // tile-exit bitmaps start empty; every label tile starts dirty
+    for (int w = (v0 >> 5) + threadIdx.x; w < ((v1 + 31) >> 5); w += blockDim.x) {
+      F.exu[w] = 0;
+      F.exd[w] = 0;
+    }
+    {
+      const int ntl = F.units[K_LABEL], nu = F.units[K_DENSE], lu = u_ - pre[i];
+      const int per = (ntl + nu - 1) / nu;
+      for (int t = lu * per + threadIdx.x; t < min(ntl, (lu + 1) * per); t += blockDim.x) F.tdirty[t] = 1;
+    }
     if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
       ctrl_after_init(st);
       st->units_done = 0;
@@ -78,10 +145,10 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
     int u, i, x0, y0, c0, ppt;
   };
   auto next_tile = [&](Tile& t, int u) -> bool {
-    for (; u < A.total[K_SWEEP]; u += gridDim.x) {
-      const int i = field_of_unit(pre, A.nf, u);
+    int i = 0;
+    u = next_active_unit(A, pre, A.total[K_SWEEP], u, [](const Field<T>& F) { return F.st->phase == PH_C; }, i);
+    if (u < A.total[K_SWEEP]) {
       const Field<T>& F = A.fields[i];
-      if (F.st->phase != PH_C) continue;
       const SweepTiling& TL = F.TL;
       const int lt = u - pre[i];
       const int bx = lt % TL.tiles_x;
@@ -167,22 +234,28 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
 
       // One plane p of the tile: stage it, derive its quantities into dst
       // (role B), then classify the vertices of plane A (Cv previous).
-      auto step = [&](int qq, int p, PV& dst, uint16_t& fd_dst, const PV& Cv, const PV& Av, uint16_t fdA) -> bool {
+      auto step = [&](int qq, int p, PV& dst, uint32_t& fd_dst, const PV& Cv, const PV& Av, uint32_t fdA) -> bool {
         const int pcoord = t.c0 - 1 + p;  // plane coordinate (z in 3D, y in 2D)
         unsigned char* sp = smem + (kTMA ? (qq & SM1) * SG::STAGE_BYTES : 0);
         const T* stage = reinterpret_cast<const T*>(sp);
         if (kTMA) {
-          const bool got = mbar_wait_or_abort(&full[qq & SM1], (uint32_t)((qq / SG::STAGES) & 1), &s_abort);
-          if (!__all_sync(kFull, got)) {
+          // lane 0 waits for the stage; the warp follows its verdict
+          bool got = true;
+          if (lane == 0) got = mbar_wait_or_abort(&full[qq & SM1], (uint32_t)((qq / SG::STAGES) & 1), &s_abort);
+          got = __shfl_sync(kFull, got, 0);
+          if (!got) {
             if (lane == 0) atomicExch(&s_abort, 1);
             return false;
           }
           dst = plane_vals<T, ND>(stage, tx, w);
-          if (ND == 3)
-            fd_dst = (uint16_t)(sp[SG::G_BYTES + (2 * w) * SG::TX + tx] |
-                                (sp[SG::G_BYTES + (2 * w + 1) * SG::TX + tx] << 8));
-          else
+          if (ND == 3) {
+            uint32_t fd = 0;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) fd |= (uint32_t)sp[SG::G_BYTES + (RPT * w + k) * SG::TX + tx] << (8 * k);
+            fd_dst = fd;
+          } else {
             fd_dst = sp[SG::G_BYTES + tx];
+          }
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[qq & SM1]);
         } else {
@@ -198,12 +271,12 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
           }
           __syncthreads();
           dst = plane_vals<T, ND>(stage, tx, w);
-          uint16_t fd = 0;
+          uint32_t fd = 0;
 #pragma unroll
           for (int k = 0; k < RPT; ++k) {
             const int vx = t.x0 + tx, vy = (ND == 3) ? t.y0 + RPT * w + k : pcoord, vz = (ND == 3) ? pcoord : 0;
             if (vx < G.nx && vy >= 0 && vy < G.ny && vz >= 0 && vz < G.nz)
-              fd |= (uint16_t)(F.fdir[vx + G.nx * (vy + G.ny * vz)] << (8 * k));
+              fd |= (uint32_t)F.fdir[vx + G.nx * (vy + G.ny * vz)] << (8 * k);
           }
           fd_dst = fd;
         }
@@ -216,7 +289,7 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
             gb |= ((uint32_t)is_max_at<T, RPT>(Cv, Av, dst, k) << (8 * k)) |
                   ((uint32_t)is_min_at<T, RPT>(Cv, Av, dst, k) << (8 * k + 4));
           const uint32_t fa = fdA;
-          const uint32_t fb = fa & (fa >> 1) & (fa >> 2) & (fa >> 3) & 0x1111u;  // nibble == 15
+          const uint32_t fb = fa & (fa >> 1) & (fa >> 2) & (fa >> 3) & 0x11111111u;  // nibble == 15
           uint32_t diff = (gb ^ fb) & vmask;
           if (!(p - 2 < chunk && pcoord - 1 < axis_n)) diff = 0;
           if (__any_sync(kFull, diff != 0)) {
@@ -251,7 +324,7 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
       };
 
       PV P0{}, P1{}, P2{};
-      uint16_t f0 = 0, f1 = 0, f2 = 0;
+      uint32_t f0 = 0, f1 = 0, f2 = 0;
       for (int p = 0; p < t.ppt && ok; p += 3, q += 3) {  // planes rotate through P0, P1, P2
         ok = step(q, p, P0, f0, P1, P2, f2) && step(q + 1, p + 1, P1, f1, P2, P0, f0) &&
              step(q + 2, p + 2, P2, f2, P0, P1, f1);
@@ -291,11 +364,10 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
 template <class T, int ND>
 __global__ void __launch_bounds__(kThreads) k_mark_c(GroupArgs<T> A) {
   const int* pre = A.prefix + K_SPARSE * (A.nf + 1);
-  MSZ_UNIT_LOOP(A, K_SPARSE) {
-    const int i = field_of_unit(pre, A.nf, u_);
+  auto active = [](const Field<T>& F) { return F.st->action == ACT_MARK_C; };
+  MSZ_ACTIVE_UNITS(A, K_SPARSE, pre, i, active) {
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
-    if (st->action != ACT_MARK_C) continue;
     const uint32_t type = st->T, nc = st->ncase;
     const int S = F.units[K_SPARSE], k = u_ - pre[i];
     const uint32_t b = (uint32_t)(((uint64_t)nc * k) / S), e = (uint32_t)(((uint64_t)nc * (k + 1)) / S);
@@ -321,18 +393,6 @@ __global__ void __launch_bounds__(kThreads) k_mark_c(GroupArgs<T> A) {
 // vertex outside the tile on its integral line, or to the extremum it reaches
 // inside. Job 0: f (fdir, Mf, mf). Job 1: g (gdir, Pup, Pdn).
 // ---------------------------------------------------------------------------
-template <int ND>
-struct LabelGeom {
-  static constexpr int TX = (ND == 3) ? 32 : 64;
-  static constexpr int TY = (ND == 3) ? 8 : 32;
-  static constexpr int TZ = (ND == 3) ? 8 : 1;
-  static constexpr int TV = TX * TY * TZ;  // 2048 vertices
-  static constexpr int SX = TX + 2, SY = TY + 2, SZ = (ND == 3) ? TZ + 2 : 1;
-  static constexpr int HALO = SX * SY * SZ;  // < 65536: pointers fit in 16 bits
-  static constexpr int PER_THREAD = TV / kThreads;
-  static constexpr int ROWS = SY * SZ;
-};
-
 template <class T, int ND>
 size_t label_smem_bytes() {
   using LG = LabelGeom<ND>;
@@ -352,11 +412,10 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(GroupArgs<T> A) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int HS = LG::SX, HSS = LG::SX * LG::SY;
   constexpr int NC = (ND == 3) ? 15 : 7;
-  MSZ_UNIT_LOOP(A, K_LABEL) {
-    const int fi = field_of_unit(pre, A.nf, u_);
+  auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_INIT; };
+  MSZ_ACTIVE_UNITS(A, K_LABEL, pre, fi, active) {
     const Field<T>& F = A.fields[fi];
     DevState* st = F.st;
-    if (st->action != ACT_LABELS || st->lstate != L_INIT) continue;
     const bool job = st->ljob != 0;
     const T* src = job ? F.g : F.f;
     uint8_t* dir = job ? F.gdir : F.fdir;
@@ -366,6 +425,17 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(GroupArgs<T> A) {
     const int tiles_x = (G.nx + LG::TX - 1) / LG::TX;
     const int tiles_y = (G.ny + LG::TY - 1) / LG::TY;
     const int tile = u_ - pre[fi];
+    // g's terminals only change in tiles whose tile or halo was edited
+    const bool redo = !job || F.tdirty[tile];
+    __syncthreads();
+    if (!redo) {
+      if (unit_done(st, F.units[K_LABEL]) && threadIdx.x == 0) {
+        st->lstate = L_EINIT;
+        st->ticks++;
+        st->units_done = 0;
+      }
+      continue;
+    }
     const int x0 = (tile % tiles_x) * LG::TX;
     const int y0 = ((tile / tiles_x) % tiles_y) * LG::TY;
     const int z0 = (tile / (tiles_x * tiles_y)) * LG::TZ;
@@ -440,16 +510,60 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(GroupArgs<T> A) {
       if (x < G.nx && y < G.ny && z < G.nz) {
         const int v = x + G.nx * (y + G.ny * z);
         const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
-        auto global_of = [&](int h) -> int {  // terminal halo cell -> global index
+        // terminal cell -> global index; a terminal in the halo is a tile
+        // exit, recorded in the bitmap the cross-tile jumping walks
+        auto global_of = [&](int h, uint32_t* ex) -> int {
           const int hx = h % LG::SX, hy = (h / LG::SX) % LG::SY, hz = h / HSS;
-          return (x0 - 1 + hx) + G.nx * ((y0 - 1 + hy) + G.ny * ((ND == 3) ? (z0 - 1 + hz) : 0));
+          const int e = (x0 - 1 + hx) + G.nx * ((y0 - 1 + hy) + G.ny * ((ND == 3) ? (z0 - 1 + hz) : 0));
+          const bool halo = hx == 0 || hx == LG::SX - 1 || hy == 0 || hy == LG::SY - 1 ||
+                            (ND == 3 && (hz == 0 || hz == LG::SZ - 1));
+          if (halo) atomicOr(&ex[e >> 5], 1u << (e & 31));
+          return e;
         };
         dir[v] = dbyte[k];
-        OA[v] = global_of(Pu[c]);
-        OB[v] = global_of(Pd[c]);
+        OA[v] = global_of(Pu[c], F.exu);
+        OB[v] = global_of(Pd[c], F.exd);
       }
     }
+    __syncthreads();
+    if (job && threadIdx.x == 0) F.tdirty[tile] = 0;  // f's pass leaves every tile dirty for g's first
     if (unit_done(st, F.units[K_LABEL]) && threadIdx.x == 0) {
+      st->lstate = L_EINIT;
+      st->ticks++;
+      st->units_done = 0;
+    }
+  }
+}
+
+// Labels, second level. Every tile exit e starts from its tile terminal,
+// L[e] = T[e] (k_einit); then pointer jumping over the exits only (k_jump):
+// L[e] <- L[L[e]] while L[e] is not an extremum (T[x] == x marks one). A
+// round that changes nothing means every exit knows its extremum.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_einit(GroupArgs<T> A) {
+  const int* pre = A.prefix + K_DENSE * (A.nf + 1);
+  auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_EINIT; };
+  MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
+    const Field<T>& F = A.fields[i];
+    DevState* st = F.st;
+    const bool job = st->ljob != 0;
+    const int32_t* TA = job ? F.Pup : F.Mf;
+    const int32_t* TB = job ? F.Pdn : F.mf;
+    int32_t* LA = job ? F.Lgu : F.Lfu;
+    int32_t* LB = job ? F.Lgd : F.Lfd;
+    const int v0 = (u_ - pre[i]) * kDenseChunk;
+    const int v1 = min(F.G.n, v0 + kDenseChunk);
+    for (int w = (v0 >> 5) + threadIdx.x; w < ((v1 + 31) >> 5); w += blockDim.x) {
+      for (uint32_t m = F.exu[w]; m; m &= m - 1) {
+        const int e = (w << 5) + __ffs(m) - 1;
+        LA[e] = TA[e];
+      }
+      for (uint32_t m = F.exd[w]; m; m &= m - 1) {
+        const int e = (w << 5) + __ffs(m) - 1;
+        LB[e] = TB[e];
+      }
+    }
+    if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
       st->lstate = L_JUMP;
       st->jump_rounds = 0;
       st->ticks++;
@@ -458,27 +572,38 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(GroupArgs<T> A) {
   }
 }
 
-// One pointer-jumping round, in place: P[v] <- P[P[v]]. A round that changes
-// nothing means every pointer is a root (an extremum).
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
-  MSZ_UNIT_LOOP(A, K_DENSE) {
-    const int i = field_of_unit(pre, A.nf, u_);
+  auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_JUMP; };
+  MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
-    if (st->action != ACT_LABELS || st->lstate != L_JUMP) continue;
     const bool job = st->ljob != 0;
-    int32_t* PA = job ? F.Pup : F.Mf;
-    int32_t* PB = job ? F.Pdn : F.mf;
+    const int32_t* TA = job ? F.Pup : F.Mf;
+    const int32_t* TB = job ? F.Pdn : F.mf;
+    int32_t* LA = job ? F.Lgu : F.Lfu;
+    int32_t* LB = job ? F.Lgd : F.Lfd;
     const int v0 = (u_ - pre[i]) * kDenseChunk;
     const int v1 = min(F.G.n, v0 + kDenseChunk);
     uint32_t changed[1] = {0};
-    for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-      const int p = PA[v], q = PA[p];
-      if (q != p) { PA[v] = q; ++changed[0]; }
-      const int r = PB[v], s = PB[r];
-      if (s != r) { PB[v] = s; ++changed[0]; }
+    for (int w = (v0 >> 5) + threadIdx.x; w < ((v1 + 31) >> 5); w += blockDim.x) {
+      for (uint32_t m = F.exu[w]; m; m &= m - 1) {
+        const int e = (w << 5) + __ffs(m) - 1;
+        const int x = LA[e];
+        if (TA[x] != x) {
+          const int y = LA[x];
+          if (y != x) { LA[e] = y; ++changed[0]; }
+        }
+      }
+      for (uint32_t m = F.exd[w]; m; m &= m - 1) {
+        const int e = (w << 5) + __ffs(m) - 1;
+        const int x = LB[e];
+        if (TB[x] != x) {
+          const int y = LB[x];
+          if (y != x) { LB[e] = y; ++changed[0]; }
+        }
+      }
     }
     block_add<1>(changed, &st->acc_changed);
     if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
@@ -488,6 +613,13 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
   }
 }
 
+// Extremum reached from v: its tile terminal t when t is an extremum
+// (T[t] == t), else the resolved label of the exit t.
+__device__ __forceinline__ int resolve_label(const int32_t* Tt, const int32_t* L, int v) {
+  const int t = Tt[v];
+  return (Tt[t] == t) ? t : L[t];
+}
+
 // R-loop check (Sec. 4.2): count wrong labels; a wrongly labelled vertex whose
 // steepest neighbour in g differs from f's is a troublemaker. Wrong max label:
 // decrease its ascending neighbour in g (Eq. 6). Wrong min label: decrease the
@@ -495,17 +627,31 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
 template <class T, int ND>
 __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
-  MSZ_UNIT_LOOP(A, K_DENSE) {
-    const int i = field_of_unit(pre, A.nf, u_);
+  auto active = [](const Field<T>& F) {
+    return F.st->action == ACT_LABELS && F.st->lstate == L_DONE && F.st->ljob == 1;
+  };
+  MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
-    if (st->action != ACT_LABELS || st->lstate != L_DONE || st->ljob != 1) continue;
     const int v0 = (u_ - pre[i]) * kDenseChunk;
     const int v1 = min(F.G.n, v0 + kDenseChunk);
     uint32_t acc[4] = {0, 0, 0, 0};
+    const bool fres = st->f_resolved != 0;
     for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-      const bool wM = F.Pup[v] != F.Mf[v];
-      const bool wm = F.Pdn[v] != F.mf[v];
+      int M, m;
+      if (fres) {
+        M = F.Mf[v];
+        m = F.mf[v];
+      } else {  // first R-check: f's labels resolved in place (safe: exits keep their label)
+        M = resolve_label(F.Mf, F.Lfu, v);
+        m = resolve_label(F.mf, F.Lfd, v);
+      }
+      const bool wM = resolve_label(F.Pup, F.Lgu, v) != M;
+      const bool wm = resolve_label(F.Pdn, F.Lgd, v) != m;
+      if (!fres) {
+        F.Mf[v] = M;
+        F.mf[v] = m;
+      }
       acc[0] += wM;
       acc[1] += wm;
       if (wM || wm) {
@@ -533,12 +679,11 @@ __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
   const int* pre = A.prefix + K_SPARSE * (A.nf + 1);
-  MSZ_UNIT_LOOP(A, K_SPARSE) {
-    const int i = field_of_unit(pre, A.nf, u_);
+  auto active = [](const Field<T>& F) { return F.st->action == ACT_MARK_C || F.st->action == ACT_APPLY_R; };
+  MSZ_ACTIVE_UNITS(A, K_SPARSE, pre, i, active) {
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
     const uint32_t act = st->action;
-    if (act != ACT_MARK_C && act != ACT_APPLY_R) continue;
     const uint32_t nt = st->ntouch;
     const int S = F.units[K_SPARSE], k = u_ - pre[i];
     const uint32_t b = (uint32_t)(((uint64_t)nt * k) / S), e = (uint32_t)(((uint64_t)nt * (k + 1)) / S);
@@ -556,6 +701,8 @@ __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
         ++acc[0];
       }
       F.flags[u] = bb;
+      if (F.G.nd == 3) mark_dirty_tiles<3>(F.tdirty, F.G, u);
+      else mark_dirty_tiles<2>(F.tdirty, F.G, u);
     }
     block_add<2>(acc, st->acc_ap);
     if (unit_done(st, S) && threadIdx.x == 0) {
@@ -600,12 +747,19 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_emit_count(GroupArgs<T> A) {
   const int* pre = A.prefix + K_EMIT * (A.nf + 1);
   __shared__ uint32_t s;
-  MSZ_UNIT_LOOP(A, K_EMIT) {
-    const int i = field_of_unit(pre, A.nf, u_);
+  auto active = [](const Field<T>& F) { return F.st->phase == PH_DONE && !F.st->emitted; };
+  MSZ_ACTIVE_UNITS(A, K_EMIT, pre, i, active) {
     const Field<T>& F = A.fields[i];
-    if (F.st->phase != PH_DONE || F.st->emitted) continue;
     const int tile = u_ - pre[i];
     const int base = tile * kEmitTile + threadIdx.x * kEmitItems;
+    // final labels of g (in place: exits and extrema keep their label)
+    for (int k = 0; k < kEmitItems; ++k) {
+      const int v = base + k;
+      if (v < F.G.n) {
+        F.Pup[v] = resolve_label(F.Pup, F.Lgu, v);
+        F.Pdn[v] = resolve_label(F.Pdn, F.Lgd, v);
+      }
+    }
     __syncthreads();
     if (threadIdx.x == 0) s = 0;
     __syncthreads();
@@ -665,11 +819,10 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_emit_write(GroupArgs<T> A) {
   const int* pre = A.prefix + K_EMIT * (A.nf + 1);
   __shared__ uint32_t ws[kThreads / 32];
-  MSZ_UNIT_LOOP(A, K_EMIT) {
-    const int fi = field_of_unit(pre, A.nf, u_);
+  auto active = [](const Field<T>& F) { return F.st->phase == PH_DONE && !F.st->emitted; };
+  MSZ_ACTIVE_UNITS(A, K_EMIT, pre, fi, active) {
     const Field<T>& F = A.fields[fi];
     DevState* st = F.st;
-    if (st->phase != PH_DONE || st->emitted) continue;
     const int tile = u_ - pre[fi];
     const int base = tile * kEmitTile + threadIdx.x * kEmitItems;
     const uint32_t m = emit_mask(F, base);
@@ -722,6 +875,6 @@ __global__ void __launch_bounds__(kThreads) k_scatter(T* dst, int n, const uint3
   }
 }
 
-#undef MSZ_UNIT_LOOP
+#undef MSZ_ACTIVE_UNITS
 
 }  // namespace msz

@@ -122,10 +122,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
+// try_wait that may suspend the thread for up to ~1 us while the phase is
+// incomplete (fewer polling instructions than a tight loop).
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait that also gives up as soon as *abort is set by another warp.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, const int* abort) {
   for (uint32_t i = 0; i < (1u << 24); ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_sleep(bar, parity)) return true;
     if ((i & 63u) == 63u && *(const volatile int*)abort) return false;
   }
   return false;
@@ -155,25 +168,26 @@ struct PlaneVals {
   T lllM[RPT], lllm[RPT];    // max / min of LLL
 };
 
-// Reads the thread's neighbourhood from a staged plane. 3D: rows y-1 .. y+2
-// (stage rows 2w .. 2w+3) at columns x-1, x, x+1 for the two vertices of
-// rows y = 2w, 2w+1 (tile-local).
+// Reads the thread's neighbourhood from a staged plane. 3D: rows y-1 .. y+RPT
+// (stage rows RPT*w .. RPT*w+RPT+1) at columns x-1, x, x+1 for the RPT
+// vertices of rows y = RPT*w .. RPT*w+RPT-1 (tile-local).
 template <class T, int ND>
 __device__ __forceinline__ PlaneVals<T, SweepGeom<T, ND>::RPT> plane_vals(const T* s, int tx, int w) {
   using SG = SweepGeom<T, ND>;
   PlaneVals<T, SG::RPT> P;
   const int c = tx + SG::PADX;
   if constexpr (ND == 3) {
-    const T* r0 = s + (2 * w) * SG::BX + c;  // row y-1
-    T a[4][3];
+    constexpr int R = SG::RPT;
+    const T* r0 = s + (R * w) * SG::BX + c;  // row y-1
+    T a[R + 2][3];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < R + 2; ++r) {
       a[r][0] = r0[r * SG::BX - 1];
       a[r][1] = r0[r * SG::BX];
       a[r][2] = r0[r * SG::BX + 1];
     }
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {  // vertex row = r k+1
+    for (int k = 0; k < R; ++k) {  // vertex row = r k+1
       P.a0[k] = a[k + 1][1];
       P.lurM[k] = vmax3(a[k + 1][2], a[k + 2][1], a[k + 2][2]);
       P.lurm[k] = vmin3(a[k + 1][2], a[k + 2][1], a[k + 2][2]);
