@@ -29,7 +29,11 @@
 namespace msz {
 
 enum : uint32_t { PH_INIT = 0, PH_FLABELS = 1, PH_C = 2, PH_R = 3, PH_DONE = 4, PH_ERR = 5 };
-enum : uint32_t { ACT_NONE = 0, ACT_MARK_C = 1, ACT_LABELS = 2, ACT_APPLY_R = 3 };
+// Actions within a phase. In PH_C, ACT_NONE means the field's first (full)
+// classification sweep is pending; afterwards a C round runs ACT_GATHER
+// (cases of the current type -> requests), ACT_MARK_C (apply) and
+// ACT_RECLASS (reclassify the closed 1-rings of the edited vertices).
+enum : uint32_t { ACT_NONE = 0, ACT_MARK_C = 1, ACT_LABELS = 2, ACT_APPLY_R = 3, ACT_GATHER = 4, ACT_RECLASS = 5 };
 enum : uint32_t { L_INIT = 0, L_EINIT = 1, L_JUMP = 2, L_DONE = 3 };
 enum : uint32_t { E_NONFINITE = 1, E_ARG = 2, E_BOUND = 4, E_TIMEOUT = 8 };
 
@@ -37,14 +41,14 @@ enum : uint32_t { E_NONFINITE = 1, E_ARG = 2, E_BOUND = 4, E_TIMEOUT = 8 };
 enum { K_DENSE = 0, K_SWEEP = 1, K_LABEL = 2, K_SPARSE = 3, K_EMIT = 4, NKIND = 5 };
 constexpr int kDenseChunk = 8192;  // vertices per dense unit
 constexpr int kEmitItems = 16;
-constexpr int kEmitTile = kThreads * kEmitItems;  // vertices per emission unit
+constexpr int kEmitTile = kThreads * kEmitItems;  // vertices per emission / case-gather unit
 
 // Per-field device state (one contiguous array per engine).
 struct DevState {
   uint32_t phase, action, T, lstate, ljob, units_done, err_bits;
   int32_t status;
-  uint32_t counts[4];
-  uint32_t ncase, ntouch;
+  uint32_t counts[4];  // false critical points of g per type (kept current by every classification)
+  uint32_t ntouch;  // entries of the touched list (apply, then reclassification)
   uint32_t acc_changed;
   uint32_t acc_ap[2];  // apply: decreases, freezes
   uint32_t acc_r[4];   // rcheck: wrong max, wrong min, asc troublemakers, desc troublemakers
@@ -75,7 +79,9 @@ struct Field {
   uint32_t* exu;  // bitmaps of tile-exit vertices (ascending, descending lines)
   uint32_t* exd;
   uint8_t* tdirty;  // label tiles whose terminals must be recomputed
-  uint32_t* cases;
+  uint8_t* cls;     // false-type bits of g per vertex (FPmax, FPmin, FNmax, FNmin), padded to kEmitTile
+  uint32_t* epoch;  // round in which a vertex was last reclassified (claims a vertex once per round)
+  uint32_t* ccnt;   // false critical points per kEmitTile-vertex tile and type: [tile][4]
   uint32_t* touched;
   uint32_t* tile_cnt;
   uint32_t* edit_idx;
@@ -125,6 +131,17 @@ __device__ __forceinline__ bool unit_done(DevState* st, int units) {
   return s_last;
 }
 
+// The same for n units of one field completed by the block at once.
+__device__ __forceinline__ bool units_done_n(DevState* st, uint32_t n, int units) {
+  __shared__ bool s_last_n;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last_n = atomicAdd(&st->units_done, n) + n == (uint32_t)units;
+  __syncthreads();
+  if (s_last_n) __threadfence();
+  return s_last_n;
+}
+
 template <int NW>
 __device__ __forceinline__ void block_add(uint32_t (&v)[NW], uint32_t* dst) {
   __shared__ uint32_t s[NW];
@@ -159,11 +176,15 @@ __device__ void ctrl_after_init(DevState* st) {
   st->ticks++;
 }
 
-// C-loop control after a sweep (Sec. 4.1): the next sub-loop with cases, the
-// end of a pass after FNmin, or the R-loop when a whole pass is clean.
-__device__ void ctrl_after_sweep(DevState* st) {
+// C-loop control after a classification of g (the full sweep or the
+// incremental one after an apply; Sec. 4.1): the next sub-loop type with
+// cases, the end of a pass after FNmin, or the R-loop when a whole pass is
+// clean. The type counts are those of the current g, so advancing the type
+// needs no new sweep.
+__device__ void ctrl_after_classify(DevState* st) {
   uint32_t c[4];
   for (int t = 0; t < 4; ++t) c[t] = vload(&st->counts[t]);
+  st->ntouch = 0;
   if (vload(&st->err_bits) & E_TIMEOUT) {
     st->phase = PH_ERR;
     st->status = MSZ_ERR_TIMEOUT;
@@ -173,7 +194,7 @@ __device__ void ctrl_after_sweep(DevState* st) {
   st->cnt.sweeps++;
   uint32_t T_ = st->T;
   for (;;) {
-    if (c[T_]) { st->action = ACT_MARK_C; break; }
+    if (c[T_]) { st->action = ACT_GATHER; break; }
     if (T_ < 3) { ++T_; continue; }
     st->cnt.c_passes++;
     if ((c[0] | c[1] | c[2] | c[3]) == 0) {
@@ -236,7 +257,7 @@ __device__ void ctrl_after_apply(DevState* st, uint32_t act) {
   if (act == ACT_MARK_C) {
     const uint32_t t = st->T;
     st->cnt.c_rounds[t]++;
-    st->cnt.c_cases[t] += st->counts[t];
+    st->cnt.c_cases[t] += st->counts[t];  // the cases of this round (counts are pre-apply)
   } else {
     st->cnt.r_rounds++;
     st->cnt.r_cases[0] += st->acc_r[2];
@@ -245,13 +266,13 @@ __device__ void ctrl_after_apply(DevState* st, uint32_t act) {
     st->T = 0;
   }
   st->rounds++;
+  // the touched list stays for the reclassification that follows
+  st->action = ACT_RECLASS;
   if (st->rounds > st->max_rounds) {
     st->phase = PH_ERR;
     st->status = MSZ_ERR_NOCONVERGE;
+    st->action = ACT_NONE;
   }
-  st->action = ACT_NONE;
-  st->ncase = st->ntouch = 0;
-  st->counts[0] = st->counts[1] = st->counts[2] = st->counts[3] = 0;
   st->acc_ap[0] = st->acc_ap[1] = 0;
   st->acc_r[2] = st->acc_r[3] = 0;
 }

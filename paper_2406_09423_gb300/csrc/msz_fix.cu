@@ -142,7 +142,9 @@ struct FieldBufs {
   uint32_t* exu = nullptr;
   uint32_t* exd = nullptr;
   uint8_t* tdirty = nullptr;
-  uint32_t* cases = nullptr;
+  uint8_t* cls = nullptr;
+  uint32_t* epoch = nullptr;
+  uint32_t* ccnt = nullptr;
   uint32_t* touched = nullptr;
   uint32_t* tile_cnt = nullptr;
   uint32_t* edit_idx = nullptr;
@@ -178,7 +180,9 @@ void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs
   B.exu = (uint32_t*)b.take(nw * 4);
   B.exd = (uint32_t*)b.take(nw * 4);
   B.tdirty = (uint8_t*)b.take((size_t)label_tiles(G));
-  B.cases = (uint32_t*)b.take(n * 4);
+  B.cls = (uint8_t*)b.take(nt * kEmitTile);
+  B.epoch = (uint32_t*)b.take(n * 4);
+  B.ccnt = (uint32_t*)b.take(nt * 4 * 4);
   B.touched = (uint32_t*)b.take(n * 4);
   B.tile_cnt = (uint32_t*)b.take(nt * 4);
   if (with_outputs) {
@@ -289,7 +293,9 @@ struct Group {
       F.exu = B.exu;
       F.exd = B.exd;
       F.tdirty = B.tdirty;
-      F.cases = B.cases;
+      F.cls = B.cls;
+      F.epoch = B.epoch;
+      F.ccnt = B.ccnt;
       F.touched = B.touched;
       F.tile_cnt = B.tile_cnt;
       F.edit_idx = B.edit_idx;
@@ -350,6 +356,7 @@ struct Group {
     return MSZ_OK;
   }
 
+  // csweep, gather_mark, label_tile, einit, jump x kJumpsPerStep, rcheck, apply, reclass
   int launches_per_step() const { return empty() ? 0 : 7 + kJumpsPerStep; }
 
   void init(cudaStream_t s) {
@@ -358,7 +365,7 @@ struct Group {
   }
 
   // Kernel-kind timing (single-field plans with MSZ_OPT_TIME_KERNELS):
-  // e = 8 events per step, see collect_times.
+  // e = kStepEvents events per step, see collect_times.
   void step(cudaStream_t s, cudaEvent_t* e) {
     if (empty()) return;
     if (e) cudaEventRecord(e[0], s);
@@ -366,7 +373,7 @@ struct Group {
     else k_csweep<T, ND, false><<<grid[K_SWEEP], SG::NT, 0, s>>>(args);
     if (e) cudaEventRecord(e[1], s);
     if (e) cudaEventRecord(e[6], s);
-    k_mark_c<T, ND><<<grid[K_SPARSE], kThreads, 0, s>>>(args);
+    k_gather_mark<T, ND><<<grid[K_EMIT], kThreads, 0, s>>>(args);
     if (e) cudaEventRecord(e[2], s);
     k_label_tile<T, ND><<<grid[K_LABEL], kThreads, label_smem, s>>>(args);
     k_einit<T><<<grid[K_DENSE], kThreads, 0, s>>>(args);
@@ -377,6 +384,8 @@ struct Group {
     if (e) cudaEventRecord(e[5], s);
     k_apply<T><<<grid[K_SPARSE], kThreads, 0, s>>>(args);
     if (e) cudaEventRecord(e[7], s);
+    k_reclass<T, ND><<<grid[K_SPARSE], kThreads, 0, s>>>(args);
+    if (e) cudaEventRecord(e[8], s);
   }
 
   void emit(cudaStream_t s) {
@@ -389,6 +398,7 @@ struct Group {
 
 constexpr int kMaxChunk = 32;
 constexpr int kKinds = 4;
+constexpr int kStepEvents = 9;
 constexpr int kGraphSteps = 4;
 
 }  // namespace
@@ -420,7 +430,7 @@ struct msz_engine_s {
   cudaGraphExec_t graph = nullptr;
   bool use_graph = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  cudaEvent_t tev[kMaxChunk][2 * kKinds] = {};
+  cudaEvent_t tev[kMaxChunk][kStepEvents] = {};
   bool tev_ready = false;
   double kernel_ms[kKinds] = {0, 0, 0, 0};
   uint64_t launches = 0;
@@ -516,7 +526,7 @@ void free_engine(msz_engine_s* E) {
   if (E->ev1) cudaEventDestroy(E->ev1);
   if (E->tev_ready)
     for (int i = 0; i < kMaxChunk; ++i)
-      for (int j = 0; j < 2 * kKinds; ++j) cudaEventDestroy(E->tev[i][j]);
+      for (int j = 0; j < kStepEvents; ++j) cudaEventDestroy(E->tev[i][j]);
   delete[] E->host_mem;
   delete E;
 }
@@ -629,14 +639,15 @@ void launch_steps(msz_engine_s* E, cudaStream_t s, int steps, bool timed) {
 
 void collect_times(msz_engine_s* E, int steps) {
   for (int i = 0; i < steps; ++i) {
-    float a = 0, b = 0, c = 0, d1 = 0, d2 = 0;
+    float a = 0, a2 = 0, b = 0, c = 0, d1 = 0, d2 = 0;
     cudaEvent_t* e = E->tev[i];
     cudaEventElapsedTime(&a, e[0], e[1]);
+    cudaEventElapsedTime(&a2, e[7], e[8]);
     cudaEventElapsedTime(&b, e[2], e[3]);
     cudaEventElapsedTime(&c, e[4], e[5]);
     cudaEventElapsedTime(&d1, e[6], e[2]);
     cudaEventElapsedTime(&d2, e[5], e[7]);
-    E->kernel_ms[0] += a;
+    E->kernel_ms[0] += a + a2;  // classification: full sweep + incremental
     E->kernel_ms[1] += b;
     E->kernel_ms[2] += c;
     E->kernel_ms[3] += d1 + d2;
@@ -685,7 +696,7 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
   const bool timed = (E->opt.flags & MSZ_OPT_TIME_KERNELS) != 0;
   if (timed && !E->tev_ready) {
     for (int i = 0; i < kMaxChunk; ++i)
-      for (int j = 0; j < 2 * kKinds; ++j) cudaEventCreate(&E->tev[i][j]);
+      for (int j = 0; j < kStepEvents; ++j) cudaEventCreate(&E->tev[i][j]);
     E->tev_ready = true;
   }
   for (int k = 0; k < kKinds; ++k) E->kernel_ms[k] = 0.0;

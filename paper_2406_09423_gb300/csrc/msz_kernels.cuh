@@ -92,6 +92,8 @@ __global__ void __launch_bounds__(kThreads) k_init(GroupArgs<T> A) {
       }
       F.g[v] = hv;
       F.flags[v] = 0;
+      F.cls[v] = 0;
+      F.epoch[v] = 0;
     }
     if (err) atomicOr(&st->err_bits, err);
     // tile-exit bitmaps start empty; every label tile starts dirty
@@ -103,6 +105,8 @@ __global__ void __launch_bounds__(kThreads) k_init(GroupArgs<T> A) {
       const int ntl = F.units[K_LABEL], nu = F.units[K_DENSE], lu = u_ - pre[i];
       const int per = (ntl + nu - 1) / nu;
       for (int t = lu * per + threadIdx.x; t < min(ntl, (lu + 1) * per); t += blockDim.x) F.tdirty[t] = 1;
+      const int ncc = 4 * F.units[K_EMIT], pc = (ncc + nu - 1) / nu;
+      for (int t = lu * pc + threadIdx.x; t < min(ncc, (lu + 1) * pc); t += blockDim.x) F.ccnt[t] = 0;
     }
     if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
       ctrl_after_init(st);
@@ -146,7 +150,9 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
   };
   auto next_tile = [&](Tile& t, int u) -> bool {
     int i = 0;
-    u = next_active_unit(A, pre, A.total[K_SWEEP], u, [](const Field<T>& F) { return F.st->phase == PH_C; }, i);
+    u = next_active_unit(
+        A, pre, A.total[K_SWEEP], u,
+        [](const Field<T>& F) { return F.st->phase == PH_C && F.st->action == ACT_NONE; }, i);
     if (u < A.total[K_SWEEP]) {
       const Field<T>& F = A.fields[i];
       const SweepTiling& TL = F.TL;
@@ -304,18 +310,26 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
                 const unsigned gmx = gk & 1u, gmn = (gk >> 4) & 1u, fmx = fk & 1u, fmn = (fk >> 4) & 1u;
                 bits = (gmx & ~fmx) | ((gmn & ~fmn) << 1) | ((fmx & ~gmx) << 2) | ((fmn & ~gmn) << 3);
               }
+              uint32_t bc[4];
 #pragma unroll
               for (int c = 0; c < 4; ++c) {
-                const uint32_t b = __ballot_sync(kFull, (bits >> c) & 1u);
-                if (lane == 0) cnt[c] += __popc(b);
+                bc[c] = __ballot_sync(kFull, (bits >> c) & 1u);
+                if (lane == 0) cnt[c] += __popc(bc[c]);
               }
-              const uint32_t mask = __ballot_sync(kFull, bits != 0);
-              if (mask) {
-                const int leader = __ffs(mask) - 1;
-                uint32_t b0 = 0;
-                if (lane == leader) b0 = atomicAdd(&st->ncase, (uint32_t)__popc(mask));
-                b0 = __shfl_sync(kFull, b0, leader);
-                if (bits) F.cases[b0 + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)(x + G.nx * (y + G.ny * z));
+              if (__any_sync(kFull, bits != 0)) {
+                // class bits of the false vertices (cls starts zeroed) and the
+                // per-tile type counts: one atomic per (tile, type) of the warp
+                const int v = x + G.nx * (y + G.ny * z);
+                if (bits) F.cls[v] = (uint8_t)bits;
+                const int ct = bits ? v / kEmitTile : -1;
+                const uint32_t grp = __match_any_sync(kFull, ct);
+                if (bits && lane == __ffs(grp) - 1) {
+#pragma unroll
+                  for (int c = 0; c < 4; ++c) {
+                    const uint32_t nc = __popc(bc[c] & grp);
+                    if (nc) atomicAdd(&F.ccnt[ct * 4 + c], nc);
+                  }
+                }
               }
             }
           }
@@ -341,7 +355,7 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
           __threadfence();
           if (atomicAdd(&st->units_done, 1u) == (uint32_t)(F.units[K_SWEEP] - 1)) {
             __threadfence();
-            ctrl_after_sweep(st);
+            ctrl_after_classify(st);
             st->units_done = 0;
           }
         }
@@ -357,28 +371,112 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
   }
 }
 
-// C-loop requests for the field's current type (Eqs. 2-5): FPmax and FNmin
-// edit the false vertex itself; FPmin and FNmax edit its neighbour that is
-// maximal in g, which is its steepest ascent since it is not a maximum of
-// g's ring. Units are slices of the case list.
+// C-loop requests for the field's current type (Eqs. 2-5), gathered from
+// the per-vertex false-type bits; only tiles that hold cases of the type are
+// read. FPmax and FNmin edit the false vertex itself; FPmin and FNmax edit
+// its neighbour that is maximal in g, which is its steepest ascent since it
+// is not a maximum of g's ring. Units are kEmitTile-vertex tiles; a block
+// reports its completed tiles of a field with one atomic.
 template <class T, int ND>
-__global__ void __launch_bounds__(kThreads) k_mark_c(GroupArgs<T> A) {
-  const int* pre = A.prefix + K_SPARSE * (A.nf + 1);
-  auto active = [](const Field<T>& F) { return F.st->action == ACT_MARK_C; };
-  MSZ_ACTIVE_UNITS(A, K_SPARSE, pre, i, active) {
+__global__ void __launch_bounds__(kThreads) k_gather_mark(GroupArgs<T> A) {
+  const int* pre = A.prefix + K_EMIT * (A.nf + 1);
+  auto active = [](const Field<T>& F) { return F.st->action == ACT_GATHER; };
+  int cur = -1;
+  uint32_t ndone = 0;
+  auto flush = [&]() {
+    if (cur >= 0 && units_done_n(A.fields[cur].st, ndone, A.fields[cur].units[K_EMIT]) && threadIdx.x == 0) {
+      DevState* st = A.fields[cur].st;
+      st->action = ACT_MARK_C;
+      st->ticks++;
+      st->units_done = 0;
+    }
+  };
+  MSZ_ACTIVE_UNITS(A, K_EMIT, pre, i, active) {
+    if (i != cur) {
+      flush();
+      cur = i;
+      ndone = 0;
+    }
     const Field<T>& F = A.fields[i];
-    DevState* st = F.st;
-    const uint32_t type = st->T, nc = st->ncase;
-    const int S = F.units[K_SPARSE], k = u_ - pre[i];
-    const uint32_t b = (uint32_t)(((uint64_t)nc * k) / S), e = (uint32_t)(((uint64_t)nc * (k + 1)) / S);
-    for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) {
-      const int v = (int)F.cases[j];
+    const uint32_t type = F.st->T;
+    const int tile = u_ - pre[i];
+    ++ndone;
+    if (F.ccnt[tile * 4 + type] == 0) continue;
+    const int base = tile * kEmitTile + threadIdx.x * kEmitItems;
+    const uint4 q = *reinterpret_cast<const uint4*>(F.cls + base);
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll 1
+    for (int k = 0; k < kEmitItems; ++k) {
+      const int v = base + k;
+      if (v >= F.G.n) break;  // padding of the last tile
+      if (!((w[k >> 2] >> (8 * (k & 3) + type)) & 1u)) continue;
       int x, y, z;
       coords(F.G, v, x, y, z);
       const uint8_t d = direction_of<T, ND>(F.g, F.G, v, x, y, z);
-      if (!((case_bits(d, F.fdir[v]) >> type) & 1u)) continue;
       const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny);
       request<T, ND>(F, v, t);
+    }
+  }
+  flush();
+}
+
+// Incremental classification after an apply. A vertex's false-type bits
+// depend only on g over its closed 1-ring, so only the closed 1-rings of the
+// vertices the apply touched can change: the result equals a full sweep of
+// the new g. Items are (touched vertex, ring slot) pairs; the first item to
+// reach a vertex in this round claims it (epoch stamp = round number) and
+// recomputes its bits with the direction test of the requests; the field and
+// tile type counts move by the difference. Units are slices of the items.
+template <class T, int ND>
+__global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
+  const int* pre = A.prefix + K_SPARSE * (A.nf + 1);
+  constexpr int NPOS = Slots<ND>::NPOS;
+  constexpr int R = 2 * NPOS + 1;
+  auto active = [](const Field<T>& F) { return F.st->action == ACT_RECLASS; };
+  MSZ_ACTIVE_UNITS(A, K_SPARSE, pre, i, active) {
+    const Field<T>& F = A.fields[i];
+    DevState* st = F.st;
+    const Geom G = F.G;
+    const uint32_t stamp = (uint32_t)st->rounds;
+    const uint64_t items = (uint64_t)st->ntouch * R;
+    const int S = F.units[K_SPARSE], k = u_ - pre[i];
+    const uint64_t b = items * (uint64_t)k / (uint64_t)S, e = items * (uint64_t)(k + 1) / (uint64_t)S;
+    uint32_t acc[4] = {0, 0, 0, 0};
+    for (uint64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
+      const int u = (int)F.touched[j / R];
+      const int s = (int)(j % R);
+      int x, y, z;
+      coords(G, u, x, y, z);
+      int v = u;
+      if (s < 2 * NPOS) {
+        const int sg = (s < NPOS) ? 1 : -1;
+        const int m = (int)((Slots<ND>::MASKS >> (4 * (s < NPOS ? s : s - NPOS))) & 7u);
+        const int dx = sg * (m & 1), dy = sg * ((m >> 1) & 1), dz = sg * ((m >> 2) & 1);
+        x += dx;
+        y += dy;
+        z += dz;
+        if (x < 0 || x >= G.nx || y < 0 || y >= G.ny || z < 0 || z >= G.nz) continue;
+        v = u + dx + dy * G.nx + dz * G.nxny;
+      }
+      if (atomicExch(&F.epoch[v], stamp) == stamp) continue;
+      const unsigned nb = case_bits(direction_of<T, ND>(F.g, G, v, x, y, z), F.fdir[v]);
+      const unsigned ob = F.cls[v];
+      if (nb != ob) {
+        F.cls[v] = (uint8_t)nb;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const uint32_t d = ((nb >> c) & 1u) - ((ob >> c) & 1u);  // +1, 0 or -1 (mod 2^32)
+          if (d) {
+            atomicAdd(&F.ccnt[(v / kEmitTile) * 4 + c], d);
+            acc[c] += d;
+          }
+        }
+      }
+    }
+    block_add<4>(acc, st->counts);
+    if (unit_done(st, S) && threadIdx.x == 0) {
+      ctrl_after_classify(st);
+      st->units_done = 0;
     }
   }
 }
