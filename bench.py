@@ -101,6 +101,32 @@ def peaks():
         return None
 
 
+def kernel_bytes(name, st, n, es):
+    """Algorithmic DRAM bytes of a kernel's working launches (element size es,
+    3D field of n vertices) from its work units, or None for the sparse
+    kernels whose traffic is dominated by scattered L2 accesses:
+    k_csweep      g (es) + f's direction byte per vertex swept;
+    k_label_tile  g (es) + direction byte + two tile terminals (8) per vertex
+                  of the tiles recomputed;
+    k_einit       the two exit bitmaps (n / 4 bytes) + terminal read and label
+                  write (8) per exit;
+    k_jump        the two exit bitmaps + label read, terminal and label
+                  gathers (12) per exit, per round;
+    k_rcheck      four label words (16) + two direction bytes per vertex."""
+    u, w = st["units"], st["work_launches"]
+    if name == "k_csweep":
+        return u * (es + 1)
+    if name == "k_label_tile":
+        return u * (es + 9)
+    if name == "k_einit":
+        return w * n / 4 + u * 8
+    if name == "k_jump":
+        return w * n / 4 + u * 12
+    if name == "k_rcheck":
+        return u * 18
+    return None
+
+
 def make_workload(torch, dev, size):
     from paper_2406_09423_gb300 import synth
 
@@ -462,30 +488,45 @@ def main():
                "h2d_bytes_per_step": h2d // steps_e2e, "d2h_bytes_per_step": d2h // steps_e2e,
                "wall_s": wall, "steps": steps_e2e, "api": "msz_fix_host (pinned host buffers)"}
 
-    # Roofline of the dominant kernel (the C-loop sweep): algorithmic bytes per
-    # launch = N * (4 B of g + 1 B of f's direction byte); duration = CUDA-event
-    # time of its launches on the fix stream / launches that swept, from a
-    # replay of the three timed fixes with per-kernel events (the timed region
-    # itself runs the graph-captured loop without events).
+    # Per-kernel device times from a replay of the three timed fixes on a plan
+    # with kernel timing: CUDA events around every launch, on the fix stream;
+    # a launch "works" when it completes a stage of the field's state machine.
+    # Algorithmic bytes of the working launches come from their work units
+    # (kernel_bytes); the roofline is that of the kernel with the most working
+    # time among those with an HBM byte count.
     tplan = msz.Plan(tuple(f.shape), f.dtype, time_kernels=True)
+    kstats = {}
     for rel, xi, fh in cases:
         r = tplan.fix(f, fh, xi, copy=False)
-        sweeps += r.counts["sweeps"]
         for key, val in r.kernel_ms.items():
             kernel_ms[key] = kernel_ms.get(key, 0.0) + val
+        for st in tplan.kernel_stats():
+            acc = kstats.setdefault(st["name"], {k: 0 for k in ("launches", "work_launches", "ms", "work_ms",
+                                                                 "units")})
+            for k in acc:
+                acc[k] += st[k]
     tplan.close()
     pk = peaks()
     peak_gbs = pk["hbm_gbs"] if pk else 6800.0
-    sweep_ms = kernel_ms.get("csweep", 0.0)
+    peak_src = "MEASURED_PEAKS.json hbm_gbs (measured)" if pk else "fallback 6.8 TB/s"
+    kernels = []
+    for name, st in kstats.items():
+        b = kernel_bytes(name, st, n, 4)
+        row = dict(st, name=name, algorithmic_bytes=b)
+        if b is not None and st["work_ms"] > 0:
+            row["achieved_gbs"] = b / (st["work_ms"] / 1e3) / 1e9
+            row["frac"] = row["achieved_gbs"] / peak_gbs
+        kernels.append(row)
     roofline = None
-    if sweep_ms > 0 and sweeps > 0:
-        bytes_per_launch = n * 5.0
-        avg_ms = sweep_ms / sweeps
-        ach = bytes_per_launch / (avg_ms / 1e3) / 1e9
-        roofline = {"bound": "hbm", "achieved": ach, "peak": peak_gbs, "unit": "GB/s", "frac": ach / peak_gbs,
-                    "traffic": None, "kernel": "k_csweep<float,3,TMA>",
-                    "avg_launch_ms": avg_ms, "bytes_per_launch": bytes_per_launch,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if pk else "fallback 6.8 TB/s"}
+    hbm_rows = [k for k in kernels if "achieved_gbs" in k]
+    if hbm_rows:
+        top = max(hbm_rows, key=lambda k: k["work_ms"])
+        avg_ms = top["work_ms"] / top["work_launches"]
+        roofline = {"bound": "hbm", "achieved": top["achieved_gbs"], "peak": peak_gbs, "unit": "GB/s",
+                    "frac": top["frac"], "traffic": None, "kernel": top["name"],
+                    "avg_launch_ms": avg_ms, "bytes_per_launch": top["algorithmic_bytes"] / top["work_launches"],
+                    "work_launches": top["work_launches"], "peak_source": peak_src,
+                    "share_of_kernel_time": top["ms"] / sum(k["ms"] for k in kernels)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -525,7 +566,7 @@ def main():
             "cpu_baseline": cpu,
             "latency_ms": {"p50": p50, "p99": p99}, "per_xi": per_xi,
             "step_mvps": {"min": step_rates[0], "max": step_rates[-1]},
-            "kernel_ms": kernel_ms,
+            "kernel_ms": kernel_ms, "kernels": kernels,
             "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)

@@ -112,6 +112,30 @@ int64_t msz_plan_bytes(int ndim, const int64_t dims[3], int dtype);
 
 int msz_plan_destroy(msz_plan p);
 
+/* Per-kernel statistics of the last msz_fix on a plan created with
+ * MSZ_OPT_TIME_KERNELS (no counterpart in the paper: instrumentation). Every
+ * launch of a loop step is bracketed by CUDA events; a launch "works" when it
+ * completes a stage of the field's state machine (the others find the field
+ * in another stage and return at once). units counts the work of the working
+ * launches: vertices (k_csweep, k_rcheck, k_label_tile: vertices of the tiles
+ * recomputed), tile exits visited (k_einit, k_jump), cases (k_gather_mark),
+ * touched vertices (k_apply), ring items (k_reclass). */
+#define MSZ_NUM_KERNELS 8
+typedef struct {
+  const char* name;        /* kernel name, static string */
+  uint64_t launches;       /* launches inside the loop's steps */
+  uint64_t work_launches;  /* of which did work for the field */
+  double ms;               /* device time of all launches */
+  double work_ms;          /* device time of the working launches */
+  uint64_t units;          /* work units of the working launches (see above) */
+} msz_kernel_stat;
+
+/* Fills out[0 .. min(n, MSZ_NUM_KERNELS) - 1] in step order (k_csweep,
+ * k_gather_mark, k_label_tile, k_einit, k_jump, k_rcheck, k_apply, k_reclass);
+ * returns the number filled, or MSZ_ERR_ARG (no plan / out, or a plan made
+ * without MSZ_OPT_TIME_KERNELS). Host memory only. */
+int msz_plan_kernel_stats(msz_plan p, msz_kernel_stat* out, int n);
+
 /* The correction loop (Sec. 4, Fig. 3 top): given the original field f and
  * the decompressed field fhat (device, N values of the plan's type) and the
  * bound xi, runs C-loops and R-loops until no false critical point and no

@@ -192,6 +192,11 @@ class Plan:
             native.check(r.status, "msz_fix")
         return _result(torch, r, self.shape, f.dtype, copy)
 
+    def kernel_stats(self) -> list[dict]:
+        """Per-kernel launches, device times and work units of the last fix
+        (plans made with time_kernels=True; msz_plan_kernel_stats)."""
+        return native.msz_plan_kernel_stats(self._p)
+
     def close(self):
         if self._p:
             native.msz_plan_destroy(self._p)

@@ -38,10 +38,14 @@ enum : uint32_t { L_INIT = 0, L_EINIT = 1, L_JUMP = 2, L_DONE = 3 };
 enum : uint32_t { E_NONFINITE = 1, E_ARG = 2, E_BOUND = 4, E_TIMEOUT = 8 };
 
 // Work-unit kinds.
-enum { K_DENSE = 0, K_SWEEP = 1, K_LABEL = 2, K_SPARSE = 3, K_EMIT = 4, NKIND = 5 };
+enum { K_DENSE = 0, K_SWEEP = 1, K_LABEL = 2, K_SPARSE = 3, K_EMIT = 4, K_CASE = 5, NKIND = 6 };
 constexpr int kDenseChunk = 8192;  // vertices per dense unit
 constexpr int kEmitItems = 16;
-constexpr int kEmitTile = kThreads * kEmitItems;  // vertices per emission / case-gather unit
+constexpr int kEmitTile = kThreads * kEmitItems;  // vertices per emission unit and per case-count tile
+constexpr int kCaseTiles = kThreads / 32;          // case-count tiles per gather unit (one per warp)
+
+// Kernels of a loop step, in launch order of their kinds (per-kernel timing).
+enum { KID_SWEEP = 0, KID_GATHER, KID_LABEL, KID_EINIT, KID_JUMP, KID_RCHECK, KID_APPLY, KID_RECLASS, NKID };
 
 // Per-field device state (one contiguous array per engine).
 struct DevState {
@@ -56,6 +60,7 @@ struct DevState {
   uint32_t f_resolved, pad1;  // f's labels resolved in place (first R-check)
   uint64_t rounds, max_rounds, n_edits;
   uint64_t ticks;  // advanced by every state transition (stall detection)
+  uint64_t kunits[NKID];  // work units per kernel (kernel timing runs only)
   msz_counts cnt;
 };
 
@@ -101,6 +106,10 @@ struct GroupArgs {
   const CUtensorMap* maps;  // [2 * nf]: g (halo box, NaN fill), f's direction bytes
   int nf;
   int total[NKIND];
+  // Kernel timing runs only (null otherwise): the launch's step and slot; the
+  // block completing a field's work sets bit `slot` of steplog[step].
+  uint32_t* steplog;
+  int step, slot;
 };
 
 // ---------------------------------------------------------------------------
@@ -117,6 +126,25 @@ __device__ __forceinline__ int field_of_unit(const int* pre, int nf, int u) {
     else hi = mid;
   }
   return lo;
+}
+
+// Kernel timing runs: this launch did work (moved a field's state machine),
+// and the work units it processed.
+template <class T>
+__device__ __forceinline__ void log_work(const GroupArgs<T>& A) {
+  if (A.steplog) atomicOr(&A.steplog[A.step], 1u << A.slot);
+}
+template <class T>
+__device__ __forceinline__ void log_units(const GroupArgs<T>& A, DevState* st, int kid, uint64_t n) {
+  if (A.steplog && n) atomicAdd((unsigned long long*)&st->kunits[kid], (unsigned long long)n);
+}
+
+// The same summed over a warp (every lane calls it).
+template <class T>
+__device__ __forceinline__ void log_units_warp(const GroupArgs<T>& A, DevState* st, int kid, uint32_t n) {
+  if (!A.steplog) return;
+  n = __reduce_add_sync(kFull, n);
+  if ((threadIdx.x & 31) == 0 && n) atomicAdd((unsigned long long*)&st->kunits[kid], (unsigned long long)n);
 }
 
 // Completion of one unit of a field by the whole block: true in the block
@@ -281,15 +309,24 @@ __device__ void ctrl_after_apply(DevState* st, uint32_t act) {
 // Edit requests (Sec. 5.1 deterministic mode): idempotent flags collected
 // from one snapshot of g, applied afterwards; a freeze overrides a decrease.
 // ---------------------------------------------------------------------------
+// Slot in a list whose length counter is *ctr: one atomic per group of
+// lanes that arrive together (the field is the same for all of them).
+__device__ __forceinline__ uint32_t list_slot(uint32_t* ctr) {
+  const uint32_t active = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(active) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(ctr, (uint32_t)__popc(active));
+  base = __shfl_sync(active, base, leader);
+  return base + (uint32_t)__popc(active & ((1u << lane) - 1u));
+}
+
 template <class T>
 __device__ __forceinline__ void mark(const Field<T>& F, int u, uint8_t bit) {
   uint32_t* w = reinterpret_cast<uint32_t*>(F.flags) + (u >> 2);
   const int sh = (u & 3) * 8;
   const uint32_t old = atomicOr(w, (uint32_t)bit << sh);
-  if (((old >> sh) & (FL_DEC | FL_FREEZE)) == 0) {
-    const uint32_t k = atomicAdd(&F.st->ntouch, 1u);
-    F.touched[k] = (uint32_t)u;
-  }
+  if (((old >> sh) & (FL_DEC | FL_FREEZE)) == 0) F.touched[list_slot(&F.st->ntouch)] = (uint32_t)u;
 }
 
 // A false case anchored at a asks for a decreasing edit of t. If t is frozen

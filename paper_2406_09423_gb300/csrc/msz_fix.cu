@@ -197,6 +197,15 @@ void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs
 // One (dtype, dimension) group of an engine's fields.
 // ---------------------------------------------------------------------------
 constexpr int kJumpsPerStep = 4;
+constexpr int kStepSlots = 7 + kJumpsPerStep;  // launches per step
+constexpr int kStepEvents = kStepSlots + 1;
+// kernel of each launch slot of a step
+constexpr int kSlotKernel[kStepSlots] = {KID_SWEEP, KID_GATHER, KID_LABEL, KID_EINIT, KID_JUMP, KID_JUMP,
+                                         KID_JUMP,  KID_JUMP,   KID_RCHECK, KID_APPLY, KID_RECLASS};
+static_assert(kJumpsPerStep == 4, "slot table assumes four jump launches per step");
+static_assert(NKID == MSZ_NUM_KERNELS, "kernel table and ABI disagree");
+const char* const kKernelNames[NKID] = {"k_csweep", "k_gather_mark", "k_label_tile", "k_einit",
+                                        "k_jump",   "k_rcheck",      "k_apply",      "k_reclass"};
 
 template <class T, int ND>
 struct Group {
@@ -308,6 +317,7 @@ struct Group {
       F.units[K_LABEL] = label_tiles(G);
       F.units[K_SPARSE] = std::max(1, std::min(1024, (G.n + 65535) / 65536));
       F.units[K_EMIT] = emit_tiles(G);
+      F.units[K_CASE] = (emit_tiles(G) + kCaseTiles - 1) / kCaseTiles;
       if (tma && !encode(&h_maps[2 * j], G, B.g, B.fdir)) tma = false;
     }
     for (int k = 0; k < NKIND; ++k)
@@ -328,6 +338,7 @@ struct Group {
     grid[K_DENSE] = occ_grid((const void*)k_jump<T>, kThreads, 0, args.total[K_DENSE]);
     grid[K_SPARSE] = occ_grid((const void*)k_apply<T>, kThreads, 0, args.total[K_SPARSE]);
     grid[K_EMIT] = occ_grid((const void*)k_emit_write<T>, kThreads, 0, args.total[K_EMIT]);
+    grid[K_CASE] = occ_grid((const void*)k_gather_mark<T, ND>, kThreads, 0, args.total[K_CASE]);
     grid[K_SWEEP] = tma ? occ_grid((const void*)k_csweep<T, ND, true>, SG::NTP, 0, args.total[K_SWEEP])
                         : occ_grid((const void*)k_csweep<T, ND, false>, SG::NT, 0, args.total[K_SWEEP]);
     label_smem = label_smem_bytes<T, ND>();
@@ -357,35 +368,40 @@ struct Group {
   }
 
   // csweep, gather_mark, label_tile, einit, jump x kJumpsPerStep, rcheck, apply, reclass
-  int launches_per_step() const { return empty() ? 0 : 7 + kJumpsPerStep; }
+  int launches_per_step() const { return empty() ? 0 : kStepSlots; }
 
   void init(cudaStream_t s) {
     if (empty()) return;
     k_init<T><<<grid[K_DENSE], kThreads, 0, s>>>(args);
   }
 
-  // Kernel-kind timing (single-field plans with MSZ_OPT_TIME_KERNELS):
-  // e = kStepEvents events per step, see collect_times.
-  void step(cudaStream_t s, cudaEvent_t* e) {
+  // One loop step. Kernel timing (single-field plans with
+  // MSZ_OPT_TIME_KERNELS): e holds kStepEvents events, one before each launch
+  // and one after the last; each launch gets the step's log slot.
+  void step(cudaStream_t s, cudaEvent_t* e = nullptr, uint32_t* steplog = nullptr, int si = 0) {
     if (empty()) return;
-    if (e) cudaEventRecord(e[0], s);
-    if (tma) k_csweep<T, ND, true><<<grid[K_SWEEP], SG::NTP, 0, s>>>(args);
-    else k_csweep<T, ND, false><<<grid[K_SWEEP], SG::NT, 0, s>>>(args);
-    if (e) cudaEventRecord(e[1], s);
-    if (e) cudaEventRecord(e[6], s);
-    k_gather_mark<T, ND><<<grid[K_EMIT], kThreads, 0, s>>>(args);
-    if (e) cudaEventRecord(e[2], s);
-    k_label_tile<T, ND><<<grid[K_LABEL], kThreads, label_smem, s>>>(args);
-    k_einit<T><<<grid[K_DENSE], kThreads, 0, s>>>(args);
-    for (int j = 0; j < kJumpsPerStep; ++j) k_jump<T><<<grid[K_DENSE], kThreads, 0, s>>>(args);
-    if (e) cudaEventRecord(e[3], s);
-    if (e) cudaEventRecord(e[4], s);
-    k_rcheck<T, ND><<<grid[K_DENSE], kThreads, 0, s>>>(args);
-    if (e) cudaEventRecord(e[5], s);
-    k_apply<T><<<grid[K_SPARSE], kThreads, 0, s>>>(args);
-    if (e) cudaEventRecord(e[7], s);
-    k_reclass<T, ND><<<grid[K_SPARSE], kThreads, 0, s>>>(args);
-    if (e) cudaEventRecord(e[8], s);
+    int slot = 0;
+    auto a = [&]() {
+      GroupArgs<T> x = args;
+      if (e) {
+        cudaEventRecord(e[slot], s);
+        x.steplog = steplog;
+        x.step = si;
+        x.slot = slot;
+      }
+      ++slot;
+      return x;
+    };
+    if (tma) k_csweep<T, ND, true><<<grid[K_SWEEP], SG::NTP, 0, s>>>(a());
+    else k_csweep<T, ND, false><<<grid[K_SWEEP], SG::NT, 0, s>>>(a());
+    k_gather_mark<T, ND><<<grid[K_CASE], kThreads, 0, s>>>(a());
+    k_label_tile<T, ND><<<grid[K_LABEL], kThreads, label_smem, s>>>(a());
+    k_einit<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
+    for (int j = 0; j < kJumpsPerStep; ++j) k_jump<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
+    k_rcheck<T, ND><<<grid[K_DENSE], kThreads, 0, s>>>(a());
+    k_apply<T><<<grid[K_SPARSE], kThreads, 0, s>>>(a());
+    k_reclass<T, ND><<<grid[K_SPARSE], kThreads, 0, s>>>(a());
+    if (e) cudaEventRecord(e[slot], s);
   }
 
   void emit(cudaStream_t s) {
@@ -398,7 +414,7 @@ struct Group {
 
 constexpr int kMaxChunk = 32;
 constexpr int kKinds = 4;
-constexpr int kStepEvents = 9;
+
 constexpr int kGraphSteps = 4;
 
 }  // namespace
@@ -433,6 +449,11 @@ struct msz_engine_s {
   cudaEvent_t tev[kMaxChunk][kStepEvents] = {};
   bool tev_ready = false;
   double kernel_ms[kKinds] = {0, 0, 0, 0};
+  // per-kernel statistics of the last timed run (single-field engines)
+  uint32_t* d_steplog = nullptr;
+  uint32_t h_steplog[kMaxChunk] = {};
+  uint64_t ks_launches[NKID] = {}, ks_work[NKID] = {}, ks_units[NKID] = {};
+  double ks_ms[NKID] = {}, ks_work_ms[NKID] = {};
   uint64_t launches = 0;
   // staging for msz_fix_host
   void* in_f = nullptr;
@@ -472,6 +493,7 @@ size_t layout_engine(msz_engine_s* E, unsigned char* base, bool with_outputs) {
     carve_field(b, E->geoms[i], E->dtypes[i], with_outputs, base ? E->bufs[i] : tmp);
   }
   E->d_states = (DevState*)b.take(sizeof(DevState) * E->nf, 256);
+  E->d_steplog = (uint32_t*)b.take(sizeof(uint32_t) * kMaxChunk, 256);
   E->each_group([&](auto& g) { g.carve(b); });
   return b.off;
 }
@@ -632,25 +654,31 @@ int64_t engine_bytes(int nf, const int* ndim, const int64_t* dims, const int* dt
 void launch_steps(msz_engine_s* E, cudaStream_t s, int steps, bool timed) {
   for (int i = 0; i < steps; ++i) {
     cudaEvent_t* e = timed ? E->tev[i] : nullptr;
-    E->each_group([&](auto& g) { g.step(s, e); });
+    E->each_group([&](auto& g) { g.step(s, e, E->d_steplog, i); });
   }
   E->launches += (uint64_t)steps * E->launches_per_step();
 }
 
+// Per-launch device times of a timed chunk, split into launches that did work
+// for the field (bit set in the step log) and the rest.
 void collect_times(msz_engine_s* E, int steps) {
   for (int i = 0; i < steps; ++i) {
-    float a = 0, a2 = 0, b = 0, c = 0, d1 = 0, d2 = 0;
     cudaEvent_t* e = E->tev[i];
-    cudaEventElapsedTime(&a, e[0], e[1]);
-    cudaEventElapsedTime(&a2, e[7], e[8]);
-    cudaEventElapsedTime(&b, e[2], e[3]);
-    cudaEventElapsedTime(&c, e[4], e[5]);
-    cudaEventElapsedTime(&d1, e[6], e[2]);
-    cudaEventElapsedTime(&d2, e[5], e[7]);
-    E->kernel_ms[0] += a + a2;  // classification: full sweep + incremental
-    E->kernel_ms[1] += b;
-    E->kernel_ms[2] += c;
-    E->kernel_ms[3] += d1 + d2;
+    for (int k = 0; k < kStepSlots; ++k) {
+      float dt = 0.f;
+      cudaEventElapsedTime(&dt, e[k], e[k + 1]);
+      const int kid = kSlotKernel[k];
+      E->ks_launches[kid]++;
+      E->ks_ms[kid] += dt;
+      if ((E->h_steplog[i] >> k) & 1u) {
+        E->ks_work[kid]++;
+        E->ks_work_ms[kid] += dt;
+      }
+      const int kind = (kid == KID_SWEEP || kid == KID_RECLASS) ? 0
+                       : (kid == KID_LABEL || kid == KID_EINIT || kid == KID_JUMP) ? 1
+                       : (kid == KID_RCHECK) ? 2 : 3;
+      E->kernel_ms[kind] += dt;
+    }
   }
 }
 
@@ -700,6 +728,11 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
     E->tev_ready = true;
   }
   for (int k = 0; k < kKinds; ++k) E->kernel_ms[k] = 0.0;
+  for (int k = 0; k < NKID; ++k) {
+    E->ks_launches[k] = E->ks_work[k] = E->ks_units[k] = 0;
+    E->ks_ms[k] = E->ks_work_ms[k] = 0.0;
+  }
+  if (timed && cudaMemsetAsync(E->d_steplog, 0, sizeof(uint32_t) * kMaxChunk, s) != cudaSuccess) return MSZ_ERR_CUDA;
   const bool graph = E->use_graph && !timed && ensure_graph(E) == MSZ_OK;
   // Steps in growing chunks; one state read per chunk. A chunk in which no
   // field's state machine moved means a stall.
@@ -713,6 +746,10 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
       launch_steps(E, s, std::min(chunk * kGraphSteps, kMaxChunk), timed);
     }
     if (cudaMemcpyAsync(H, E->d_states, sizeof(DevState) * nf, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return MSZ_ERR_CUDA;
+    if (timed && (cudaMemcpyAsync(E->h_steplog, E->d_steplog, sizeof(uint32_t) * kMaxChunk, cudaMemcpyDeviceToHost,
+                                  s) != cudaSuccess ||
+                  cudaMemsetAsync(E->d_steplog, 0, sizeof(uint32_t) * kMaxChunk, s) != cudaSuccess))
       return MSZ_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return MSZ_ERR_CUDA;
     if (timed) collect_times(E, std::min(chunk * kGraphSteps, kMaxChunk));
@@ -744,6 +781,11 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
     return MSZ_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return MSZ_ERR_CUDA;
   if (cudaGetLastError() != cudaSuccess) return MSZ_ERR_CUDA;
+  if (timed && nf == 1) {
+    for (int k = 0; k < NKID; ++k) E->ks_units[k] = H[0].kunits[k];
+    E->ks_units[KID_SWEEP] = (uint64_t)E->geoms[0].n * E->ks_work[KID_SWEEP];
+    E->ks_units[KID_RCHECK] = (uint64_t)E->geoms[0].n * E->ks_work[KID_RCHECK];
+  }
   float ms = 0.f;
   if (E->ev0 && E->ev1 && cudaEventElapsedTime(&ms, E->ev0, E->ev1) != cudaSuccess) ms = 0.f;
   int worst = MSZ_OK;
@@ -809,6 +851,21 @@ int msz_plan_destroy(msz_plan p) {
   free_engine(p->E);
   delete p;
   return MSZ_OK;
+}
+
+int msz_plan_kernel_stats(msz_plan p, msz_kernel_stat* out, int n) {
+  if (!p || !out || n < 0 || !(p->E->opt.flags & MSZ_OPT_TIME_KERNELS)) return MSZ_ERR_ARG;
+  const msz_engine_s* E = p->E;
+  const int m = std::min(n, (int)NKID);
+  for (int k = 0; k < m; ++k) {
+    out[k].name = kKernelNames[k];
+    out[k].launches = E->ks_launches[k];
+    out[k].work_launches = E->ks_work[k];
+    out[k].ms = E->ks_ms[k];
+    out[k].work_ms = E->ks_work_ms[k];
+    out[k].units = E->ks_units[k];
+  }
+  return m;
 }
 
 int msz_fix(msz_plan p, const void* orig_dev, const void* decomp_dev, double xi, void* stream, msz_result* out) {

@@ -356,6 +356,7 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
           if (atomicAdd(&st->units_done, 1u) == (uint32_t)(F.units[K_SWEEP] - 1)) {
             __threadfence();
             ctrl_after_classify(st);
+            log_work(A);
             st->units_done = 0;
           }
         }
@@ -375,46 +376,55 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
 // the per-vertex false-type bits; only tiles that hold cases of the type are
 // read. FPmax and FNmin edit the false vertex itself; FPmin and FNmax edit
 // its neighbour that is maximal in g, which is its steepest ascent since it
-// is not a maximum of g's ring. Units are kEmitTile-vertex tiles; a block
-// reports its completed tiles of a field with one atomic.
+// is not a maximum of g's ring. A unit is kCaseTiles case-count tiles, one
+// per warp; a block reports its completed units of a field with one atomic.
 template <class T, int ND>
 __global__ void __launch_bounds__(kThreads) k_gather_mark(GroupArgs<T> A) {
-  const int* pre = A.prefix + K_EMIT * (A.nf + 1);
+  const int* pre = A.prefix + K_CASE * (A.nf + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto active = [](const Field<T>& F) { return F.st->action == ACT_GATHER; };
   int cur = -1;
-  uint32_t ndone = 0;
+  uint32_t ndone = 0, ncases = 0;
   auto flush = [&]() {
-    if (cur >= 0 && units_done_n(A.fields[cur].st, ndone, A.fields[cur].units[K_EMIT]) && threadIdx.x == 0) {
+    if (cur >= 0) log_units_warp(A, A.fields[cur].st, KID_GATHER, ncases);
+    ncases = 0;
+    if (cur >= 0 && units_done_n(A.fields[cur].st, ndone, A.fields[cur].units[K_CASE]) && threadIdx.x == 0) {
       DevState* st = A.fields[cur].st;
       st->action = ACT_MARK_C;
       st->ticks++;
+      log_work(A);
       st->units_done = 0;
     }
   };
-  MSZ_ACTIVE_UNITS(A, K_EMIT, pre, i, active) {
+  MSZ_ACTIVE_UNITS(A, K_CASE, pre, i, active) {
     if (i != cur) {
       flush();
       cur = i;
       ndone = 0;
     }
+    ++ndone;
     const Field<T>& F = A.fields[i];
     const uint32_t type = F.st->T;
-    const int tile = u_ - pre[i];
-    ++ndone;
-    if (F.ccnt[tile * 4 + type] == 0) continue;
-    const int base = tile * kEmitTile + threadIdx.x * kEmitItems;
-    const uint4 q = *reinterpret_cast<const uint4*>(F.cls + base);
-    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+    const int tile = (u_ - pre[i]) * kCaseTiles + warp;
+    if (tile * kEmitTile >= F.G.n || F.ccnt[tile * 4 + type] == 0) continue;
 #pragma unroll 1
-    for (int k = 0; k < kEmitItems; ++k) {
-      const int v = base + k;
-      if (v >= F.G.n) break;  // padding of the last tile
-      if (!((w[k >> 2] >> (8 * (k & 3) + type)) & 1u)) continue;
-      int x, y, z;
-      coords(F.G, v, x, y, z);
-      const uint8_t d = direction_of<T, ND>(F.g, F.G, v, x, y, z);
-      const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny);
-      request<T, ND>(F, v, t);
+    for (int r = 0; r < kEmitTile / (32 * 16); ++r) {
+      const int base = tile * kEmitTile + (r * 32 + lane) * 16;
+      const uint4 q = *reinterpret_cast<const uint4*>(F.cls + base);
+      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+      uint32_t hits = 0;  // bit k: byte k holds a case of the type
+#pragma unroll
+      for (int k = 0; k < 16; ++k) hits |= ((w[k >> 2] >> (8 * (k & 3) + type)) & 1u) << k;
+      if (F.G.n - base < 16) hits &= (F.G.n - base > 0) ? (1u << (F.G.n - base)) - 1u : 0u;  // padding
+      ncases += __popc(hits);
+      for (; hits; hits &= hits - 1) {
+        const int v = base + __ffs(hits) - 1;
+        int x, y, z;
+        coords(F.G, v, x, y, z);
+        const uint8_t d = direction_of<T, ND>(F.g, F.G, v, x, y, z);
+        const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny);
+        request<T, ND>(F, v, t);
+      }
     }
   }
   flush();
@@ -441,6 +451,7 @@ __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
     const uint64_t items = (uint64_t)st->ntouch * R;
     const int S = F.units[K_SPARSE], k = u_ - pre[i];
     const uint64_t b = items * (uint64_t)k / (uint64_t)S, e = items * (uint64_t)(k + 1) / (uint64_t)S;
+    if (threadIdx.x == 0) log_units(A, st, KID_RECLASS, e - b);
     uint32_t acc[4] = {0, 0, 0, 0};
     for (uint64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
       const int u = (int)F.touched[j / R];
@@ -476,6 +487,7 @@ __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
     block_add<4>(acc, st->counts);
     if (unit_done(st, S) && threadIdx.x == 0) {
       ctrl_after_classify(st);
+      log_work(A);
       st->units_done = 0;
     }
   }
@@ -530,6 +542,7 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(GroupArgs<T> A) {
       if (unit_done(st, F.units[K_LABEL]) && threadIdx.x == 0) {
         st->lstate = L_EINIT;
         st->ticks++;
+        log_work(A);
         st->units_done = 0;
       }
       continue;
@@ -625,9 +638,13 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(GroupArgs<T> A) {
     }
     __syncthreads();
     if (job && threadIdx.x == 0) F.tdirty[tile] = 0;  // f's pass leaves every tile dirty for g's first
+    if (threadIdx.x == 0)
+      log_units(A, st, KID_LABEL,
+                (uint64_t)min(LG::TX, G.nx - x0) * min(LG::TY, G.ny - y0) * min(LG::TZ, G.nz - z0));
     if (unit_done(st, F.units[K_LABEL]) && threadIdx.x == 0) {
       st->lstate = L_EINIT;
       st->ticks++;
+      log_work(A);
       st->units_done = 0;
     }
   }
@@ -651,18 +668,23 @@ __global__ void __launch_bounds__(kThreads) k_einit(GroupArgs<T> A) {
     int32_t* LB = job ? F.Lgd : F.Lfd;
     const int v0 = (u_ - pre[i]) * kDenseChunk;
     const int v1 = min(F.G.n, v0 + kDenseChunk);
+    uint32_t nex = 0;
     for (int w = (v0 >> 5) + threadIdx.x; w < ((v1 + 31) >> 5); w += blockDim.x) {
       for (uint32_t m = F.exu[w]; m; m &= m - 1) {
         const int e = (w << 5) + __ffs(m) - 1;
         LA[e] = TA[e];
+        ++nex;
       }
       for (uint32_t m = F.exd[w]; m; m &= m - 1) {
         const int e = (w << 5) + __ffs(m) - 1;
         LB[e] = TB[e];
+        ++nex;
       }
     }
+    log_units_warp(A, st, KID_EINIT, nex);
     if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
       st->lstate = L_JUMP;
+      log_work(A);
       st->jump_rounds = 0;
       st->ticks++;
       st->units_done = 0;
@@ -684,8 +706,9 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
     int32_t* LB = job ? F.Lgd : F.Lfd;
     const int v0 = (u_ - pre[i]) * kDenseChunk;
     const int v1 = min(F.G.n, v0 + kDenseChunk);
-    uint32_t changed[1] = {0};
+    uint32_t changed[1] = {0}, nex = 0;
     for (int w = (v0 >> 5) + threadIdx.x; w < ((v1 + 31) >> 5); w += blockDim.x) {
+      if (A.steplog) nex += __popc(F.exu[w]) + __popc(F.exd[w]);
       for (uint32_t m = F.exu[w]; m; m &= m - 1) {
         const int e = (w << 5) + __ffs(m) - 1;
         const int x = LA[e];
@@ -703,9 +726,11 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
         }
       }
     }
+    log_units_warp(A, st, KID_JUMP, nex);
     block_add<1>(changed, &st->acc_changed);
     if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
       ctrl_after_jump(st);
+      log_work(A);
       st->units_done = 0;
     }
   }
@@ -767,6 +792,7 @@ __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
     block_add<4>(acc, st->acc_r);
     if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
       ctrl_after_rcheck(st);
+      log_work(A);
       st->units_done = 0;
     }
   }
@@ -785,6 +811,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
     const uint32_t nt = st->ntouch;
     const int S = F.units[K_SPARSE], k = u_ - pre[i];
     const uint32_t b = (uint32_t)(((uint64_t)nt * k) / S), e = (uint32_t)(((uint64_t)nt * (k + 1)) / S);
+    if (threadIdx.x == 0) log_units(A, st, KID_APPLY, e - b);
     uint32_t acc[2] = {0, 0};
     for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) {
       const int u = (int)F.touched[j];
@@ -805,6 +832,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
     block_add<2>(acc, st->acc_ap);
     if (unit_done(st, S) && threadIdx.x == 0) {
       ctrl_after_apply(st, act);
+      log_work(A);
       st->units_done = 0;
     }
   }

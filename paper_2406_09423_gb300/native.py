@@ -17,7 +17,10 @@ LIB_PATH = os.path.join(HERE, "_build", "libmsz.so")
 MSZ_F32, MSZ_F64 = 0, 1
 MSZ_OPT_NO_TMA = 1
 MSZ_OPT_TIME_KERNELS = 2
-KERNEL_KINDS = ("csweep", "labels", "rcheck", "mark_apply")
+# msz_result.kernel_ms: classification (full sweep + incremental), labels
+# (tile terminals + exit jumping), R-loop check, requests + apply
+KERNEL_KINDS = ("classify", "labels", "rcheck", "mark_apply")
+MSZ_NUM_KERNELS = 8
 STATUS = {
     0: "MSZ_OK", -1: "MSZ_ERR_ARG", -2: "MSZ_ERR_DTYPE", -3: "MSZ_ERR_NONFINITE",
     -4: "MSZ_ERR_BOUND", -5: "MSZ_ERR_OOM", -6: "MSZ_ERR_NOCONVERGE", -7: "MSZ_ERR_TIMEOUT",
@@ -75,6 +78,17 @@ class MszResult(ctypes.Structure):
     ]
 
 
+class MszKernelStat(ctypes.Structure):
+    _fields_ = [
+        ("name", ctypes.c_char_p),
+        ("launches", ctypes.c_uint64),
+        ("work_launches", ctypes.c_uint64),
+        ("ms", ctypes.c_double),
+        ("work_ms", ctypes.c_double),
+        ("units", ctypes.c_uint64),
+    ]
+
+
 _lib = None
 
 
@@ -92,6 +106,8 @@ def lib() -> ctypes.CDLL:
         L.msz_plan_bytes.restype = I64
         L.msz_plan_destroy.argtypes = [P]
         L.msz_plan_destroy.restype = I
+        L.msz_plan_kernel_stats.argtypes = [P, ctypes.POINTER(MszKernelStat), I]
+        L.msz_plan_kernel_stats.restype = I
         L.msz_fix.argtypes = [P, P, P, D, P, ctypes.POINTER(MszResult)]
         L.msz_fix.restype = I
         L.msz_fix_host.argtypes = [P, P, P, D, P, P, P, P, P, ctypes.POINTER(MszResult)]
@@ -171,6 +187,15 @@ def msz_plan_bytes(shape, dtype) -> int:
 
 def msz_plan_destroy(plan):
     check(lib().msz_plan_destroy(plan), "msz_plan_destroy")
+
+
+def msz_plan_kernel_stats(plan) -> list[dict]:
+    out = (MszKernelStat * MSZ_NUM_KERNELS)()
+    m = lib().msz_plan_kernel_stats(plan, out, MSZ_NUM_KERNELS)
+    check(m if m < 0 else 0, "msz_plan_kernel_stats")
+    return [{"name": out[k].name.decode(), "launches": int(out[k].launches),
+             "work_launches": int(out[k].work_launches), "ms": float(out[k].ms),
+             "work_ms": float(out[k].work_ms), "units": int(out[k].units)} for k in range(m)]
 
 
 def msz_fix(plan, orig_ptr: int, decomp_ptr: int, xi: float, stream: int = 0) -> MszResult:

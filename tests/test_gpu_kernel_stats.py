@@ -1,0 +1,76 @@
+"""Kernel-timing instrumentation (msz_plan_kernel_stats): a plan with kernel
+timing gives the same results as a plain one, and its per-kernel launch,
+working-launch and work-unit counts agree with the fix's own counters."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2406_09423_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _msz():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2406_09423_gb300 as msz
+
+    return msz
+
+
+@pytest.mark.parametrize("shape", [(48, 40, 72), (300, 257)])
+def test_kernel_stats_consistent(shape):
+    msz = _msz()
+    if len(shape) == 3:
+        f = synth.turbulence3d(max(shape), 7, kmax=6.0, shape=shape)
+    else:
+        f = synth.bumps2d(shape[1], shape[0], 3)
+    xi = synth.xi_for(f, 1e-3)
+    fh = synth.quantise(f, xi)
+    tf, th = torch.from_numpy(f).cuda(), torch.from_numpy(fh).cuda()
+    plain = msz.Plan(f.shape, torch.float32)
+    timed = msz.Plan(f.shape, torch.float32, time_kernels=True)
+    a = plain.fix(tf, th, xi)
+    b = timed.fix(tf, th, xi)
+    assert a.counts == b.counts
+    assert torch.equal(a.edit_idx, b.edit_idx)
+    st = {s["name"]: s for s in timed.kernel_stats()}
+    assert list(st) == ["k_csweep", "k_gather_mark", "k_label_tile", "k_einit", "k_jump", "k_rcheck",
+                        "k_apply", "k_reclass"]
+    steps = st["k_csweep"]["launches"]
+    assert steps > 0
+    for name, s in st.items():
+        assert s["launches"] == (4 * steps if name == "k_jump" else steps)
+        assert 0 <= s["work_launches"] <= s["launches"]
+        assert 0.0 <= s["work_ms"] <= s["ms"] + 1e-9
+    c = b.counts
+    n = f.size
+    assert st["k_csweep"]["work_launches"] == 1 and st["k_csweep"]["units"] == n
+    rounds = sum(c[k] for k in ("c_rounds_fpmax", "c_rounds_fpmin", "c_rounds_fnmax", "c_rounds_fnmin"))
+    assert st["k_gather_mark"]["work_launches"] == rounds
+    assert st["k_gather_mark"]["units"] == sum(
+        c[k] for k in ("c_cases_fpmax", "c_cases_fpmin", "c_cases_fnmax", "c_cases_fnmin"))
+    assert st["k_apply"]["work_launches"] == rounds + c["r_rounds"]
+    assert st["k_reclass"]["work_launches"] == rounds + c["r_rounds"]
+    assert st["k_rcheck"]["work_launches"] == c["label_evals"]
+    assert st["k_rcheck"]["units"] == n * c["label_evals"]
+    # f's labels once, then g's at every evaluation
+    assert st["k_label_tile"]["work_launches"] == c["label_evals"] + 1
+    assert st["k_einit"]["work_launches"] == c["label_evals"] + 1
+    assert 0 < st["k_label_tile"]["units"] <= n * (c["label_evals"] + 1)
+    assert st["k_jump"]["work_launches"] >= st["k_einit"]["work_launches"]
+    # classification sweeps: one full, one incremental per apply
+    assert c["sweeps"] == 1 + rounds + c["r_rounds"]
+    plain.close()
+    timed.close()
+
+
+def test_kernel_stats_needs_timing_plan():
+    msz = _msz()
+    from paper_2406_09423_gb300 import native
+
+    p = msz.Plan((16, 16), torch.float32)
+    with pytest.raises(RuntimeError):
+        native.msz_plan_kernel_stats(p._p)
+    p.close()
