@@ -108,22 +108,28 @@ def kernel_bytes(name, st, n, es):
     k_csweep      g (es) + f's direction byte per vertex swept;
     k_label_tile  g (es) + direction byte + two tile terminals (8) per vertex
                   of the tiles recomputed;
-    k_einit       the two exit bitmaps (n / 4 bytes) + terminal read and label
-                  write (8) per exit;
-    k_jump        the two exit bitmaps + label read, terminal and label
-                  gathers (12) per exit, per round;
-    k_rcheck      four label words (16) + two direction bytes per vertex."""
+    k_ecount      per bitmap word: two exit-bitmap words read, two prefix
+                  words written (16);
+    k_efill       bitmaps and prefixes (n / 2 bytes per launch) + terminal
+                  read and table entry written (8) per exit;
+    k_jump        4 bytes per exit-table access (entry read; gather and write
+                  of the entries still holding a rank);
+    k_escatter    bitmaps and prefixes (n / 2 per launch) + table entry read
+                  and exit label written (8) per exit;
+    k_rcheck      four label words per vertex (16)."""
     u, w = st["units"], st["work_launches"]
     if name == "k_csweep":
         return u * (es + 1)
     if name == "k_label_tile":
         return u * (es + 9)
-    if name == "k_einit":
-        return w * n / 4 + u * 8
+    if name == "k_ecount":
+        return u * 16
+    if name in ("k_efill", "k_escatter"):
+        return w * n / 2 + u * 8
     if name == "k_jump":
-        return w * n / 4 + u * 12
+        return u * 4
     if name == "k_rcheck":
-        return u * 18
+        return u * 16
     return None
 
 

@@ -118,9 +118,10 @@ int msz_plan_destroy(msz_plan p);
  * completes a stage of the field's state machine (the others find the field
  * in another stage and return at once). units counts the work of the working
  * launches: vertices (k_csweep, k_rcheck, k_label_tile: vertices of the tiles
- * recomputed), tile exits visited (k_einit, k_jump), cases (k_gather_mark),
+ * recomputed), bitmap words (k_ecount), exits (k_efill, k_escatter), exit-table
+ * accesses (k_jump), fields (k_escan), cases (k_gather_mark),
  * touched vertices (k_apply), ring items (k_reclass). */
-#define MSZ_NUM_KERNELS 8
+#define MSZ_NUM_KERNELS 11
 typedef struct {
   const char* name;        /* kernel name, static string */
   uint64_t launches;       /* launches inside the loop's steps */
@@ -131,7 +132,8 @@ typedef struct {
 } msz_kernel_stat;
 
 /* Fills out[0 .. min(n, MSZ_NUM_KERNELS) - 1] in step order (k_csweep,
- * k_gather_mark, k_label_tile, k_einit, k_jump, k_rcheck, k_apply, k_reclass);
+ * k_gather_mark, k_label_tile, k_ecount, k_escan, k_efill, k_jump,
+ * k_escatter, k_rcheck, k_apply, k_reclass);
  * returns the number filled, or MSZ_ERR_ARG (no plan / out, or a plan made
  * without MSZ_OPT_TIME_KERNELS). Host memory only. */
 int msz_plan_kernel_stats(msz_plan p, msz_kernel_stat* out, int n);

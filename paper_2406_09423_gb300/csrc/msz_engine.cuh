@@ -34,7 +34,15 @@ enum : uint32_t { PH_INIT = 0, PH_FLABELS = 1, PH_C = 2, PH_R = 3, PH_DONE = 4, 
 // (cases of the current type -> requests), ACT_MARK_C (apply) and
 // ACT_RECLASS (reclassify the closed 1-rings of the edited vertices).
 enum : uint32_t { ACT_NONE = 0, ACT_MARK_C = 1, ACT_LABELS = 2, ACT_APPLY_R = 3, ACT_GATHER = 4, ACT_RECLASS = 5 };
-enum : uint32_t { L_INIT = 0, L_EINIT = 1, L_JUMP = 2, L_DONE = 3 };
+// Stages of one label evaluation (job 0: f, job 1: g): tile terminals, exit
+// counts, exit ranks, compact exit table, pointer jumping on it, labels back
+// to the exit vertices, then f's labels in place (job 0) or the R-loop check.
+enum : uint32_t { L_INIT = 0, L_COUNT = 1, L_SCAN = 2, L_FILL = 3, L_JUMP = 4, L_SCATTER = 5, L_DONE = 6 };
+// Tile terminal flag: the terminal is an extremum (else a tile exit).
+constexpr uint32_t kExt = 0x80000000u;
+// Compact exit table entry flag: the entry holds the exit's label (an
+// extremum), else the rank of the next exit on its line.
+constexpr uint32_t kRes = 0x80000000u;
 enum : uint32_t { E_NONFINITE = 1, E_ARG = 2, E_BOUND = 4, E_TIMEOUT = 8 };
 
 // Work-unit kinds.
@@ -45,7 +53,10 @@ constexpr int kEmitTile = kThreads * kEmitItems;  // vertices per emission unit 
 constexpr int kCaseTiles = kThreads / 32;          // case-count tiles per gather unit (one per warp)
 
 // Kernels of a loop step, in launch order of their kinds (per-kernel timing).
-enum { KID_SWEEP = 0, KID_GATHER, KID_LABEL, KID_EINIT, KID_JUMP, KID_RCHECK, KID_APPLY, KID_RECLASS, NKID };
+enum {
+  KID_SWEEP = 0, KID_GATHER, KID_LABEL, KID_ECOUNT, KID_ESCAN, KID_EFILL, KID_JUMP, KID_ESCATTER, KID_RCHECK,
+  KID_APPLY, KID_RECLASS, NKID
+};
 
 // Per-field device state (one contiguous array per engine).
 struct DevState {
@@ -57,7 +68,7 @@ struct DevState {
   uint32_t acc_ap[2];  // apply: decreases, freezes
   uint32_t acc_r[4];   // rcheck: wrong max, wrong min, asc troublemakers, desc troublemakers
   uint32_t jump_rounds, emitted;
-  uint32_t f_resolved, pad1;  // f's labels resolved in place (first R-check)
+  uint32_t nexit[2];  // tile exits (ascending, descending lines) of the current evaluation
   uint64_t rounds, max_rounds, n_edits;
   uint64_t ticks;  // advanced by every state transition (stall detection)
   uint64_t kunits[NKID];  // work units per kernel (kernel timing runs only)
@@ -73,16 +84,16 @@ struct Field {
   uint8_t* fdir;
   uint8_t* gdir;
   uint8_t* flags;
-  int32_t* Mf;    // f: tile terminals, then (after the first R-check) labels
+  int32_t* Mf;    // f: tile terminals (kExt-flagged), labels once f's evaluation is done
   int32_t* mf;
-  int32_t* Pup;   // g: tile terminals, labels once the field has converged
+  int32_t* Pup;   // g: tile terminals (kExt-flagged), labels once the field has converged
   int32_t* Pdn;
-  int32_t* Lfu;   // resolved labels of tile exits (f, g; ascending, descending)
-  int32_t* Lfd;
-  int32_t* Lgu;
-  int32_t* Lgd;
-  uint32_t* exu;  // bitmaps of tile-exit vertices (ascending, descending lines)
-  uint32_t* exd;
+  // per direction (0: ascending lines / max labels, 1: descending / min)
+  uint32_t* ex[2];  // bitmap of tile-exit vertices
+  uint32_t* ep[2];  // per bitmap word: exits before it within its dense unit
+  uint32_t* ub[2];  // per dense unit: exits before it (after the scan; counts before)
+  uint32_t* lc[2];  // compact exit table, indexed by exit rank
+  int32_t* lx[2];   // label of every exit vertex (scattered back from lc)
   uint8_t* tdirty;  // label tiles whose terminals must be recomputed
   uint8_t* cls;     // false-type bits of g per vertex (FPmax, FPmin, FNmax, FNmin), padded to kEmitTile
   uint32_t* epoch;  // round in which a vertex was last reclassified (claims a vertex once per round)
@@ -244,17 +255,20 @@ __device__ void ctrl_after_jump(DevState* st) {
   st->jump_rounds++;
   st->ticks++;
   if (c == 0) {
-    if (st->ljob == 0) {
-      st->phase = PH_C;
-      st->action = ACT_NONE;
-      st->T = 0;
-    } else {
-      st->lstate = L_DONE;
-    }
+    st->lstate = L_SCATTER;
   } else if (st->jump_rounds > 64) {
     st->phase = PH_ERR;
     st->status = MSZ_ERR_TIMEOUT;
   }
+}
+
+// End of f's evaluation (its labels are in Mf / mf): the C-loop starts with
+// the full classification sweep.
+__device__ void ctrl_after_flabels(DevState* st) {
+  st->phase = PH_C;
+  st->action = ACT_NONE;
+  st->T = 0;
+  st->ticks++;
 }
 
 __device__ void ctrl_after_rcheck(DevState* st) {
@@ -265,7 +279,6 @@ __device__ void ctrl_after_rcheck(DevState* st) {
   st->cnt.mismatch[1] += wm;
   st->acc_r[0] = st->acc_r[1] = 0;
   st->lstate = L_INIT;
-  st->f_resolved = 1;
   st->ticks++;
   if (wM + wm == 0) {
     st->phase = PH_DONE;

@@ -135,12 +135,11 @@ struct FieldBufs {
   int32_t* mf = nullptr;
   int32_t* Pup = nullptr;
   int32_t* Pdn = nullptr;
-  int32_t* Lfu = nullptr;
-  int32_t* Lfd = nullptr;
-  int32_t* Lgu = nullptr;
-  int32_t* Lgd = nullptr;
-  uint32_t* exu = nullptr;
-  uint32_t* exd = nullptr;
+  uint32_t* ex[2] = {nullptr, nullptr};
+  uint32_t* ep[2] = {nullptr, nullptr};
+  uint32_t* ub[2] = {nullptr, nullptr};
+  uint32_t* lc[2] = {nullptr, nullptr};
+  int32_t* lx[2] = {nullptr, nullptr};
   uint8_t* tdirty = nullptr;
   uint8_t* cls = nullptr;
   uint32_t* epoch = nullptr;
@@ -172,13 +171,14 @@ void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs
   B.flags = (uint8_t*)b.take(nt * kEmitTile);
   B.Mf = (int32_t*)b.take(n * 4);
   B.mf = (int32_t*)b.take(n * 4);
-  B.Lfu = (int32_t*)b.take(n * 4);
-  B.Lfd = (int32_t*)b.take(n * 4);
-  B.Lgu = (int32_t*)b.take(n * 4);
-  B.Lgd = (int32_t*)b.take(n * 4);
-  const size_t nw = (n + 31) / 32;
-  B.exu = (uint32_t*)b.take(nw * 4);
-  B.exd = (uint32_t*)b.take(nw * 4);
+  const size_t nw = (n + 31) / 32, nu = (n + kDenseChunk - 1) / kDenseChunk;
+  for (int d = 0; d < 2; ++d) {
+    B.ex[d] = (uint32_t*)b.take(nw * 4);
+    B.ep[d] = (uint32_t*)b.take(nw * 4);
+    B.ub[d] = (uint32_t*)b.take(nu * 4);
+    B.lc[d] = (uint32_t*)b.take(n * 4);
+    B.lx[d] = (int32_t*)b.take(n * 4);
+  }
   B.tdirty = (uint8_t*)b.take((size_t)label_tiles(G));
   B.cls = (uint8_t*)b.take(nt * kEmitTile);
   B.epoch = (uint32_t*)b.take(n * 4);
@@ -197,15 +197,17 @@ void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs
 // One (dtype, dimension) group of an engine's fields.
 // ---------------------------------------------------------------------------
 constexpr int kJumpsPerStep = 4;
-constexpr int kStepSlots = 7 + kJumpsPerStep;  // launches per step
+constexpr int kStepSlots = 10 + kJumpsPerStep;  // launches per step (without graph conditionals)
 constexpr int kStepEvents = kStepSlots + 1;
 // kernel of each launch slot of a step
-constexpr int kSlotKernel[kStepSlots] = {KID_SWEEP, KID_GATHER, KID_LABEL, KID_EINIT, KID_JUMP, KID_JUMP,
-                                         KID_JUMP,  KID_JUMP,   KID_RCHECK, KID_APPLY, KID_RECLASS};
+constexpr int kSlotKernel[kStepSlots] = {KID_SWEEP, KID_GATHER,   KID_LABEL,  KID_ECOUNT, KID_ESCAN,
+                                         KID_EFILL, KID_JUMP,     KID_JUMP,   KID_JUMP,   KID_JUMP,
+                                         KID_ESCATTER, KID_RCHECK, KID_APPLY, KID_RECLASS};
 static_assert(kJumpsPerStep == 4, "slot table assumes four jump launches per step");
 static_assert(NKID == MSZ_NUM_KERNELS, "kernel table and ABI disagree");
-const char* const kKernelNames[NKID] = {"k_csweep", "k_gather_mark", "k_label_tile", "k_einit",
-                                        "k_jump",   "k_rcheck",      "k_apply",      "k_reclass"};
+const char* const kKernelNames[NKID] = {"k_csweep", "k_gather_mark", "k_label_tile", "k_ecount",
+                                        "k_escan",  "k_efill",       "k_jump",       "k_escatter",
+                                        "k_rcheck", "k_apply",       "k_reclass"};
 
 template <class T, int ND>
 struct Group {
@@ -295,12 +297,13 @@ struct Group {
       F.mf = B.mf;
       F.Pup = B.Pup;
       F.Pdn = B.Pdn;
-      F.Lfu = B.Lfu;
-      F.Lfd = B.Lfd;
-      F.Lgu = B.Lgu;
-      F.Lgd = B.Lgd;
-      F.exu = B.exu;
-      F.exd = B.exd;
+      for (int d = 0; d < 2; ++d) {
+        F.ex[d] = B.ex[d];
+        F.ep[d] = B.ep[d];
+        F.ub[d] = B.ub[d];
+        F.lc[d] = B.lc[d];
+        F.lx[d] = B.lx[d];
+      }
       F.tdirty = B.tdirty;
       F.cls = B.cls;
       F.epoch = B.epoch;
@@ -375,9 +378,14 @@ struct Group {
     k_init<T><<<grid[K_DENSE], kThreads, 0, s>>>(args);
   }
 
-  // One loop step. Kernel timing (single-field plans with
-  // MSZ_OPT_TIME_KERNELS): e holds kStepEvents events, one before each launch
-  // and one after the last; each launch gets the step's log slot.
+  // Conditions of this group's graph step bodies (see k_decide).
+  cudaGraphConditionalHandle hs = 0, hc = 0, hr = 0;
+  static constexpr int kLabelLaunches = 7 + kJumpsPerStep;  // label_tile .. rcheck
+
+  // One loop step, all kernels (each acts only on the fields in its stage).
+  // Kernel timing (single-field plans with MSZ_OPT_TIME_KERNELS): e holds
+  // kStepEvents events, one before each launch and one after the last; each
+  // launch gets the step's log slot.
   void step(cudaStream_t s, cudaEvent_t* e = nullptr, uint32_t* steplog = nullptr, int si = 0) {
     if (empty()) return;
     int slot = 0;
@@ -392,16 +400,38 @@ struct Group {
       ++slot;
       return x;
     };
-    if (tma) k_csweep<T, ND, true><<<grid[K_SWEEP], SG::NTP, 0, s>>>(a());
-    else k_csweep<T, ND, false><<<grid[K_SWEEP], SG::NT, 0, s>>>(a());
-    k_gather_mark<T, ND><<<grid[K_CASE], kThreads, 0, s>>>(a());
+    sweep(s, a());
+    gather(s, a());
+    labels(s, a);
+    tail(s, a);
+    if (e) cudaEventRecord(e[slot], s);
+  }
+
+  // Step pieces (the graph puts the first three under conditions).
+  void sweep(cudaStream_t s, const GroupArgs<T>& x) {
+    if (tma) k_csweep<T, ND, true><<<grid[K_SWEEP], SG::NTP, 0, s>>>(x);
+    else k_csweep<T, ND, false><<<grid[K_SWEEP], SG::NT, 0, s>>>(x);
+  }
+  void gather(cudaStream_t s, const GroupArgs<T>& x) {
+    k_gather_mark<T, ND><<<grid[K_CASE], kThreads, 0, s>>>(x);
+  }
+  template <class A>
+  void labels(cudaStream_t s, A&& a) {
     k_label_tile<T, ND><<<grid[K_LABEL], kThreads, label_smem, s>>>(a());
-    k_einit<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
+    k_ecount<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
+    k_escan<T><<<nf, 1024, 0, s>>>(a());
+    k_efill<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
     for (int j = 0; j < kJumpsPerStep; ++j) k_jump<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
+    k_escatter<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
     k_rcheck<T, ND><<<grid[K_DENSE], kThreads, 0, s>>>(a());
+  }
+  template <class A>
+  void tail(cudaStream_t s, A&& a) {
     k_apply<T><<<grid[K_SPARSE], kThreads, 0, s>>>(a());
     k_reclass<T, ND><<<grid[K_SPARSE], kThreads, 0, s>>>(a());
-    if (e) cudaEventRecord(e[slot], s);
+  }
+  void decide(cudaStream_t s, unsigned long long* launches) {
+    k_decide<T><<<1, 256, 0, s>>>(args, hs, hc, hr, launches, kLabelLaunches);
   }
 
   void emit(cudaStream_t s) {
@@ -451,6 +481,8 @@ struct msz_engine_s {
   double kernel_ms[kKinds] = {0, 0, 0, 0};
   // per-kernel statistics of the last timed run (single-field engines)
   uint32_t* d_steplog = nullptr;
+  unsigned long long* d_launch_count = nullptr;  // kernels the graph steps launched (device count)
+  unsigned long long h_launch_count = 0;
   uint32_t h_steplog[kMaxChunk] = {};
   uint64_t ks_launches[NKID] = {}, ks_work[NKID] = {}, ks_units[NKID] = {};
   double ks_ms[NKID] = {}, ks_work_ms[NKID] = {};
@@ -494,6 +526,7 @@ size_t layout_engine(msz_engine_s* E, unsigned char* base, bool with_outputs) {
   }
   E->d_states = (DevState*)b.take(sizeof(DevState) * E->nf, 256);
   E->d_steplog = (uint32_t*)b.take(sizeof(uint32_t) * kMaxChunk, 256);
+  E->d_launch_count = (unsigned long long*)b.take(sizeof(unsigned long long), 256);
   E->each_group([&](auto& g) { g.carve(b); });
   return b.off;
 }
@@ -674,26 +707,91 @@ void collect_times(msz_engine_s* E, int steps) {
         E->ks_work[kid]++;
         E->ks_work_ms[kid] += dt;
       }
-      const int kind = (kid == KID_SWEEP || kid == KID_RECLASS) ? 0
-                       : (kid == KID_LABEL || kid == KID_EINIT || kid == KID_JUMP) ? 1
-                       : (kid == KID_RCHECK) ? 2 : 3;
+      const int kind = (kid == KID_SWEEP || kid == KID_RECLASS)         ? 0
+                       : (kid == KID_GATHER || kid == KID_APPLY)         ? 3
+                       : (kid == KID_RCHECK)                             ? 2
+                                                                         : 1;  // label stages
       E->kernel_ms[kind] += dt;
     }
   }
 }
 
-// Captures kGraphSteps steps of every group once (on a private stream).
+// Captures the work fn(stream) launches into graph g after the nodes in tail;
+// tail becomes the captured work's last nodes.
+template <class Fn>
+bool capture_into(cudaGraph_t g, std::vector<cudaGraphNode_t>& tail, cudaStream_t s, Fn&& fn) {
+  if (cudaStreamBeginCaptureToGraph(s, g, tail.empty() ? nullptr : tail.data(), nullptr, tail.size(),
+                                    cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return false;
+  fn(s);
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  const bool info = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess;
+  std::vector<cudaGraphNode_t> next;
+  if (info) next.assign(deps, deps + nd);
+  cudaGraph_t out = nullptr;
+  if (cudaStreamEndCapture(s, &out) != cudaSuccess || !info) return false;
+  tail.swap(next);
+  return true;
+}
+
+// Adds "if (condition h) { fn(stream) }" after tail; tail becomes that node.
+template <class Fn>
+bool add_if(cudaGraph_t g, std::vector<cudaGraphNode_t>& tail, cudaGraphConditionalHandle h, cudaStream_t s,
+            Fn&& fn) {
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeIf;
+  p.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  if (cudaGraphAddNode(&node, g, tail.empty() ? nullptr : tail.data(), nullptr, tail.size(), &p) != cudaSuccess)
+    return false;
+  std::vector<cudaGraphNode_t> none;
+  if (!capture_into(p.conditional.phGraph_out[0], none, s, fn)) return false;
+  tail.assign(1, node);
+  return true;
+}
+
+// Builds the graph of kGraphSteps loop steps of every group once. A group's
+// step: k_decide, then the full sweep, the case gather and the label stages
+// each under its condition, then apply and reclassification; so a step
+// launches only the kernels some field of the group needs.
 int ensure_graph(msz_engine_s* E) {
   if (E->graph) return MSZ_OK;
   if (!E->cap_stream && cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return MSZ_ERR_CUDA;
   cudaGraph_t gr = nullptr;
-  if (cudaStreamBeginCapture(E->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MSZ_ERR_CUDA;
-  for (int i = 0; i < kGraphSteps; ++i) E->each_group([&](auto& g) { g.step(E->cap_stream, nullptr); });
-  if (cudaStreamEndCapture(E->cap_stream, &gr) != cudaSuccess) return MSZ_ERR_CUDA;
-  const cudaError_t r = cudaGraphInstantiate(&E->graph, gr, 0);
+  if (cudaGraphCreate(&gr, 0) != cudaSuccess) return MSZ_ERR_CUDA;
+  bool ok = true;
+  E->each_group([&](auto& g) {
+    if (g.empty() || !ok) return;
+    ok = cudaGraphConditionalHandleCreate(&g.hs, gr, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
+         cudaGraphConditionalHandleCreate(&g.hc, gr, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
+         cudaGraphConditionalHandleCreate(&g.hr, gr, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  });
+  std::vector<cudaGraphNode_t> tail;
+  cudaStream_t cs = E->cap_stream;
+  for (int i = 0; ok && i < kGraphSteps; ++i) {
+    E->each_group([&](auto& g) {
+      if (g.empty() || !ok) return;
+      auto plain = [&]() { return g.args; };
+      ok = capture_into(gr, tail, cs, [&](cudaStream_t s) { g.decide(s, E->d_launch_count); }) &&
+           add_if(gr, tail, g.hs, cs, [&](cudaStream_t s) { g.sweep(s, g.args); }) &&
+           add_if(gr, tail, g.hc, cs, [&](cudaStream_t s) { g.gather(s, g.args); }) &&
+           add_if(gr, tail, g.hr, cs, [&](cudaStream_t s) { g.labels(s, plain); }) &&
+           capture_into(gr, tail, cs, [&](cudaStream_t s) { g.tail(s, plain); });
+    });
+  }
+  if (ok) ok = cudaGraphInstantiate(&E->graph, gr, 0) == cudaSuccess;
   cudaGraphDestroy(gr);
-  return r == cudaSuccess ? MSZ_OK : MSZ_ERR_CUDA;
+  if (!ok) {
+    cudaGetLastError();
+    E->graph = nullptr;
+    return MSZ_ERR_CUDA;
+  }
+  return MSZ_OK;
 }
 
 // Runs every field of the engine to completion. f / fhat / xi are indexed
@@ -734,6 +832,8 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
   }
   if (timed && cudaMemsetAsync(E->d_steplog, 0, sizeof(uint32_t) * kMaxChunk, s) != cudaSuccess) return MSZ_ERR_CUDA;
   const bool graph = E->use_graph && !timed && ensure_graph(E) == MSZ_OK;
+  if (graph && cudaMemsetAsync(E->d_launch_count, 0, sizeof(unsigned long long), s) != cudaSuccess)
+    return MSZ_ERR_CUDA;
   // Steps in growing chunks; one state read per chunk. A chunk in which no
   // field's state machine moved means a stall.
   int chunk = 1;
@@ -741,7 +841,6 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
   for (;;) {
     if (graph) {
       for (int i = 0; i < chunk; ++i) cudaGraphLaunch(E->graph, s);
-      E->launches += (uint64_t)chunk * kGraphSteps * E->launches_per_step();
     } else {
       launch_steps(E, s, std::min(chunk * kGraphSteps, kMaxChunk), timed);
     }
@@ -779,7 +878,11 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
   if (E->ev1) cudaEventRecord(E->ev1, s);
   if (cudaMemcpyAsync(H, E->d_states, sizeof(DevState) * nf, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return MSZ_ERR_CUDA;
+  if (graph && cudaMemcpyAsync(&E->h_launch_count, E->d_launch_count, sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return MSZ_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return MSZ_ERR_CUDA;
+  if (graph) E->launches += E->h_launch_count;
   if (cudaGetLastError() != cudaSuccess) return MSZ_ERR_CUDA;
   if (timed && nf == 1) {
     for (int k = 0; k < NKID; ++k) E->ks_units[k] = H[0].kunits[k];

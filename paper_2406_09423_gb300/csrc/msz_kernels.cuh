@@ -98,8 +98,8 @@ __global__ void __launch_bounds__(kThreads) k_init(GroupArgs<T> A) {
     if (err) atomicOr(&st->err_bits, err);
     // tile-exit bitmaps start empty; every label tile starts dirty
     for (int w = (v0 >> 5) + threadIdx.x; w < ((v1 + 31) >> 5); w += blockDim.x) {
-      F.exu[w] = 0;
-      F.exd[w] = 0;
+      F.ex[0][w] = 0;
+      F.ex[1][w] = 0;
     }
     {
       const int ntl = F.units[K_LABEL], nu = F.units[K_DENSE], lu = u_ - pre[i];
@@ -510,7 +510,7 @@ size_t label_smem_bytes() {
 }
 
 template <class T, int ND>
-__global__ void __launch_bounds__(kThreads) k_label_tile(GroupArgs<T> A) {
+__global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
   using LG = LabelGeom<ND>;
   extern __shared__ __align__(16) unsigned char lsm[];
   T* val = reinterpret_cast<T*>(lsm);
@@ -522,6 +522,10 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(GroupArgs<T> A) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int HS = LG::SX, HSS = LG::SX * LG::SY;
   constexpr int NC = (ND == 3) ? 15 : 7;
+  // halo-cell exit bits (ascending, descending); padded for the two-word reads
+  constexpr int kExWords = (LG::HALO + 31) / 32 + 2;
+  constexpr int kSegs = (LG::SX + 31) / 32;
+  __shared__ uint32_t exs[2][kExWords];
   auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_INIT; };
   MSZ_ACTIVE_UNITS(A, K_LABEL, pre, fi, active) {
     const Field<T>& F = A.fields[fi];
@@ -540,7 +544,7 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(GroupArgs<T> A) {
     __syncthreads();
     if (!redo) {
       if (unit_done(st, F.units[K_LABEL]) && threadIdx.x == 0) {
-        st->lstate = L_EINIT;
+        st->lstate = L_COUNT;
         st->ticks++;
         log_work(A);
         st->units_done = 0;
@@ -551,6 +555,7 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(GroupArgs<T> A) {
     const int y0 = ((tile / tiles_x) % tiles_y) * LG::TY;
     const int z0 = (tile / (tiles_x * tiles_y)) * LG::TZ;
     __syncthreads();
+    for (int k = threadIdx.x; k < 2 * kExWords; k += kThreads) exs[k / kExWords][k % kExWords] = 0u;
     for (int row = warp; row < LG::ROWS; row += kThreads / 32) {
       const int hy = row % LG::SY, hz = row / LG::SY;
       const int gy = y0 - 1 + hy, gz = (ND == 3) ? z0 - 1 + hz : 0;
@@ -622,27 +627,50 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(GroupArgs<T> A) {
         const int v = x + G.nx * (y + G.ny * z);
         const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
         // terminal cell -> global index; a terminal in the halo is a tile
-        // exit, recorded in the bitmap the cross-tile jumping walks
-        auto global_of = [&](int h, uint32_t* ex) -> int {
+        // exit, noted in the block's halo bitmap (flushed below); one inside
+        // the tile is an extremum (flag kExt)
+        auto global_of = [&](int h, uint32_t* exb) -> int {
           const int hx = h % LG::SX, hy = (h / LG::SX) % LG::SY, hz = h / HSS;
           const int e = (x0 - 1 + hx) + G.nx * ((y0 - 1 + hy) + G.ny * ((ND == 3) ? (z0 - 1 + hz) : 0));
           const bool halo = hx == 0 || hx == LG::SX - 1 || hy == 0 || hy == LG::SY - 1 ||
                             (ND == 3 && (hz == 0 || hz == LG::SZ - 1));
-          if (halo) atomicOr(&ex[e >> 5], 1u << (e & 31));
-          return e;
+          if (halo) atomicOr(&exb[h >> 5], 1u << (h & 31));
+          return (int)((uint32_t)e | (halo ? 0u : kExt));
         };
         dir[v] = dbyte[k];
-        OA[v] = global_of(Pu[c], F.exu);
-        OB[v] = global_of(Pd[c], F.exd);
+        OA[v] = global_of(Pu[c], exs[0]);
+        OB[v] = global_of(Pd[c], exs[1]);
       }
     }
     __syncthreads();
+    // Exit bits into the field's bitmaps: one atomic per global word that a
+    // halo-row segment (at most 32 cells, contiguous in x) touches.
+    for (int it = threadIdx.x; it < 2 * LG::ROWS * kSegs; it += kThreads) {
+      const int d = it / (LG::ROWS * kSegs), r = it % (LG::ROWS * kSegs), row = r / kSegs;
+      const int hx0 = (r % kSegs) * 32, len = min(32, LG::SX - hx0);
+      const int bit0 = row * LG::SX + hx0, w0 = bit0 >> 5, off = bit0 & 31;
+      uint32_t m = exs[d][w0] >> off;
+      if (off) m |= exs[d][w0 + 1] << (32 - off);
+      if (len < 32) m &= (1u << len) - 1u;
+      if (!m) continue;
+      const int hy = row % LG::SY, hz = row / LG::SY;
+      // cells with bits are in the grid, so the first one's index is >= 0
+      const long long e0 =
+          (long long)(x0 - 1 + hx0) + (long long)G.nx * ((y0 - 1 + hy) + (long long)G.ny * ((ND == 3) ? z0 - 1 + hz : 0));
+      const long long first = e0 + __ffs(m) - 1;
+      const long long w = first >> 5;
+      const int shift = (int)(e0 - (w << 5));  // position of segment bit 0 in word w (-31 .. 31)
+      const uint64_t M = shift >= 0 ? ((uint64_t)m << shift) : ((uint64_t)m >> -shift);
+      uint32_t* ex = F.ex[d];
+      if ((uint32_t)M) atomicOr(&ex[w], (uint32_t)M);
+      if ((uint32_t)(M >> 32)) atomicOr(&ex[w + 1], (uint32_t)(M >> 32));
+    }
     if (job && threadIdx.x == 0) F.tdirty[tile] = 0;  // f's pass leaves every tile dirty for g's first
     if (threadIdx.x == 0)
       log_units(A, st, KID_LABEL,
                 (uint64_t)min(LG::TX, G.nx - x0) * min(LG::TY, G.ny - y0) * min(LG::TZ, G.nz - z0));
     if (unit_done(st, F.units[K_LABEL]) && threadIdx.x == 0) {
-      st->lstate = L_EINIT;
+      st->lstate = L_COUNT;
       st->ticks++;
       log_work(A);
       st->units_done = 0;
@@ -650,48 +678,173 @@ __global__ void __launch_bounds__(kThreads) k_label_tile(GroupArgs<T> A) {
   }
 }
 
-// Labels, second level. Every tile exit e starts from its tile terminal,
-// L[e] = T[e] (k_einit); then pointer jumping over the exits only (k_jump):
-// L[e] <- L[L[e]] while L[e] is not an extremum (T[x] == x marks one). A
-// round that changes nothing means every exit knows its extremum.
+// Labels, second level (Sec. 5.2, across tiles). The tile exits of a
+// direction are ranked in bitmap order: k_ecount counts them per bitmap word
+// and dense unit, k_escan turns the unit counts into offsets. k_efill writes
+// the compact exit table: entry rank(e) holds e's label when e's tile
+// terminal is an extremum (flag kRes), else the rank of that terminal (an
+// exit of e's tile). k_jump does pointer jumping on the table, one thread per
+// entry, until every entry holds a label; k_escatter writes the labels back
+// to the exit vertices (lx), where label resolution reads them.
+__device__ __forceinline__ uint32_t exit_rank(const uint32_t* ex, const uint32_t* ep, const uint32_t* ub, int e) {
+  const int w = e >> 5;
+  return ub[e / kDenseChunk] + ep[w] + (uint32_t)__popc(ex[w] & ((1u << (e & 31)) - 1u));
+}
+
+// Label of v from its tile terminal: the extremum itself, or the label of the
+// exit its line leaves the tile through.
+__device__ __forceinline__ int resolve_label(const int32_t* Tt, const int32_t* lx, int v) {
+  const uint32_t t = (uint32_t)Tt[v];
+  return (t & kExt) ? (int)(t & ~kExt) : lx[t];
+}
+
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_einit(GroupArgs<T> A) {
+__global__ void __launch_bounds__(kThreads) k_ecount(GroupArgs<T> A) {
+  static_assert(kDenseChunk == 32 * kThreads, "one bitmap word per thread and dense unit");
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
-  auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_EINIT; };
+  __shared__ uint32_t wsum[2][kThreads / 32];
+  auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_COUNT; };
+  MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
+    const Field<T>& F = A.fields[i];
+    DevState* st = F.st;
+    const int u = u_ - pre[i];
+    const int nw = (F.G.n + 31) >> 5;
+    const int w = u * kThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t c[2], incl[2];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      c[d] = (w < nw) ? (uint32_t)__popc(F.ex[d][w]) : 0u;
+      incl[d] = c[d];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl[d], o);
+        if (lane >= o) incl[d] += y;
+      }
+      if (lane == 31) wsum[d][warp] = incl[d];
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        uint32_t x = (lane < kThreads / 32) ? wsum[d][lane] : 0u, y = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t z = __shfl_up_sync(kFull, y, o);
+          if (lane >= o) y += z;
+        }
+        if (lane < kThreads / 32) wsum[d][lane] = y - x;  // exclusive warp offsets
+        if (lane == kThreads / 32 - 1) F.ub[d][u] = y;     // unit total (scanned by k_escan)
+      }
+    }
+    __syncthreads();
+    if (w < nw) {
+      F.ep[0][w] = wsum[0][warp] + incl[0] - c[0];
+      F.ep[1][w] = wsum[1][warp] + incl[1] - c[1];
+    }
+    log_units_warp(A, st, KID_ECOUNT, (w < nw) ? 1u : 0u);
+    if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
+      st->lstate = L_SCAN;
+      st->ticks++;
+      log_work(A);
+      st->units_done = 0;
+    }
+  }
+}
+
+// Exclusive scan of the unit exit counts of both directions, one block per
+// field of the group (grid = number of fields).
+template <class T>
+__global__ void __launch_bounds__(1024) k_escan(GroupArgs<T> A) {
+  __shared__ uint32_t ws[32];
+  __shared__ uint32_t carry;
+  if ((int)blockIdx.x >= A.nf) return;
+  const Field<T>& F = A.fields[blockIdx.x];
+  DevState* st = F.st;
+  if (!(st->action == ACT_LABELS && st->lstate == L_SCAN)) return;
+  const int U = F.units[K_DENSE];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = 0; d < 2; ++d) {
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b = 0; b < U; b += blockDim.x) {
+      const int k = b + threadIdx.x;
+      const uint32_t x = (k < U) ? F.ub[d][k] : 0u;
+      uint32_t y = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t z = __shfl_up_sync(kFull, y, o);
+        if (lane >= o) y += z;
+      }
+      if (lane == 31) ws[warp] = y;
+      __syncthreads();
+      if (warp == 0) {
+        const uint32_t a = (lane < (int)(blockDim.x >> 5)) ? ws[lane] : 0u;
+        uint32_t q = a;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t z = __shfl_up_sync(kFull, q, o);
+          if (lane >= o) q += z;
+        }
+        ws[lane] = q - a;
+      }
+      __syncthreads();
+      const uint32_t c0 = carry;
+      if (k < U) F.ub[d][k] = c0 + ws[warp] + y - x;
+      __syncthreads();
+      if (threadIdx.x == blockDim.x - 1) carry = c0 + ws[warp] + y;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) st->nexit[d] = carry;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    st->lstate = L_FILL;
+    st->ticks++;
+    log_units(A, st, KID_ESCAN, 1);
+    log_work(A);
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_efill(GroupArgs<T> A) {
+  const int* pre = A.prefix + K_DENSE * (A.nf + 1);
+  auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_FILL; };
   MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
     const bool job = st->ljob != 0;
-    const int32_t* TA = job ? F.Pup : F.Mf;
-    const int32_t* TB = job ? F.Pdn : F.mf;
-    int32_t* LA = job ? F.Lgu : F.Lfu;
-    int32_t* LB = job ? F.Lgd : F.Lfd;
-    const int v0 = (u_ - pre[i]) * kDenseChunk;
-    const int v1 = min(F.G.n, v0 + kDenseChunk);
+    const int u = u_ - pre[i];
+    const int nw = (F.G.n + 31) >> 5;
+    const int w = u * kThreads + threadIdx.x;
     uint32_t nex = 0;
-    for (int w = (v0 >> 5) + threadIdx.x; w < ((v1 + 31) >> 5); w += blockDim.x) {
-      for (uint32_t m = F.exu[w]; m; m &= m - 1) {
-        const int e = (w << 5) + __ffs(m) - 1;
-        LA[e] = TA[e];
-        ++nex;
-      }
-      for (uint32_t m = F.exd[w]; m; m &= m - 1) {
-        const int e = (w << 5) + __ffs(m) - 1;
-        LB[e] = TB[e];
-        ++nex;
+    if (w < nw) {
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const int32_t* Tt = d ? (job ? F.Pdn : F.mf) : (job ? F.Pup : F.Mf);
+        uint32_t r = F.ub[d][u] + F.ep[d][w];
+        for (uint32_t m = F.ex[d][w]; m; m &= m - 1, ++r) {
+          const int e = (w << 5) + __ffs(m) - 1;
+          const uint32_t t = (uint32_t)Tt[e];
+          F.lc[d][r] = (t & kExt) ? ((t & ~kExt) | kRes) : exit_rank(F.ex[d], F.ep[d], F.ub[d], (int)t);
+          ++nex;
+        }
       }
     }
-    log_units_warp(A, st, KID_EINIT, nex);
+    log_units_warp(A, st, KID_EFILL, nex);
     if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
       st->lstate = L_JUMP;
-      log_work(A);
       st->jump_rounds = 0;
       st->ticks++;
+      log_work(A);
       st->units_done = 0;
     }
   }
 }
 
+// One round of pointer jumping on the compact exit tables: an entry that
+// holds a rank takes the entry it points to. Units are kDenseChunk entries of
+// the table. A round that finds no rank left ends the jumping.
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
@@ -699,35 +852,23 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
   MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
-    const bool job = st->ljob != 0;
-    const int32_t* TA = job ? F.Pup : F.Mf;
-    const int32_t* TB = job ? F.Pdn : F.mf;
-    int32_t* LA = job ? F.Lgu : F.Lfu;
-    int32_t* LB = job ? F.Lgd : F.Lfd;
-    const int v0 = (u_ - pre[i]) * kDenseChunk;
-    const int v1 = min(F.G.n, v0 + kDenseChunk);
-    uint32_t changed[1] = {0}, nex = 0;
-    for (int w = (v0 >> 5) + threadIdx.x; w < ((v1 + 31) >> 5); w += blockDim.x) {
-      if (A.steplog) nex += __popc(F.exu[w]) + __popc(F.exd[w]);
-      for (uint32_t m = F.exu[w]; m; m &= m - 1) {
-        const int e = (w << 5) + __ffs(m) - 1;
-        const int x = LA[e];
-        if (TA[x] != x) {
-          const int y = LA[x];
-          if (y != x) { LA[e] = y; ++changed[0]; }
-        }
-      }
-      for (uint32_t m = F.exd[w]; m; m &= m - 1) {
-        const int e = (w << 5) + __ffs(m) - 1;
-        const int x = LB[e];
-        if (TB[x] != x) {
-          const int y = LB[x];
-          if (y != x) { LB[e] = y; ++changed[0]; }
-        }
+    const uint32_t r0 = (uint32_t)(u_ - pre[i]) * kDenseChunk;
+    uint32_t open[1] = {0}, acc = 0;
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const uint32_t ne = st->nexit[d];
+      uint32_t* lc = F.lc[d];
+      for (uint32_t r = r0 + threadIdx.x; r < min(ne, r0 + (uint32_t)kDenseChunk); r += kThreads) {
+        const uint32_t x = lc[r];
+        ++acc;
+        if (x & kRes) continue;
+        lc[r] = lc[x];
+        ++open[0];
+        acc += 2;
       }
     }
-    log_units_warp(A, st, KID_JUMP, nex);
-    block_add<1>(changed, &st->acc_changed);
+    log_units_warp(A, st, KID_JUMP, acc);
+    block_add<1>(open, &st->acc_changed);
     if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
       ctrl_after_jump(st);
       log_work(A);
@@ -736,45 +877,69 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
   }
 }
 
-// Extremum reached from v: its tile terminal t when t is an extremum
-// (T[t] == t), else the resolved label of the exit t.
-__device__ __forceinline__ int resolve_label(const int32_t* Tt, const int32_t* L, int v) {
-  const int t = Tt[v];
-  return (Tt[t] == t) ? t : L[t];
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_escatter(GroupArgs<T> A) {
+  const int* pre = A.prefix + K_DENSE * (A.nf + 1);
+  auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_SCATTER; };
+  MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
+    const Field<T>& F = A.fields[i];
+    DevState* st = F.st;
+    const int u = u_ - pre[i];
+    const int nw = (F.G.n + 31) >> 5;
+    const int w = u * kThreads + threadIdx.x;
+    uint32_t nex = 0;
+    if (w < nw) {
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        uint32_t r = F.ub[d][u] + F.ep[d][w];
+        for (uint32_t m = F.ex[d][w]; m; m &= m - 1, ++r) {
+          F.lx[d][(w << 5) + __ffs(m) - 1] = (int32_t)(F.lc[d][r] & ~kRes);
+          ++nex;
+        }
+      }
+    }
+    log_units_warp(A, st, KID_ESCATTER, nex);
+    if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
+      st->lstate = L_DONE;
+      st->ticks++;
+      log_work(A);
+      st->units_done = 0;
+    }
+  }
 }
 
-// R-loop check (Sec. 4.2): count wrong labels; a wrongly labelled vertex whose
-// steepest neighbour in g differs from f's is a troublemaker. Wrong max label:
-// decrease its ascending neighbour in g (Eq. 6). Wrong min label: decrease the
-// descending neighbour that f prescribes.
+// Job 0: f's labels in place of its tile terminals (safe while other threads
+// resolve: a terminal that is an extremum keeps its value, and an exit's
+// label is read from lx). Job 1, the R-loop check (Sec. 4.2): count wrong
+// labels; a wrongly labelled vertex whose steepest neighbour in g differs
+// from f's is a troublemaker. Wrong max label: decrease its ascending
+// neighbour in g (Eq. 6). Wrong min label: decrease the descending neighbour
+// that f prescribes.
 template <class T, int ND>
 __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
-  auto active = [](const Field<T>& F) {
-    return F.st->action == ACT_LABELS && F.st->lstate == L_DONE && F.st->ljob == 1;
-  };
+  auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_DONE; };
   MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
     const int v0 = (u_ - pre[i]) * kDenseChunk;
     const int v1 = min(F.G.n, v0 + kDenseChunk);
+    if (st->ljob == 0) {
+      for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        F.Mf[v] = resolve_label(F.Mf, F.lx[0], v);
+        F.mf[v] = resolve_label(F.mf, F.lx[1], v);
+      }
+      if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
+        ctrl_after_flabels(st);
+        log_work(A);
+        st->units_done = 0;
+      }
+      continue;
+    }
     uint32_t acc[4] = {0, 0, 0, 0};
-    const bool fres = st->f_resolved != 0;
     for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-      int M, m;
-      if (fres) {
-        M = F.Mf[v];
-        m = F.mf[v];
-      } else {  // first R-check: f's labels resolved in place (safe: exits keep their label)
-        M = resolve_label(F.Mf, F.Lfu, v);
-        m = resolve_label(F.mf, F.Lfd, v);
-      }
-      const bool wM = resolve_label(F.Pup, F.Lgu, v) != M;
-      const bool wm = resolve_label(F.Pdn, F.Lgd, v) != m;
-      if (!fres) {
-        F.Mf[v] = M;
-        F.mf[v] = m;
-      }
+      const bool wM = resolve_label(F.Pup, F.lx[0], v) != F.Mf[v];
+      const bool wm = resolve_label(F.Pdn, F.lx[1], v) != F.mf[v];
       acc[0] += wM;
       acc[1] += wm;
       if (wM || wm) {
@@ -838,6 +1003,33 @@ __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
   }
 }
 
+// Graph steps: sets the conditions of this group's step bodies (a field with
+// its full classification sweep pending, one gathering cases, one in a label
+// stage) and counts the kernels the step will launch.
+template <class T>
+__global__ void __launch_bounds__(256) k_decide(GroupArgs<T> A, cudaGraphConditionalHandle hs,
+                                                cudaGraphConditionalHandle hc, cudaGraphConditionalHandle hr,
+                                                unsigned long long* launches, int label_launches) {
+  int s = 0, c = 0, r = 0;
+  for (int i = threadIdx.x; i < A.nf; i += blockDim.x) {
+    const DevState* st = A.fields[i].st;
+    const uint32_t ph = st->phase, act = st->action;
+    s |= (ph == PH_C && act == ACT_NONE);
+    c |= (act == ACT_GATHER);
+    r |= (act == ACT_LABELS);
+  }
+  s = __syncthreads_or(s);
+  c = __syncthreads_or(c);
+  r = __syncthreads_or(r);
+  if (threadIdx.x == 0) {
+    cudaGraphSetConditional(hs, s ? 1u : 0u);
+    cudaGraphSetConditional(hc, c ? 1u : 0u);
+    cudaGraphSetConditional(hr, r ? 1u : 0u);
+    // decide, apply, reclass always; the bodies that run
+    atomicAdd(launches, 3ull + (s ? 1ull : 0ull) + (c ? 1ull : 0ull) + (r ? (unsigned long long)label_launches : 0ull));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Edit list (Sec. 5.3): every vertex whose final value differs bitwise from
 // fhat, ascending. Count per tile, scan per field, write.
@@ -882,8 +1074,8 @@ __global__ void __launch_bounds__(kThreads) k_emit_count(GroupArgs<T> A) {
     for (int k = 0; k < kEmitItems; ++k) {
       const int v = base + k;
       if (v < F.G.n) {
-        F.Pup[v] = resolve_label(F.Pup, F.Lgu, v);
-        F.Pdn[v] = resolve_label(F.Pdn, F.Lgd, v);
+        F.Pup[v] = resolve_label(F.Pup, F.lx[0], v);
+        F.Pdn[v] = resolve_label(F.Pdn, F.lx[1], v);
       }
     }
     __syncthreads();

@@ -36,8 +36,8 @@ def test_kernel_stats_consistent(shape):
     assert a.counts == b.counts
     assert torch.equal(a.edit_idx, b.edit_idx)
     st = {s["name"]: s for s in timed.kernel_stats()}
-    assert list(st) == ["k_csweep", "k_gather_mark", "k_label_tile", "k_einit", "k_jump", "k_rcheck",
-                        "k_apply", "k_reclass"]
+    assert list(st) == ["k_csweep", "k_gather_mark", "k_label_tile", "k_ecount", "k_escan", "k_efill",
+                        "k_jump", "k_escatter", "k_rcheck", "k_apply", "k_reclass"]
     steps = st["k_csweep"]["launches"]
     assert steps > 0
     for name, s in st.items():
@@ -53,13 +53,16 @@ def test_kernel_stats_consistent(shape):
         c[k] for k in ("c_cases_fpmax", "c_cases_fpmin", "c_cases_fnmax", "c_cases_fnmin"))
     assert st["k_apply"]["work_launches"] == rounds + c["r_rounds"]
     assert st["k_reclass"]["work_launches"] == rounds + c["r_rounds"]
-    assert st["k_rcheck"]["work_launches"] == c["label_evals"]
-    assert st["k_rcheck"]["units"] == n * c["label_evals"]
-    # f's labels once, then g's at every evaluation
-    assert st["k_label_tile"]["work_launches"] == c["label_evals"] + 1
-    assert st["k_einit"]["work_launches"] == c["label_evals"] + 1
-    assert 0 < st["k_label_tile"]["units"] <= n * (c["label_evals"] + 1)
-    assert st["k_jump"]["work_launches"] >= st["k_einit"]["work_launches"]
+    # f's labels once (k_rcheck resolves them in place), then g's at every evaluation
+    evals = c["label_evals"] + 1
+    for name in ("k_label_tile", "k_ecount", "k_escan", "k_efill", "k_escatter", "k_rcheck"):
+        assert st[name]["work_launches"] == evals, name
+    assert st["k_rcheck"]["units"] == n * evals
+    assert st["k_ecount"]["units"] == ((n + 31) // 32) * evals
+    assert st["k_escan"]["units"] == evals
+    assert 0 < st["k_label_tile"]["units"] <= n * evals
+    assert st["k_efill"]["units"] == st["k_escatter"]["units"] > 0
+    assert st["k_jump"]["work_launches"] >= evals
     # classification sweeps: one full, one incremental per apply
     assert c["sweeps"] == 1 + rounds + c["r_rounds"]
     plain.close()
