@@ -181,6 +181,37 @@ __device__ __forceinline__ bool units_done_n(DevState* st, uint32_t n, int units
   return s_last_n;
 }
 
+// Per-block completion of a kernel's units, reported per field: the block
+// counts the units it completes of its current field and reports them with
+// one atomic when it moves to another field or runs out of units (instead of
+// one per unit: same-address atomics serialise in L2). flush() first runs
+// pre(st) in every thread (the kernel's own counters), then, in the block
+// that completes the field, done(st) in thread 0.
+struct UnitTally {
+  int cur = -1;
+  uint32_t n = 0;
+  template <class T, class Pre, class Done>
+  __device__ __forceinline__ void flush(const GroupArgs<T>& A, int kind, Pre&& pre, Done&& done) {
+    if (cur < 0) return;
+    DevState* st = A.fields[cur].st;
+    pre(st);
+    if (units_done_n(st, n, A.fields[cur].units[kind]) && threadIdx.x == 0) {
+      done(st);
+      st->units_done = 0;
+    }
+    n = 0;
+  }
+  // at the start of a unit of field i
+  template <class T, class Pre, class Done>
+  __device__ __forceinline__ void enter(const GroupArgs<T>& A, int kind, int i, Pre&& pre, Done&& done) {
+    if (i != cur) {
+      flush(A, kind, pre, done);
+      cur = i;
+    }
+    ++n;
+  }
+};
+
 template <int NW>
 __device__ __forceinline__ void block_add(uint32_t (&v)[NW], uint32_t* dst) {
   __shared__ uint32_t s[NW];

@@ -378,10 +378,6 @@ struct Group {
     k_init<T><<<grid[K_DENSE], kThreads, 0, s>>>(args);
   }
 
-  // Conditions of this group's graph step bodies (see k_decide).
-  cudaGraphConditionalHandle hs = 0, hc = 0, hr = 0;
-  static constexpr int kLabelLaunches = 7 + kJumpsPerStep;  // label_tile .. rcheck
-
   // One loop step, all kernels (each acts only on the fields in its stage).
   // Kernel timing (single-field plans with MSZ_OPT_TIME_KERNELS): e holds
   // kStepEvents events, one before each launch and one after the last; each
@@ -407,7 +403,7 @@ struct Group {
     if (e) cudaEventRecord(e[slot], s);
   }
 
-  // Step pieces (the graph puts the first three under conditions).
+  // Step pieces.
   void sweep(cudaStream_t s, const GroupArgs<T>& x) {
     if (tma) k_csweep<T, ND, true><<<grid[K_SWEEP], SG::NTP, 0, s>>>(x);
     else k_csweep<T, ND, false><<<grid[K_SWEEP], SG::NT, 0, s>>>(x);
@@ -429,9 +425,6 @@ struct Group {
   void tail(cudaStream_t s, A&& a) {
     k_apply<T><<<grid[K_SPARSE], kThreads, 0, s>>>(a());
     k_reclass<T, ND><<<grid[K_SPARSE], kThreads, 0, s>>>(a());
-  }
-  void decide(cudaStream_t s, unsigned long long* launches) {
-    k_decide<T><<<1, 256, 0, s>>>(args, hs, hc, hr, launches, kLabelLaunches);
   }
 
   void emit(cudaStream_t s) {
@@ -481,8 +474,6 @@ struct msz_engine_s {
   double kernel_ms[kKinds] = {0, 0, 0, 0};
   // per-kernel statistics of the last timed run (single-field engines)
   uint32_t* d_steplog = nullptr;
-  unsigned long long* d_launch_count = nullptr;  // kernels the graph steps launched (device count)
-  unsigned long long h_launch_count = 0;
   uint32_t h_steplog[kMaxChunk] = {};
   uint64_t ks_launches[NKID] = {}, ks_work[NKID] = {}, ks_units[NKID] = {};
   double ks_ms[NKID] = {}, ks_work_ms[NKID] = {};
@@ -526,7 +517,6 @@ size_t layout_engine(msz_engine_s* E, unsigned char* base, bool with_outputs) {
   }
   E->d_states = (DevState*)b.take(sizeof(DevState) * E->nf, 256);
   E->d_steplog = (uint32_t*)b.take(sizeof(uint32_t) * kMaxChunk, 256);
-  E->d_launch_count = (unsigned long long*)b.take(sizeof(unsigned long long), 256);
   E->each_group([&](auto& g) { g.carve(b); });
   return b.off;
 }
@@ -716,82 +706,20 @@ void collect_times(msz_engine_s* E, int steps) {
   }
 }
 
-// Captures the work fn(stream) launches into graph g after the nodes in tail;
-// tail becomes the captured work's last nodes.
-template <class Fn>
-bool capture_into(cudaGraph_t g, std::vector<cudaGraphNode_t>& tail, cudaStream_t s, Fn&& fn) {
-  if (cudaStreamBeginCaptureToGraph(s, g, tail.empty() ? nullptr : tail.data(), nullptr, tail.size(),
-                                    cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-    return false;
-  fn(s);
-  cudaStreamCaptureStatus cs;
-  const cudaGraphNode_t* deps = nullptr;
-  size_t nd = 0;
-  const bool info = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess;
-  std::vector<cudaGraphNode_t> next;
-  if (info) next.assign(deps, deps + nd);
-  cudaGraph_t out = nullptr;
-  if (cudaStreamEndCapture(s, &out) != cudaSuccess || !info) return false;
-  tail.swap(next);
-  return true;
-}
-
-// Adds "if (condition h) { fn(stream) }" after tail; tail becomes that node.
-template <class Fn>
-bool add_if(cudaGraph_t g, std::vector<cudaGraphNode_t>& tail, cudaGraphConditionalHandle h, cudaStream_t s,
-            Fn&& fn) {
-  cudaGraphNodeParams p{};
-  p.type = cudaGraphNodeTypeConditional;
-  p.conditional.handle = h;
-  p.conditional.type = cudaGraphCondTypeIf;
-  p.conditional.size = 1;
-  cudaGraphNode_t node = nullptr;
-  if (cudaGraphAddNode(&node, g, tail.empty() ? nullptr : tail.data(), nullptr, tail.size(), &p) != cudaSuccess)
-    return false;
-  std::vector<cudaGraphNode_t> none;
-  if (!capture_into(p.conditional.phGraph_out[0], none, s, fn)) return false;
-  tail.assign(1, node);
-  return true;
-}
-
-// Builds the graph of kGraphSteps loop steps of every group once. A group's
-// step: k_decide, then the full sweep, the case gather and the label stages
-// each under its condition, then apply and reclassification; so a step
-// launches only the kernels some field of the group needs.
+// Captures kGraphSteps steps of every group once (on a private stream). Each
+// step launches every kernel; a kernel whose fields are all in other stages
+// returns at once (about a microsecond in a graph).
 int ensure_graph(msz_engine_s* E) {
   if (E->graph) return MSZ_OK;
   if (!E->cap_stream && cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return MSZ_ERR_CUDA;
   cudaGraph_t gr = nullptr;
-  if (cudaGraphCreate(&gr, 0) != cudaSuccess) return MSZ_ERR_CUDA;
-  bool ok = true;
-  E->each_group([&](auto& g) {
-    if (g.empty() || !ok) return;
-    ok = cudaGraphConditionalHandleCreate(&g.hs, gr, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
-         cudaGraphConditionalHandleCreate(&g.hc, gr, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
-         cudaGraphConditionalHandleCreate(&g.hr, gr, 0, cudaGraphCondAssignDefault) == cudaSuccess;
-  });
-  std::vector<cudaGraphNode_t> tail;
-  cudaStream_t cs = E->cap_stream;
-  for (int i = 0; ok && i < kGraphSteps; ++i) {
-    E->each_group([&](auto& g) {
-      if (g.empty() || !ok) return;
-      auto plain = [&]() { return g.args; };
-      ok = capture_into(gr, tail, cs, [&](cudaStream_t s) { g.decide(s, E->d_launch_count); }) &&
-           add_if(gr, tail, g.hs, cs, [&](cudaStream_t s) { g.sweep(s, g.args); }) &&
-           add_if(gr, tail, g.hc, cs, [&](cudaStream_t s) { g.gather(s, g.args); }) &&
-           add_if(gr, tail, g.hr, cs, [&](cudaStream_t s) { g.labels(s, plain); }) &&
-           capture_into(gr, tail, cs, [&](cudaStream_t s) { g.tail(s, plain); });
-    });
-  }
-  if (ok) ok = cudaGraphInstantiate(&E->graph, gr, 0) == cudaSuccess;
+  if (cudaStreamBeginCapture(E->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MSZ_ERR_CUDA;
+  for (int i = 0; i < kGraphSteps; ++i) E->each_group([&](auto& g) { g.step(E->cap_stream); });
+  if (cudaStreamEndCapture(E->cap_stream, &gr) != cudaSuccess) return MSZ_ERR_CUDA;
+  const cudaError_t r = cudaGraphInstantiate(&E->graph, gr, 0);
   cudaGraphDestroy(gr);
-  if (!ok) {
-    cudaGetLastError();
-    E->graph = nullptr;
-    return MSZ_ERR_CUDA;
-  }
-  return MSZ_OK;
+  return r == cudaSuccess ? MSZ_OK : MSZ_ERR_CUDA;
 }
 
 // Runs every field of the engine to completion. f / fhat / xi are indexed
@@ -832,8 +760,6 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
   }
   if (timed && cudaMemsetAsync(E->d_steplog, 0, sizeof(uint32_t) * kMaxChunk, s) != cudaSuccess) return MSZ_ERR_CUDA;
   const bool graph = E->use_graph && !timed && ensure_graph(E) == MSZ_OK;
-  if (graph && cudaMemsetAsync(E->d_launch_count, 0, sizeof(unsigned long long), s) != cudaSuccess)
-    return MSZ_ERR_CUDA;
   // Steps in growing chunks; one state read per chunk. A chunk in which no
   // field's state machine moved means a stall.
   int chunk = 1;
@@ -841,6 +767,7 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
   for (;;) {
     if (graph) {
       for (int i = 0; i < chunk; ++i) cudaGraphLaunch(E->graph, s);
+      E->launches += (uint64_t)chunk * kGraphSteps * E->launches_per_step();
     } else {
       launch_steps(E, s, std::min(chunk * kGraphSteps, kMaxChunk), timed);
     }
@@ -878,11 +805,7 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
   if (E->ev1) cudaEventRecord(E->ev1, s);
   if (cudaMemcpyAsync(H, E->d_states, sizeof(DevState) * nf, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return MSZ_ERR_CUDA;
-  if (graph && cudaMemcpyAsync(&E->h_launch_count, E->d_launch_count, sizeof(unsigned long long),
-                               cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return MSZ_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return MSZ_ERR_CUDA;
-  if (graph) E->launches += E->h_launch_count;
   if (cudaGetLastError() != cudaSuccess) return MSZ_ERR_CUDA;
   if (timed && nf == 1) {
     for (int k = 0; k < NKID; ++k) E->ks_units[k] = H[0].kunits[k];

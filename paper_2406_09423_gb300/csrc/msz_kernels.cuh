@@ -5,6 +5,17 @@
 
 namespace msz {
 
+// Asynchronous copy of one element global -> shared (cp.async, cached in
+// L1 and L2), and the wait for all of the thread's copies.
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "element of 4 or 8 bytes");
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  if (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <int ND>
 struct LabelGeom {
   static constexpr int TX = (ND == 3) ? 32 : 64;
@@ -46,13 +57,16 @@ __device__ __forceinline__ void mark_dirty_tiles(uint8_t* tdirty, const Geom& G,
 
 // Next unit of this block (u, u + gridDim.x, ...) whose field satisfies
 // active(field); the units of an inactive field are skipped in O(1), so a
-// kernel with nothing to do costs one lookup per field and block.
+// kernel with nothing to do costs one lookup per field and block. fi holds
+// the field of the block's previous unit, known active: a field's state only
+// changes once all of its units of the launch are done, so while the block
+// has units of it left it needs no new check.
 template <class T, class Pred>
 __device__ __forceinline__ int next_active_unit(const GroupArgs<T>& A, const int* pre, int total, int u, Pred active,
                                                 int& fi) {
   while (u < total) {
     const int i = field_of_unit(pre, A.nf, u);
-    if (active(A.fields[i])) {
+    if (i == fi || active(A.fields[i])) {
       fi = i;
       return u;
     }
@@ -62,8 +76,8 @@ __device__ __forceinline__ int next_active_unit(const GroupArgs<T>& A, const int
   return total;
 }
 
-#define MSZ_ACTIVE_UNITS(A, KIND, PRE, FI, PRED)                                                     \
-  for (int FI = 0, u_ = next_active_unit((A), (PRE), (A).total[KIND], (int)blockIdx.x, (PRED), FI); \
+#define MSZ_ACTIVE_UNITS(A, KIND, PRE, FI, PRED)                                                      \
+  for (int FI = -1, u_ = next_active_unit((A), (PRE), (A).total[KIND], (int)blockIdx.x, (PRED), FI); \
        u_ < (A).total[KIND]; u_ = next_active_unit((A), (PRE), (A).total[KIND], u_ + (int)gridDim.x, (PRED), FI))
 
 // ---------------------------------------------------------------------------
@@ -74,7 +88,11 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_init(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
   auto active = [](const Field<T>& F) { return F.st->phase == PH_INIT; };
+  auto none = [](DevState*) {};
+  auto done = [](DevState* st) { ctrl_after_init(st); };
+  UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
+    tl.enter(A, K_DENSE, i, none, done);
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
     const int v0 = (u_ - pre[i]) * kDenseChunk;
@@ -108,11 +126,8 @@ __global__ void __launch_bounds__(kThreads) k_init(GroupArgs<T> A) {
       const int ncc = 4 * F.units[K_EMIT], pc = (ncc + nu - 1) / nu;
       for (int t = lu * pc + threadIdx.x; t < min(ncc, (lu + 1) * pc); t += blockDim.x) F.ccnt[t] = 0;
     }
-    if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
-      ctrl_after_init(st);
-      st->units_done = 0;
-    }
   }
+  tl.flush(A, K_DENSE, none, done);
 }
 
 // ---------------------------------------------------------------------------
@@ -149,7 +164,7 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
     int u, i, x0, y0, c0, ppt;
   };
   auto next_tile = [&](Tile& t, int u) -> bool {
-    int i = 0;
+    int i = -1;  // no cached field: the producer warp and the consumers decide alike
     u = next_active_unit(
         A, pre, A.total[K_SWEEP], u,
         [](const Field<T>& F) { return F.st->phase == PH_C && F.st->action == ACT_NONE; }, i);
@@ -443,7 +458,18 @@ __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
   constexpr int NPOS = Slots<ND>::NPOS;
   constexpr int R = 2 * NPOS + 1;
   auto active = [](const Field<T>& F) { return F.st->action == ACT_RECLASS; };
+  uint32_t acc[4] = {0, 0, 0, 0};
+  auto pre_flush = [&](DevState* st) {
+    block_add<4>(acc, st->counts);
+    acc[0] = acc[1] = acc[2] = acc[3] = 0;
+  };
+  auto done = [&](DevState* st) {
+    ctrl_after_classify(st);
+    log_work(A);
+  };
+  UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_SPARSE, pre, i, active) {
+    tl.enter(A, K_SPARSE, i, pre_flush, done);
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
     const Geom G = F.G;
@@ -452,7 +478,6 @@ __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
     const int S = F.units[K_SPARSE], k = u_ - pre[i];
     const uint64_t b = items * (uint64_t)k / (uint64_t)S, e = items * (uint64_t)(k + 1) / (uint64_t)S;
     if (threadIdx.x == 0) log_units(A, st, KID_RECLASS, e - b);
-    uint32_t acc[4] = {0, 0, 0, 0};
     for (uint64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
       const int u = (int)F.touched[j / R];
       const int s = (int)(j % R);
@@ -484,13 +509,8 @@ __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
         }
       }
     }
-    block_add<4>(acc, st->counts);
-    if (unit_done(st, S) && threadIdx.x == 0) {
-      ctrl_after_classify(st);
-      log_work(A);
-      st->units_done = 0;
-    }
   }
+  tl.flush(A, K_SPARSE, pre_flush, done);
 }
 
 // ---------------------------------------------------------------------------
@@ -527,7 +547,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
   constexpr int kSegs = (LG::SX + 31) / 32;
   __shared__ uint32_t exs[2][kExWords];
   auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_INIT; };
+  auto none = [](DevState*) {};
+  auto done = [&](DevState* st) {
+    st->lstate = L_COUNT;
+    st->ticks++;
+    log_work(A);
+  };
+  UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_LABEL, pre, fi, active) {
+    tl.enter(A, K_LABEL, fi, none, done);
     const Field<T>& F = A.fields[fi];
     DevState* st = F.st;
     const bool job = st->ljob != 0;
@@ -542,20 +570,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
     // g's terminals only change in tiles whose tile or halo was edited
     const bool redo = !job || F.tdirty[tile];
     __syncthreads();
-    if (!redo) {
-      if (unit_done(st, F.units[K_LABEL]) && threadIdx.x == 0) {
-        st->lstate = L_COUNT;
-        st->ticks++;
-        log_work(A);
-        st->units_done = 0;
-      }
-      continue;
-    }
+    if (!redo) continue;
     const int x0 = (tile % tiles_x) * LG::TX;
     const int y0 = ((tile / tiles_x) % tiles_y) * LG::TY;
     const int z0 = (tile / (tiles_x * tiles_y)) * LG::TZ;
     __syncthreads();
     for (int k = threadIdx.x; k < 2 * kExWords; k += kThreads) exs[k / kExWords][k % kExWords] = 0u;
+    // halo values: every in-grid cell by an asynchronous global -> shared
+    // copy (all of the block's copies in flight at once), the others NaN
     for (int row = warp; row < LG::ROWS; row += kThreads / 32) {
       const int hy = row % LG::SY, hz = row / LG::SY;
       const int gy = y0 - 1 + hy, gz = (ND == 3) ? z0 - 1 + hz : 0;
@@ -564,11 +586,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
       for (int hx = lane; hx < LG::SX; hx += 32) {
         const int gx = x0 - 1 + hx;
         const int h = hx + HS * row;
-        val[h] = (rin && gx >= 0 && gx < G.nx) ? src[rbase + gx] : qnan<T>();
+        if (rin && gx >= 0 && gx < G.nx) cp_async_elem(&val[h], src + rbase + gx);
+        else val[h] = qnan<T>();
         Pu[h] = (uint16_t)h;
         Pd[h] = (uint16_t)h;
       }
     }
+    cp_async_wait_all();
     __syncthreads();
     uint8_t dbyte[LG::PER_THREAD];
 #pragma unroll
@@ -669,13 +693,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
     if (threadIdx.x == 0)
       log_units(A, st, KID_LABEL,
                 (uint64_t)min(LG::TX, G.nx - x0) * min(LG::TY, G.ny - y0) * min(LG::TZ, G.nz - z0));
-    if (unit_done(st, F.units[K_LABEL]) && threadIdx.x == 0) {
-      st->lstate = L_COUNT;
-      st->ticks++;
-      log_work(A);
-      st->units_done = 0;
-    }
   }
+  tl.flush(A, K_LABEL, none, done);
 }
 
 // Labels, second level (Sec. 5.2, across tiles). The tile exits of a
@@ -704,7 +723,16 @@ __global__ void __launch_bounds__(kThreads) k_ecount(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
   __shared__ uint32_t wsum[2][kThreads / 32];
   auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_COUNT; };
+  auto none = [](DevState*) {};
+  auto done = [&](DevState* st) {
+    st->lstate = L_SCAN;
+    st->ticks++;
+    log_work(A);
+  };
+  UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
+    tl.enter(A, K_DENSE, i, none, done);
+    __syncthreads();  // wsum of the block's previous unit is read
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
     const int u = u_ - pre[i];
@@ -743,13 +771,8 @@ __global__ void __launch_bounds__(kThreads) k_ecount(GroupArgs<T> A) {
       F.ep[1][w] = wsum[1][warp] + incl[1] - c[1];
     }
     log_units_warp(A, st, KID_ECOUNT, (w < nw) ? 1u : 0u);
-    if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
-      st->lstate = L_SCAN;
-      st->ticks++;
-      log_work(A);
-      st->units_done = 0;
-    }
   }
+  tl.flush(A, K_DENSE, none, done);
 }
 
 // Exclusive scan of the unit exit counts of both directions, one block per
@@ -806,11 +829,23 @@ __global__ void __launch_bounds__(1024) k_escan(GroupArgs<T> A) {
   }
 }
 
+// One bitmap word per thread; the word's exits (ranks r, r + 1, ...) are
+// handled in batches of kBatch so that their loads are in flight together.
+constexpr int kBatch = 8;
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_efill(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
   auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_FILL; };
+  auto none = [](DevState*) {};
+  auto done = [&](DevState* st) {
+    st->lstate = L_JUMP;
+    st->jump_rounds = 0;
+    st->ticks++;
+    log_work(A);
+  };
+  UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
+    tl.enter(A, K_DENSE, i, none, done);
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
     const bool job = st->ljob != 0;
@@ -823,23 +858,34 @@ __global__ void __launch_bounds__(kThreads) k_efill(GroupArgs<T> A) {
       for (int d = 0; d < 2; ++d) {
         const int32_t* Tt = d ? (job ? F.Pdn : F.mf) : (job ? F.Pup : F.Mf);
         uint32_t r = F.ub[d][u] + F.ep[d][w];
-        for (uint32_t m = F.ex[d][w]; m; m &= m - 1, ++r) {
-          const int e = (w << 5) + __ffs(m) - 1;
-          const uint32_t t = (uint32_t)Tt[e];
-          F.lc[d][r] = (t & kExt) ? ((t & ~kExt) | kRes) : exit_rank(F.ex[d], F.ep[d], F.ub[d], (int)t);
-          ++nex;
+        uint32_t m = F.ex[d][w];
+        nex += __popc(m);
+        while (m) {
+          int e[kBatch];
+          uint32_t t[kBatch];
+          int c = 0;
+#pragma unroll
+          for (int j = 0; j < kBatch; ++j) {
+            e[j] = m ? (w << 5) + __ffs(m) - 1 : -1;
+            if (m) {
+              m &= m - 1;
+              ++c;
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < kBatch; ++j) t[j] = (e[j] >= 0) ? (uint32_t)Tt[e[j]] : kExt;
+#pragma unroll
+          for (int j = 0; j < kBatch; ++j)
+            if (j < c)
+              F.lc[d][r + j] =
+                  (t[j] & kExt) ? ((t[j] & ~kExt) | kRes) : exit_rank(F.ex[d], F.ep[d], F.ub[d], (int)t[j]);
+          r += c;
         }
       }
     }
     log_units_warp(A, st, KID_EFILL, nex);
-    if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
-      st->lstate = L_JUMP;
-      st->jump_rounds = 0;
-      st->ticks++;
-      log_work(A);
-      st->units_done = 0;
-    }
   }
+  tl.flush(A, K_DENSE, none, done);
 }
 
 // One round of pointer jumping on the compact exit tables: an entry that
@@ -849,11 +895,22 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
   auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_JUMP; };
+  uint32_t open[1] = {0};
+  auto pre_flush = [&](DevState* st) {
+    block_add<1>(open, &st->acc_changed);
+    open[0] = 0;
+  };
+  auto done = [&](DevState* st) {
+    ctrl_after_jump(st);
+    log_work(A);
+  };
+  UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
+    tl.enter(A, K_DENSE, i, pre_flush, done);
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
     const uint32_t r0 = (uint32_t)(u_ - pre[i]) * kDenseChunk;
-    uint32_t open[1] = {0}, acc = 0;
+    uint32_t acc = 0;
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
       const uint32_t ne = st->nexit[d];
@@ -868,20 +925,23 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
       }
     }
     log_units_warp(A, st, KID_JUMP, acc);
-    block_add<1>(open, &st->acc_changed);
-    if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
-      ctrl_after_jump(st);
-      log_work(A);
-      st->units_done = 0;
-    }
   }
+  tl.flush(A, K_DENSE, pre_flush, done);
 }
 
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_escatter(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
   auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_SCATTER; };
+  auto none = [](DevState*) {};
+  auto done = [&](DevState* st) {
+    st->lstate = L_DONE;
+    st->ticks++;
+    log_work(A);
+  };
+  UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
+    tl.enter(A, K_DENSE, i, none, done);
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
     const int u = u_ - pre[i];
@@ -892,20 +952,28 @@ __global__ void __launch_bounds__(kThreads) k_escatter(GroupArgs<T> A) {
 #pragma unroll
       for (int d = 0; d < 2; ++d) {
         uint32_t r = F.ub[d][u] + F.ep[d][w];
-        for (uint32_t m = F.ex[d][w]; m; m &= m - 1, ++r) {
-          F.lx[d][(w << 5) + __ffs(m) - 1] = (int32_t)(F.lc[d][r] & ~kRes);
-          ++nex;
+        uint32_t m = F.ex[d][w];
+        nex += __popc(m);
+        while (m) {
+          int e[kBatch];
+          uint32_t lab[kBatch];
+#pragma unroll
+          for (int j = 0; j < kBatch; ++j) {
+            e[j] = m ? (w << 5) + __ffs(m) - 1 : -1;
+            if (m) m &= m - 1;
+          }
+#pragma unroll
+          for (int j = 0; j < kBatch; ++j) lab[j] = (e[j] >= 0) ? F.lc[d][r + j] : 0u;
+#pragma unroll
+          for (int j = 0; j < kBatch; ++j)
+            if (e[j] >= 0) F.lx[d][e[j]] = (int32_t)(lab[j] & ~kRes);
+          r += kBatch;
         }
       }
     }
     log_units_warp(A, st, KID_ESCATTER, nex);
-    if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
-      st->lstate = L_DONE;
-      st->ticks++;
-      log_work(A);
-      st->units_done = 0;
-    }
   }
+  tl.flush(A, K_DENSE, none, done);
 }
 
 // Job 0: f's labels in place of its tile terminals (safe while other threads
@@ -919,7 +987,19 @@ template <class T, int ND>
 __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
   auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_DONE; };
+  uint32_t acc[4] = {0, 0, 0, 0};
+  auto pre_flush = [&](DevState* st) {
+    block_add<4>(acc, st->acc_r);
+    acc[0] = acc[1] = acc[2] = acc[3] = 0;
+  };
+  auto done = [&](DevState* st) {
+    if (st->ljob == 0) ctrl_after_flabels(st);
+    else ctrl_after_rcheck(st);
+    log_work(A);
+  };
+  UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
+    tl.enter(A, K_DENSE, i, pre_flush, done);
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
     const int v0 = (u_ - pre[i]) * kDenseChunk;
@@ -929,14 +1009,8 @@ __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
         F.Mf[v] = resolve_label(F.Mf, F.lx[0], v);
         F.mf[v] = resolve_label(F.mf, F.lx[1], v);
       }
-      if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
-        ctrl_after_flabels(st);
-        log_work(A);
-        st->units_done = 0;
-      }
       continue;
     }
-    uint32_t acc[4] = {0, 0, 0, 0};
     for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
       const bool wM = resolve_label(F.Pup, F.lx[0], v) != F.Mf[v];
       const bool wm = resolve_label(F.Pdn, F.lx[1], v) != F.mf[v];
@@ -954,13 +1028,8 @@ __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
         }
       }
     }
-    block_add<4>(acc, st->acc_r);
-    if (unit_done(st, F.units[K_DENSE]) && threadIdx.x == 0) {
-      ctrl_after_rcheck(st);
-      log_work(A);
-      st->units_done = 0;
-    }
   }
+  tl.flush(A, K_DENSE, pre_flush, done);
 }
 
 // Applies a round's requests to the touched vertices only. Units are slices
@@ -969,15 +1038,24 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
   const int* pre = A.prefix + K_SPARSE * (A.nf + 1);
   auto active = [](const Field<T>& F) { return F.st->action == ACT_MARK_C || F.st->action == ACT_APPLY_R; };
+  uint32_t acc[2] = {0, 0};
+  auto pre_flush = [&](DevState* st) {
+    block_add<2>(acc, st->acc_ap);
+    acc[0] = acc[1] = 0;
+  };
+  auto done = [&](DevState* st) {
+    ctrl_after_apply(st, st->action);  // the action this launch applied
+    log_work(A);
+  };
+  UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_SPARSE, pre, i, active) {
+    tl.enter(A, K_SPARSE, i, pre_flush, done);
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
-    const uint32_t act = st->action;
     const uint32_t nt = st->ntouch;
     const int S = F.units[K_SPARSE], k = u_ - pre[i];
     const uint32_t b = (uint32_t)(((uint64_t)nt * k) / S), e = (uint32_t)(((uint64_t)nt * (k + 1)) / S);
     if (threadIdx.x == 0) log_units(A, st, KID_APPLY, e - b);
-    uint32_t acc[2] = {0, 0};
     for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) {
       const int u = (int)F.touched[j];
       uint8_t bb = F.flags[u];
@@ -994,40 +1072,8 @@ __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
       if (F.G.nd == 3) mark_dirty_tiles<3>(F.tdirty, F.G, u);
       else mark_dirty_tiles<2>(F.tdirty, F.G, u);
     }
-    block_add<2>(acc, st->acc_ap);
-    if (unit_done(st, S) && threadIdx.x == 0) {
-      ctrl_after_apply(st, act);
-      log_work(A);
-      st->units_done = 0;
-    }
   }
-}
-
-// Graph steps: sets the conditions of this group's step bodies (a field with
-// its full classification sweep pending, one gathering cases, one in a label
-// stage) and counts the kernels the step will launch.
-template <class T>
-__global__ void __launch_bounds__(256) k_decide(GroupArgs<T> A, cudaGraphConditionalHandle hs,
-                                                cudaGraphConditionalHandle hc, cudaGraphConditionalHandle hr,
-                                                unsigned long long* launches, int label_launches) {
-  int s = 0, c = 0, r = 0;
-  for (int i = threadIdx.x; i < A.nf; i += blockDim.x) {
-    const DevState* st = A.fields[i].st;
-    const uint32_t ph = st->phase, act = st->action;
-    s |= (ph == PH_C && act == ACT_NONE);
-    c |= (act == ACT_GATHER);
-    r |= (act == ACT_LABELS);
-  }
-  s = __syncthreads_or(s);
-  c = __syncthreads_or(c);
-  r = __syncthreads_or(r);
-  if (threadIdx.x == 0) {
-    cudaGraphSetConditional(hs, s ? 1u : 0u);
-    cudaGraphSetConditional(hc, c ? 1u : 0u);
-    cudaGraphSetConditional(hr, r ? 1u : 0u);
-    // decide, apply, reclass always; the bodies that run
-    atomicAdd(launches, 3ull + (s ? 1ull : 0ull) + (c ? 1ull : 0ull) + (r ? (unsigned long long)label_launches : 0ull));
-  }
+  tl.flush(A, K_SPARSE, pre_flush, done);
 }
 
 // ---------------------------------------------------------------------------
