@@ -54,15 +54,32 @@ __device__ __forceinline__ int slot_offset(int s, int nd, int nx, int nxny) {
   return neg ? -o : o;
 }
 
+// Division of 0 <= x < 2^31 by an invariant d >= 1 through one multiply-high
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994): with s = ceil(log2 d) and
+// m = floor(2^32 (2^s - d) / d) + 1, x / d = (mulhi(x, m) + x) >> s; the sum
+// does not overflow since mulhi(x, m) <= x < 2^31.
+struct FastDiv {
+  uint32_t m, s;
+};
+inline FastDiv fast_div(uint32_t d) {
+  FastDiv f{1u, 0u};
+  while ((1ull << f.s) < d) ++f.s;
+  f.m = (uint32_t)((((1ull << 32) * ((1ull << f.s) - d)) / d) + 1);
+  return f;
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, FastDiv f) { return (__umulhi(x, f.m) + x) >> f.s; }
+
 struct Geom {
   int nx, ny, nz, nxny, n, nd;
+  FastDiv dx, dy;  // division by nx and by ny
 };
 
 __device__ __forceinline__ void coords(const Geom& G, int v, int& x, int& y, int& z) {
-  x = v % G.nx;
-  const int t = v / G.nx;
-  y = t % G.ny;
-  z = t / G.ny;
+  const int t = (int)fdiv((uint32_t)v, G.dx);
+  x = v - t * G.nx;
+  z = (int)fdiv((uint32_t)t, G.dy);
+  y = t - z * G.ny;
 }
 
 // ---------------------------------------------------------------------------

@@ -31,9 +31,12 @@ namespace msz {
 enum : uint32_t { PH_INIT = 0, PH_FLABELS = 1, PH_C = 2, PH_R = 3, PH_DONE = 4, PH_ERR = 5 };
 // Actions within a phase. In PH_C, ACT_NONE means the field's first (full)
 // classification sweep is pending; afterwards a C round runs ACT_GATHER
-// (cases of the current type -> requests), ACT_MARK_C (apply) and
-// ACT_RECLASS (reclassify the closed 1-rings of the edited vertices).
-enum : uint32_t { ACT_NONE = 0, ACT_MARK_C = 1, ACT_LABELS = 2, ACT_APPLY_R = 3, ACT_GATHER = 4, ACT_RECLASS = 5 };
+// (list the cases of the current type), ACT_REQUEST (their requests),
+// ACT_MARK_C (apply) and ACT_RECLASS (reclassify the closed 1-rings of the
+// edited vertices).
+enum : uint32_t {
+  ACT_NONE = 0, ACT_MARK_C = 1, ACT_LABELS = 2, ACT_APPLY_R = 3, ACT_GATHER = 4, ACT_RECLASS = 5, ACT_REQUEST = 6
+};
 // Stages of one label evaluation (job 0: f, job 1: g): tile terminals, exit
 // counts, exit ranks, compact exit table, pointer jumping on it, labels back
 // to the exit vertices, then f's labels in place (job 0) or the R-loop check.
@@ -54,8 +57,8 @@ constexpr int kCaseTiles = kThreads / 32;          // case-count tiles per gathe
 
 // Kernels of a loop step, in launch order of their kinds (per-kernel timing).
 enum {
-  KID_SWEEP = 0, KID_GATHER, KID_LABEL, KID_ECOUNT, KID_ESCAN, KID_EFILL, KID_JUMP, KID_ESCATTER, KID_RCHECK,
-  KID_APPLY, KID_RECLASS, NKID
+  KID_SWEEP = 0, KID_GATHER, KID_MARK, KID_LABEL, KID_ECOUNT, KID_ESCAN, KID_EFILL, KID_JUMP, KID_ESCATTER,
+  KID_RCHECK, KID_APPLY, KID_RECLASS, NKID
 };
 
 // Per-field device state (one contiguous array per engine).
@@ -64,6 +67,7 @@ struct DevState {
   int32_t status;
   uint32_t counts[4];  // false critical points of g per type (kept current by every classification)
   uint32_t ntouch;  // entries of the touched list (apply, then reclassification)
+  uint32_t ncase;   // entries of the case list (the round's cases of the current type)
   uint32_t acc_changed;
   uint32_t acc_ap[2];  // apply: decreases, freezes
   uint32_t acc_r[4];   // rcheck: wrong max, wrong min, asc troublemakers, desc troublemakers
@@ -96,6 +100,7 @@ struct Field {
   int32_t* lx[2];   // label of every exit vertex (scattered back from lc)
   uint8_t* tdirty;  // label tiles whose terminals must be recomputed
   uint8_t* cls;     // false-type bits of g per vertex (FPmax, FPmin, FNmax, FNmin), padded to kEmitTile
+  uint32_t* cases;  // the round's cases of the current type
   uint32_t* epoch;  // round in which a vertex was last reclassified (claims a vertex once per round)
   uint32_t* ccnt;   // false critical points per kEmitTile-vertex tile and type: [tile][4]
   uint32_t* touched;
@@ -156,6 +161,21 @@ __device__ __forceinline__ void log_units_warp(const GroupArgs<T>& A, DevState* 
   if (!A.steplog) return;
   n = __reduce_add_sync(kFull, n);
   if ((threadIdx.x & 31) == 0 && n) atomicAdd((unsigned long long*)&st->kunits[kid], (unsigned long long)n);
+}
+
+// Sparse kernels: the units of a field (S fixed at setup) share a list of
+// `items` entries known only at run time; only as many units as give each
+// thread about one entry take part, so short lists still spread over many
+// blocks. [b, e) is unit k's slice (empty for the units left out).
+__device__ __forceinline__ void sparse_slice(uint64_t items, int S, int k, uint64_t& b, uint64_t& e) {
+  const uint64_t want = (items + kThreads - 1) / kThreads;
+  const uint64_t act = want < (uint64_t)S ? (want ? want : 1) : (uint64_t)S;
+  if ((uint64_t)k >= act) {
+    b = e = 0;
+    return;
+  }
+  b = items * (uint64_t)k / act;
+  e = items * (uint64_t)(k + 1) / act;
 }
 
 // Completion of one unit of a field by the whole block: true in the block
@@ -254,7 +274,7 @@ __device__ void ctrl_after_init(DevState* st) {
 __device__ void ctrl_after_classify(DevState* st) {
   uint32_t c[4];
   for (int t = 0; t < 4; ++t) c[t] = vload(&st->counts[t]);
-  st->ntouch = 0;
+  st->ntouch = st->ncase = 0;
   if (vload(&st->err_bits) & E_TIMEOUT) {
     st->phase = PH_ERR;
     st->status = MSZ_ERR_TIMEOUT;
@@ -384,22 +404,43 @@ __device__ void request(const Field<T>& F, int a, int t) {
     mark(F, t, FL_DEC);
     return;
   }
+  // Freeze the non-frozen closed 1-ring of a. The ring's flag loads, then its
+  // flag atomics, are issued together; the vertices newly marked join the
+  // touched list with one atomic.
+  constexpr int NPOS = Slots<ND>::NPOS;
+  constexpr int R = 2 * NPOS + 1;
   int x, y, z;
   coords(F.G, a, x, y, z);
-  if (!(F.flags[a] & FL_FROZEN)) mark(F, a, FL_FREEZE);
-  constexpr int NPOS = Slots<ND>::NPOS;
+  int us[R];
 #pragma unroll
-  for (int s = 0; s < 2 * NPOS; ++s) {
+  for (int s = 0; s < R; ++s) {
+    if (s == 2 * NPOS) {
+      us[s] = a;
+      continue;
+    }
     const int sg = (s < NPOS) ? 1 : -1;
     const int m = (int)((Slots<ND>::MASKS >> (4 * (s < NPOS ? s : s - NPOS))) & 7u);
     const int dx = sg * (m & 1), dy = sg * ((m >> 1) & 1), dz = sg * ((m >> 2) & 1);
     const int X = x + dx, Y = y + dy, Z = z + dz;
     bool in = X >= 0 && X < F.G.nx && Y >= 0 && Y < F.G.ny;
     if (ND == 3) in = in && Z >= 0 && Z < F.G.nz;
-    if (in) {
-      const int u = a + dx + dy * F.G.nx + dz * F.G.nxny;
-      if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE);
-    }
+    us[s] = in ? a + dx + dy * F.G.nx + dz * F.G.nxny : -1;
+  }
+  uint8_t fl[R];
+#pragma unroll
+  for (int s = 0; s < R; ++s) fl[s] = (us[s] >= 0) ? F.flags[us[s]] : (uint8_t)FL_FROZEN;
+  uint32_t fresh = 0;
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    if (fl[s] & FL_FROZEN) continue;
+    const int u = us[s];
+    const int sh = (u & 3) * 8;
+    const uint32_t old = atomicOr(reinterpret_cast<uint32_t*>(F.flags) + (u >> 2), (uint32_t)FL_FREEZE << sh);
+    if (((old >> sh) & (FL_DEC | FL_FREEZE)) == 0) fresh |= 1u << s;
+  }
+  if (fresh) {
+    uint32_t k = atomicAdd(&F.st->ntouch, (uint32_t)__popc(fresh));
+    for (; fresh; fresh &= fresh - 1) F.touched[k++] = (uint32_t)us[__ffs(fresh) - 1];
   }
 }
 

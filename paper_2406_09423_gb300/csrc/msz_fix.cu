@@ -63,6 +63,8 @@ bool geom_from(int ndim, const int64_t* dims, Geom& G) {
   G.nxny = (int)(nx * ny);
   G.n = (int)n;
   G.nd = ndim;
+  G.dx = fast_div((uint32_t)nx);
+  G.dy = fast_div((uint32_t)ny);
   return true;
 }
 
@@ -142,6 +144,7 @@ struct FieldBufs {
   int32_t* lx[2] = {nullptr, nullptr};
   uint8_t* tdirty = nullptr;
   uint8_t* cls = nullptr;
+  uint32_t* cases = nullptr;
   uint32_t* epoch = nullptr;
   uint32_t* ccnt = nullptr;
   uint32_t* touched = nullptr;
@@ -181,6 +184,7 @@ void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs
   }
   B.tdirty = (uint8_t*)b.take((size_t)label_tiles(G));
   B.cls = (uint8_t*)b.take(nt * kEmitTile);
+  B.cases = (uint32_t*)b.take(n * 4);
   B.epoch = (uint32_t*)b.take(n * 4);
   B.ccnt = (uint32_t*)b.take(nt * 4 * 4);
   B.touched = (uint32_t*)b.take(n * 4);
@@ -197,17 +201,17 @@ void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs
 // One (dtype, dimension) group of an engine's fields.
 // ---------------------------------------------------------------------------
 constexpr int kJumpsPerStep = 4;
-constexpr int kStepSlots = 10 + kJumpsPerStep;  // launches per step (without graph conditionals)
+constexpr int kStepSlots = 11 + kJumpsPerStep;  // launches per step
 constexpr int kStepEvents = kStepSlots + 1;
 // kernel of each launch slot of a step
-constexpr int kSlotKernel[kStepSlots] = {KID_SWEEP, KID_GATHER,   KID_LABEL,  KID_ECOUNT, KID_ESCAN,
-                                         KID_EFILL, KID_JUMP,     KID_JUMP,   KID_JUMP,   KID_JUMP,
-                                         KID_ESCATTER, KID_RCHECK, KID_APPLY, KID_RECLASS};
+constexpr int kSlotKernel[kStepSlots] = {KID_SWEEP,  KID_GATHER, KID_MARK,     KID_LABEL,  KID_ECOUNT,
+                                         KID_ESCAN,  KID_EFILL,  KID_JUMP,     KID_JUMP,   KID_JUMP,
+                                         KID_JUMP,   KID_ESCATTER, KID_RCHECK, KID_APPLY, KID_RECLASS};
 static_assert(kJumpsPerStep == 4, "slot table assumes four jump launches per step");
 static_assert(NKID == MSZ_NUM_KERNELS, "kernel table and ABI disagree");
-const char* const kKernelNames[NKID] = {"k_csweep", "k_gather_mark", "k_label_tile", "k_ecount",
-                                        "k_escan",  "k_efill",       "k_jump",       "k_escatter",
-                                        "k_rcheck", "k_apply",       "k_reclass"};
+const char* const kKernelNames[NKID] = {"k_csweep", "k_gather", "k_mark",     "k_label_tile",
+                                        "k_ecount", "k_escan",  "k_efill",    "k_jump",
+                                        "k_escatter", "k_rcheck", "k_apply",  "k_reclass"};
 
 template <class T, int ND>
 struct Group {
@@ -306,6 +310,7 @@ struct Group {
       }
       F.tdirty = B.tdirty;
       F.cls = B.cls;
+      F.cases = B.cases;
       F.epoch = B.epoch;
       F.ccnt = B.ccnt;
       F.touched = B.touched;
@@ -318,7 +323,7 @@ struct Group {
       F.units[K_DENSE] = (G.n + kDenseChunk - 1) / kDenseChunk;
       F.units[K_SWEEP] = F.TL.ntiles;
       F.units[K_LABEL] = label_tiles(G);
-      F.units[K_SPARSE] = std::max(1, std::min(1024, (G.n + 65535) / 65536));
+      F.units[K_SPARSE] = std::max(1, std::min(4096, G.n / 2048));
       F.units[K_EMIT] = emit_tiles(G);
       F.units[K_CASE] = (emit_tiles(G) + kCaseTiles - 1) / kCaseTiles;
       if (tma && !encode(&h_maps[2 * j], G, B.g, B.fdir)) tma = false;
@@ -341,7 +346,7 @@ struct Group {
     grid[K_DENSE] = occ_grid((const void*)k_jump<T>, kThreads, 0, args.total[K_DENSE]);
     grid[K_SPARSE] = occ_grid((const void*)k_apply<T>, kThreads, 0, args.total[K_SPARSE]);
     grid[K_EMIT] = occ_grid((const void*)k_emit_write<T>, kThreads, 0, args.total[K_EMIT]);
-    grid[K_CASE] = occ_grid((const void*)k_gather_mark<T, ND>, kThreads, 0, args.total[K_CASE]);
+    grid[K_CASE] = occ_grid((const void*)k_gather<T, ND>, kThreads, 0, args.total[K_CASE]);
     grid[K_SWEEP] = tma ? occ_grid((const void*)k_csweep<T, ND, true>, SG::NTP, 0, args.total[K_SWEEP])
                         : occ_grid((const void*)k_csweep<T, ND, false>, SG::NT, 0, args.total[K_SWEEP]);
     label_smem = label_smem_bytes<T, ND>();
@@ -397,7 +402,7 @@ struct Group {
       return x;
     };
     sweep(s, a());
-    gather(s, a());
+    gather(s, a);
     labels(s, a);
     tail(s, a);
     if (e) cudaEventRecord(e[slot], s);
@@ -408,8 +413,10 @@ struct Group {
     if (tma) k_csweep<T, ND, true><<<grid[K_SWEEP], SG::NTP, 0, s>>>(x);
     else k_csweep<T, ND, false><<<grid[K_SWEEP], SG::NT, 0, s>>>(x);
   }
-  void gather(cudaStream_t s, const GroupArgs<T>& x) {
-    k_gather_mark<T, ND><<<grid[K_CASE], kThreads, 0, s>>>(x);
+  template <class A>
+  void gather(cudaStream_t s, A&& a) {
+    k_gather<T, ND><<<grid[K_CASE], kThreads, 0, s>>>(a());
+    k_mark<T, ND><<<grid[K_SPARSE], kThreads, 0, s>>>(a());
   }
   template <class A>
   void labels(cudaStream_t s, A&& a) {
@@ -698,7 +705,7 @@ void collect_times(msz_engine_s* E, int steps) {
         E->ks_work_ms[kid] += dt;
       }
       const int kind = (kid == KID_SWEEP || kid == KID_RECLASS)         ? 0
-                       : (kid == KID_GATHER || kid == KID_APPLY)         ? 3
+                       : (kid == KID_GATHER || kid == KID_MARK || kid == KID_APPLY) ? 3
                        : (kid == KID_RCHECK)                             ? 2
                                                                          : 1;  // label stages
       E->kernel_ms[kind] += dt;

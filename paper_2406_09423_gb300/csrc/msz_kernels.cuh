@@ -387,37 +387,28 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
   }
 }
 
-// C-loop requests for the field's current type (Eqs. 2-5), gathered from
-// the per-vertex false-type bits; only tiles that hold cases of the type are
-// read. FPmax and FNmin edit the false vertex itself; FPmin and FNmax edit
-// its neighbour that is maximal in g, which is its steepest ascent since it
-// is not a maximum of g's ring. A unit is kCaseTiles case-count tiles, one
-// per warp; a block reports its completed units of a field with one atomic.
+// The round's cases of the field's current type, listed from the per-vertex
+// false-type bits; only tiles that hold cases of the type are read. A unit
+// is kCaseTiles case-count tiles, one per warp; each 512-byte chunk of a
+// tile appends its cases with one atomic per warp.
 template <class T, int ND>
-__global__ void __launch_bounds__(kThreads) k_gather_mark(GroupArgs<T> A) {
+__global__ void __launch_bounds__(kThreads) k_gather(GroupArgs<T> A) {
   const int* pre = A.prefix + K_CASE * (A.nf + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto active = [](const Field<T>& F) { return F.st->action == ACT_GATHER; };
-  int cur = -1;
-  uint32_t ndone = 0, ncases = 0;
-  auto flush = [&]() {
-    if (cur >= 0) log_units_warp(A, A.fields[cur].st, KID_GATHER, ncases);
+  uint32_t ncases = 0;
+  auto pre_flush = [&](DevState* st) {
+    log_units_warp(A, st, KID_GATHER, ncases);
     ncases = 0;
-    if (cur >= 0 && units_done_n(A.fields[cur].st, ndone, A.fields[cur].units[K_CASE]) && threadIdx.x == 0) {
-      DevState* st = A.fields[cur].st;
-      st->action = ACT_MARK_C;
-      st->ticks++;
-      log_work(A);
-      st->units_done = 0;
-    }
   };
+  auto done = [&](DevState* st) {
+    st->action = ACT_REQUEST;
+    st->ticks++;
+    log_work(A);
+  };
+  UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_CASE, pre, i, active) {
-    if (i != cur) {
-      flush();
-      cur = i;
-      ndone = 0;
-    }
-    ++ndone;
+    tl.enter(A, K_CASE, i, pre_flush, done);
     const Field<T>& F = A.fields[i];
     const uint32_t type = F.st->T;
     const int tile = (u_ - pre[i]) * kCaseTiles + warp;
@@ -426,23 +417,63 @@ __global__ void __launch_bounds__(kThreads) k_gather_mark(GroupArgs<T> A) {
     for (int r = 0; r < kEmitTile / (32 * 16); ++r) {
       const int base = tile * kEmitTile + (r * 32 + lane) * 16;
       const uint4 q = *reinterpret_cast<const uint4*>(F.cls + base);
-      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+      const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
       uint32_t hits = 0;  // bit k: byte k holds a case of the type
 #pragma unroll
-      for (int k = 0; k < 16; ++k) hits |= ((w[k >> 2] >> (8 * (k & 3) + type)) & 1u) << k;
+      for (int k = 0; k < 16; ++k) hits |= ((w4[k >> 2] >> (8 * (k & 3) + type)) & 1u) << k;
       if (F.G.n - base < 16) hits &= (F.G.n - base > 0) ? (1u << (F.G.n - base)) - 1u : 0u;  // padding
-      ncases += __popc(hits);
-      for (; hits; hits &= hits - 1) {
-        const int v = base + __ffs(hits) - 1;
-        int x, y, z;
-        coords(F.G, v, x, y, z);
-        const uint8_t d = direction_of<T, ND>(F.g, F.G, v, x, y, z);
-        const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny);
-        request<T, ND>(F, v, t);
+      const uint32_t c = __popc(hits);
+      uint32_t incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
       }
+      const uint32_t total = __shfl_sync(kFull, incl, 31);
+      if (!total) continue;
+      uint32_t at = 0;
+      if (lane == 31) at = atomicAdd(&F.st->ncase, total);
+      at = __shfl_sync(kFull, at, 31) + incl - c;
+      for (; hits; hits &= hits - 1) F.cases[at++] = (uint32_t)(base + __ffs(hits) - 1);
+      ncases += c;
     }
   }
-  flush();
+  tl.flush(A, K_CASE, pre_flush, done);
+}
+
+// C-loop requests for the listed cases (Eqs. 2-5), one case per thread over
+// the whole grid: FPmax and FNmin edit the false vertex itself; FPmin and
+// FNmax edit its neighbour that is maximal in g, which is its steepest ascent
+// since it is not a maximum of g's ring.
+template <class T, int ND>
+__global__ void __launch_bounds__(kThreads) k_mark(GroupArgs<T> A) {
+  const int* pre = A.prefix + K_SPARSE * (A.nf + 1);
+  auto active = [](const Field<T>& F) { return F.st->action == ACT_REQUEST; };
+  auto none = [](DevState*) {};
+  auto done = [&](DevState* st) {
+    st->action = ACT_MARK_C;
+    st->ticks++;
+    log_work(A);
+  };
+  UnitTally tl;
+  MSZ_ACTIVE_UNITS(A, K_SPARSE, pre, i, active) {
+    tl.enter(A, K_SPARSE, i, none, done);
+    const Field<T>& F = A.fields[i];
+    DevState* st = F.st;
+    const uint32_t type = st->T;
+    uint64_t b, e;
+    sparse_slice(st->ncase, F.units[K_SPARSE], u_ - pre[i], b, e);
+    if (threadIdx.x == 0) log_units(A, st, KID_MARK, e - b);
+    for (uint64_t j = b + threadIdx.x; j < e; j += kThreads) {
+      const int v = (int)F.cases[j];
+      int x, y, z;
+      coords(F.G, v, x, y, z);
+      const uint8_t d = direction_of<T, ND>(F.g, F.G, v, x, y, z);
+      const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny);
+      request<T, ND>(F, v, t);
+    }
+  }
+  tl.flush(A, K_SPARSE, none, done);
 }
 
 // Incremental classification after an apply. A vertex's false-type bits
@@ -474,9 +505,8 @@ __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
     DevState* st = F.st;
     const Geom G = F.G;
     const uint32_t stamp = (uint32_t)st->rounds;
-    const uint64_t items = (uint64_t)st->ntouch * R;
-    const int S = F.units[K_SPARSE], k = u_ - pre[i];
-    const uint64_t b = items * (uint64_t)k / (uint64_t)S, e = items * (uint64_t)(k + 1) / (uint64_t)S;
+    uint64_t b, e;
+    sparse_slice((uint64_t)st->ntouch * R, F.units[K_SPARSE], u_ - pre[i], b, e);
     if (threadIdx.x == 0) log_units(A, st, KID_RECLASS, e - b);
     for (uint64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
       const int u = (int)F.touched[j / R];
@@ -526,7 +556,7 @@ __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
 template <class T, int ND>
 size_t label_smem_bytes() {
   using LG = LabelGeom<ND>;
-  return ((LG::HALO * sizeof(T) + 15) / 16) * 16 + 2 * ((LG::HALO + 7) / 8) * 8 * sizeof(uint16_t);
+  return ((LG::HALO * sizeof(T) + 15) / 16) * 16 + (size_t)LG::HALO * sizeof(uint32_t);
 }
 
 template <class T, int ND>
@@ -536,8 +566,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
   T* val = reinterpret_cast<T*>(lsm);
   // Pointers in halo coordinates: halo cells and extrema point to themselves
   // (terminal); interior cells to their steepest neighbour.
-  uint16_t* Pu = reinterpret_cast<uint16_t*>(lsm + ((LG::HALO * sizeof(T) + 15) / 16) * 16);
-  uint16_t* Pd = Pu + ((LG::HALO + 7) / 8) * 8;
+  // ascending pointer (low 16 bits) and descending pointer (high 16 bits)
+  uint32_t* PP = reinterpret_cast<uint32_t*>(lsm + ((LG::HALO * sizeof(T) + 15) / 16) * 16);
   const int* pre = A.prefix + K_LABEL * (A.nf + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int HS = LG::SX, HSS = LG::SX * LG::SY;
@@ -588,8 +618,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
         const int h = hx + HS * row;
         if (rin && gx >= 0 && gx < G.nx) cp_async_elem(&val[h], src + rbase + gx);
         else val[h] = qnan<T>();
-        Pu[h] = (uint16_t)h;
-        Pd[h] = (uint16_t)h;
+        PP[h] = (uint32_t)h | ((uint32_t)h << 16);
       }
     }
     cp_async_wait_all();
@@ -600,8 +629,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
       const int i = threadIdx.x + k * kThreads;
       const int lx = i % LG::TX, ly = (i / LG::TX) % LG::TY, lz = i / (LG::TX * LG::TY);
       const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
+      // best candidate so far as (offset * 16 + slot): one select per winner
       T hv = -INFINITY, lv = INFINITY;
-      int hs = kSelf, ls = kSelf, ho = 0, lo = 0;
+      int hp = kSelf, lp = kSelf;
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         int o, slot;
@@ -617,28 +647,35 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
           o = tab[j][0];
           slot = tab[j][1];
         }
+        const int pk = o * 16 + slot;
         const T uval = val[c + o];
-        if (uval >= hv) { hv = uval; hs = slot; ho = o; }
-        if (uval < lv) { lv = uval; ls = slot; lo = o; }
+        if (uval >= hv) { hv = uval; hp = pk; }
+        if (uval < lv) { lv = uval; lp = pk; }
       }
-      dbyte[k] = (uint8_t)(hs | (ls << 4));
-      if (val[c] == val[c]) {  // cells outside the grid are NaN and keep self pointers
-        Pu[c] = (uint16_t)(c + ho);
-        Pd[c] = (uint16_t)(c + lo);
-      }
+      dbyte[k] = (uint8_t)((hp & 15) | ((lp & 15) << 4));
+      if (val[c] == val[c])  // cells outside the grid are NaN and keep self pointers
+        PP[c] = (uint32_t)(c + (hp >> 4)) | ((uint32_t)(c + (lp >> 4)) << 16);
     }
     __syncthreads();
+    // pointer doubling; a cell whose two pointers reach terminals is done
+    uint32_t live = (1u << LG::PER_THREAD) - 1u;
     for (int round = 0; round < 2 * LG::TV; ++round) {
       int changed = 0;
 #pragma unroll
       for (int k = 0; k < LG::PER_THREAD; ++k) {
+        if (!((live >> k) & 1u)) continue;
         const int i = threadIdx.x + k * kThreads;
         const int lx = i % LG::TX, ly = (i / LG::TX) % LG::TY, lz = i / (LG::TX * LG::TY);
         const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
-        const int a = Pu[c], a2 = Pu[a];
-        if (a2 != a) { Pu[c] = (uint16_t)a2; changed = 1; }
-        const int b = Pd[c], b2 = Pd[b];
-        if (b2 != b) { Pd[c] = (uint16_t)b2; changed = 1; }
+        const uint32_t p = PP[c];
+        const uint32_t a = p & 0xffffu, b = p >> 16;
+        const uint32_t a2 = PP[a] & 0xffffu, b2 = PP[b] >> 16;
+        if (a2 == a && b2 == b) {
+          live &= ~(1u << k);
+        } else {
+          PP[c] = a2 | (b2 << 16);
+          changed = 1;
+        }
       }
       if (!__syncthreads_or(changed)) break;
     }
@@ -662,8 +699,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
           return (int)((uint32_t)e | (halo ? 0u : kExt));
         };
         dir[v] = dbyte[k];
-        OA[v] = global_of(Pu[c], exs[0]);
-        OB[v] = global_of(Pd[c], exs[1]);
+        const uint32_t p = PP[c];
+        OA[v] = global_of((int)(p & 0xffffu), exs[0]);
+        OB[v] = global_of((int)(p >> 16), exs[1]);
       }
     }
     __syncthreads();
@@ -889,8 +927,8 @@ __global__ void __launch_bounds__(kThreads) k_efill(GroupArgs<T> A) {
 }
 
 // One round of pointer jumping on the compact exit tables: an entry that
-// holds a rank takes the entry it points to. Units are kDenseChunk entries of
-// the table. A round that finds no rank left ends the jumping.
+// holds a rank takes the entry it points to. Each dense unit takes an equal
+// share of both tables. A round that finds no rank left ends the jumping.
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
@@ -909,19 +947,30 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
     tl.enter(A, K_DENSE, i, pre_flush, done);
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
-    const uint32_t r0 = (uint32_t)(u_ - pre[i]) * kDenseChunk;
+    const uint64_t u = (uint64_t)(u_ - pre[i]), U = (uint64_t)F.units[K_DENSE];
     uint32_t acc = 0;
+    constexpr int kJB = 4;  // entries per thread and iteration, loads issued together
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
-      const uint32_t ne = st->nexit[d];
+      // this unit's equal share of the direction's table
+      const uint64_t ne = st->nexit[d];
+      const uint32_t r0 = (uint32_t)(ne * u / U), re = (uint32_t)(ne * (u + 1) / U);
       uint32_t* lc = F.lc[d];
-      for (uint32_t r = r0 + threadIdx.x; r < min(ne, r0 + (uint32_t)kDenseChunk); r += kThreads) {
-        const uint32_t x = lc[r];
-        ++acc;
-        if (x & kRes) continue;
-        lc[r] = lc[x];
-        ++open[0];
-        acc += 2;
+      for (uint32_t rb = r0 + threadIdx.x; rb < re; rb += kJB * kThreads) {
+        uint32_t x[kJB], y[kJB];
+#pragma unroll
+        for (int k = 0; k < kJB; ++k) x[k] = (rb + k * kThreads < re) ? lc[rb + k * kThreads] : kRes;
+#pragma unroll
+        for (int k = 0; k < kJB; ++k) y[k] = (x[k] & kRes) ? 0u : lc[x[k]];
+#pragma unroll
+        for (int k = 0; k < kJB; ++k) {
+          if (rb + k * kThreads >= re) continue;
+          ++acc;
+          if (x[k] & kRes) continue;
+          lc[rb + k * kThreads] = y[k];
+          ++open[0];
+          acc += 2;
+        }
       }
     }
     log_units_warp(A, st, KID_JUMP, acc);
@@ -1011,20 +1060,45 @@ __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
       }
       continue;
     }
-    for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-      const bool wM = resolve_label(F.Pup, F.lx[0], v) != F.Mf[v];
-      const bool wm = resolve_label(F.Pdn, F.lx[1], v) != F.mf[v];
-      acc[0] += wM;
-      acc[1] += wm;
-      if (wM || wm) {
+    // kRB vertices per thread and iteration, their loads issued together
+    constexpr int kRB = 4;
+    for (int vb = v0 + threadIdx.x; vb < v1; vb += kRB * kThreads) {
+      uint32_t tu[kRB], td[kRB];
+      int32_t M[kRB], m[kRB];
+#pragma unroll
+      for (int k = 0; k < kRB; ++k) {
+        const int v = vb + k * kThreads;
+        const bool in = v < v1;
+        tu[k] = in ? (uint32_t)F.Pup[v] : kExt;
+        td[k] = in ? (uint32_t)F.Pdn[v] : kExt;
+        M[k] = in ? F.Mf[v] : 0;
+        m[k] = in ? F.mf[v] : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < kRB; ++k) {
+        tu[k] = (tu[k] & kExt) ? (tu[k] & ~kExt) : (uint32_t)F.lx[0][tu[k]];
+        td[k] = (td[k] & kExt) ? (td[k] & ~kExt) : (uint32_t)F.lx[1][td[k]];
+      }
+      uint32_t wrong = 0;  // bit 2k: max label wrong, bit 2k+1: min label wrong
+#pragma unroll
+      for (int k = 0; k < kRB; ++k)
+        if (vb + k * kThreads < v1)
+          wrong |= ((uint32_t)((int32_t)tu[k] != M[k]) << (2 * k)) | ((uint32_t)((int32_t)td[k] != m[k]) << (2 * k + 1));
+      for (; wrong; wrong &= wrong - 1) {
+        const int bit = __ffs(wrong) - 1, v = vb + (bit >> 1) * kThreads;
         const uint8_t d = F.gdir[v], fd = F.fdir[v];
-        if (wM && (d & 15) != (fd & 15)) {
-          ++acc[2];
-          request<T, ND>(F, v, v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny));
-        }
-        if (wm && (d >> 4) != (fd >> 4)) {
-          ++acc[3];
-          request<T, ND>(F, v, v + slot_offset(fd >> 4, ND, F.G.nx, F.G.nxny));
+        if ((bit & 1) == 0) {
+          ++acc[0];
+          if ((d & 15) != (fd & 15)) {
+            ++acc[2];
+            request<T, ND>(F, v, v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny));
+          }
+        } else {
+          ++acc[1];
+          if ((d >> 4) != (fd >> 4)) {
+            ++acc[3];
+            request<T, ND>(F, v, v + slot_offset(fd >> 4, ND, F.G.nx, F.G.nxny));
+          }
         }
       }
     }
@@ -1052,9 +1126,9 @@ __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
     tl.enter(A, K_SPARSE, i, pre_flush, done);
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
-    const uint32_t nt = st->ntouch;
-    const int S = F.units[K_SPARSE], k = u_ - pre[i];
-    const uint32_t b = (uint32_t)(((uint64_t)nt * k) / S), e = (uint32_t)(((uint64_t)nt * (k + 1)) / S);
+    uint64_t b64, e64;
+    sparse_slice(st->ntouch, F.units[K_SPARSE], u_ - pre[i], b64, e64);
+    const uint32_t b = (uint32_t)b64, e = (uint32_t)e64;
     if (threadIdx.x == 0) log_units(A, st, KID_APPLY, e - b);
     for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) {
       const int u = (int)F.touched[j];

@@ -36,7 +36,7 @@ def test_kernel_stats_consistent(shape):
     assert a.counts == b.counts
     assert torch.equal(a.edit_idx, b.edit_idx)
     st = {s["name"]: s for s in timed.kernel_stats()}
-    assert list(st) == ["k_csweep", "k_gather_mark", "k_label_tile", "k_ecount", "k_escan", "k_efill",
+    assert list(st) == ["k_csweep", "k_gather", "k_mark", "k_label_tile", "k_ecount", "k_escan", "k_efill",
                         "k_jump", "k_escatter", "k_rcheck", "k_apply", "k_reclass"]
     steps = st["k_csweep"]["launches"]
     assert steps > 0
@@ -48,9 +48,10 @@ def test_kernel_stats_consistent(shape):
     n = f.size
     assert st["k_csweep"]["work_launches"] == 1 and st["k_csweep"]["units"] == n
     rounds = sum(c[k] for k in ("c_rounds_fpmax", "c_rounds_fpmin", "c_rounds_fnmax", "c_rounds_fnmin"))
-    assert st["k_gather_mark"]["work_launches"] == rounds
-    assert st["k_gather_mark"]["units"] == sum(
-        c[k] for k in ("c_cases_fpmax", "c_cases_fpmin", "c_cases_fnmax", "c_cases_fnmin"))
+    cases = sum(c[k] for k in ("c_cases_fpmax", "c_cases_fpmin", "c_cases_fnmax", "c_cases_fnmin"))
+    for name in ("k_gather", "k_mark"):
+        assert st[name]["work_launches"] == rounds, name
+        assert st[name]["units"] == cases, name
     assert st["k_apply"]["work_launches"] == rounds + c["r_rounds"]
     assert st["k_reclass"]["work_launches"] == rounds + c["r_rounds"]
     # f's labels once (k_rcheck resolves them in place), then g's at every evaluation
