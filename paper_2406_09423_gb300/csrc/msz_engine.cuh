@@ -61,6 +61,8 @@ enum {
   KID_RCHECK, KID_APPLY, KID_RECLASS, NKID
 };
 
+constexpr int kStripes = 16;
+
 // Per-field device state (one contiguous array per engine).
 struct DevState {
   uint32_t phase, action, T, lstate, ljob, units_done, err_bits;
@@ -71,6 +73,10 @@ struct DevState {
   uint32_t acc_changed;
   uint32_t acc_ap[2];  // apply: decreases, freezes
   uint32_t acc_r[4];   // rcheck: wrong max, wrong min, asc troublemakers, desc troublemakers
+  // Blocks add their partial counters to stripe blockIdx % kStripes (not one
+  // address: same-address atomics serialise in L2); the completing thread
+  // folds the stripes into the counters above (see fold_stripes).
+  uint32_t stripe[kStripes][4];
   uint32_t jump_rounds, emitted;
   uint32_t nexit[2];  // tile exits (ascending, descending lines) of the current evaluation
   uint64_t rounds, max_rounds, n_edits;
@@ -165,17 +171,19 @@ __device__ __forceinline__ void log_units_warp(const GroupArgs<T>& A, DevState* 
 
 // Sparse kernels: the units of a field (S fixed at setup) share a list of
 // `items` entries known only at run time; only as many units as give each
-// thread about one entry take part, so short lists still spread over many
-// blocks. [b, e) is unit k's slice (empty for the units left out).
-__device__ __forceinline__ void sparse_slice(uint64_t items, int S, int k, uint64_t& b, uint64_t& e) {
+// thread about one entry take part (returned; they alone count towards the
+// field's completion), so short lists still spread over many blocks and idle
+// blocks report nothing. [b, e) is unit k's slice (empty for the others).
+__device__ __forceinline__ uint32_t sparse_slice(uint64_t items, int S, int k, uint64_t& b, uint64_t& e) {
   const uint64_t want = (items + kThreads - 1) / kThreads;
   const uint64_t act = want < (uint64_t)S ? (want ? want : 1) : (uint64_t)S;
   if ((uint64_t)k >= act) {
     b = e = 0;
-    return;
+  } else {
+    b = items * (uint64_t)k / act;
+    e = items * (uint64_t)(k + 1) / act;
   }
-  b = items * (uint64_t)k / act;
-  e = items * (uint64_t)(k + 1) / act;
+  return (uint32_t)act;
 }
 
 // Completion of one unit of a field by the whole block: true in the block
@@ -210,12 +218,13 @@ __device__ __forceinline__ bool units_done_n(DevState* st, uint32_t n, int units
 struct UnitTally {
   int cur = -1;
   uint32_t n = 0;
+  uint32_t target = 0;  // units that complete the field (0: all of the kind's units)
   template <class T, class Pre, class Done>
   __device__ __forceinline__ void flush(const GroupArgs<T>& A, int kind, Pre&& pre, Done&& done) {
     if (cur < 0) return;
     DevState* st = A.fields[cur].st;
     pre(st);
-    if (units_done_n(st, n, A.fields[cur].units[kind]) && threadIdx.x == 0) {
+    if (units_done_n(st, n, target ? (int)target : A.fields[cur].units[kind]) && threadIdx.x == 0) {
       done(st);
       st->units_done = 0;
     }
@@ -249,6 +258,24 @@ __device__ __forceinline__ void block_add(uint32_t (&v)[NW], uint32_t* dst) {
   if (threadIdx.x < NW && s[threadIdx.x]) atomicAdd(&dst[threadIdx.x], s[threadIdx.x]);
 }
 
+// block_add into the block's stripe of st->stripe (counters 0 .. NW-1).
+template <int NW>
+__device__ __forceinline__ void block_add_striped(uint32_t (&v)[NW], DevState* st) {
+  block_add<NW>(v, &st->stripe[blockIdx.x % kStripes][0]);
+}
+
+// Sums the stripes of counters 0 .. nw-1 into dst (mod 2^32) and clears them.
+__device__ __forceinline__ void fold_stripes(DevState* st, uint32_t* dst, int nw) {
+  for (int k = 0; k < nw; ++k) {
+    uint32_t sum = 0;
+    for (int s = 0; s < kStripes; ++s) {
+      sum += vload(&st->stripe[s][k]);
+      st->stripe[s][k] = 0;
+    }
+    dst[k] += sum;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // State transitions (run by one thread of the block completing the field)
 // ---------------------------------------------------------------------------
@@ -272,6 +299,7 @@ __device__ void ctrl_after_init(DevState* st) {
 // clean. The type counts are those of the current g, so advancing the type
 // needs no new sweep.
 __device__ void ctrl_after_classify(DevState* st) {
+  fold_stripes(st, st->counts, 4);  // the reclassification's count changes
   uint32_t c[4];
   for (int t = 0; t < 4; ++t) c[t] = vload(&st->counts[t]);
   st->ntouch = st->ncase = 0;
@@ -301,6 +329,7 @@ __device__ void ctrl_after_classify(DevState* st) {
 }
 
 __device__ void ctrl_after_jump(DevState* st) {
+  fold_stripes(st, &st->acc_changed, 1);
   const uint32_t c = vload(&st->acc_changed);
   st->acc_changed = 0;
   st->jump_rounds++;
@@ -323,6 +352,7 @@ __device__ void ctrl_after_flabels(DevState* st) {
 }
 
 __device__ void ctrl_after_rcheck(DevState* st) {
+  fold_stripes(st, st->acc_r, 4);
   const uint32_t wM = vload(&st->acc_r[0]), wm = vload(&st->acc_r[1]);
   const uint32_t ta = vload(&st->acc_r[2]), td = vload(&st->acc_r[3]);
   st->cnt.label_evals++;
@@ -343,6 +373,7 @@ __device__ void ctrl_after_rcheck(DevState* st) {
 }
 
 __device__ void ctrl_after_apply(DevState* st, uint32_t act) {
+  fold_stripes(st, st->acc_ap, 2);
   st->cnt.dec_edits += vload(&st->acc_ap[0]);
   st->cnt.freezes += vload(&st->acc_ap[1]);
   st->ticks++;
@@ -404,43 +435,22 @@ __device__ void request(const Field<T>& F, int a, int t) {
     mark(F, t, FL_DEC);
     return;
   }
-  // Freeze the non-frozen closed 1-ring of a. The ring's flag loads, then its
-  // flag atomics, are issued together; the vertices newly marked join the
-  // touched list with one atomic.
-  constexpr int NPOS = Slots<ND>::NPOS;
-  constexpr int R = 2 * NPOS + 1;
   int x, y, z;
   coords(F.G, a, x, y, z);
-  int us[R];
+  if (!(F.flags[a] & FL_FROZEN)) mark(F, a, FL_FREEZE);
+  constexpr int NPOS = Slots<ND>::NPOS;
 #pragma unroll
-  for (int s = 0; s < R; ++s) {
-    if (s == 2 * NPOS) {
-      us[s] = a;
-      continue;
-    }
+  for (int s = 0; s < 2 * NPOS; ++s) {
     const int sg = (s < NPOS) ? 1 : -1;
     const int m = (int)((Slots<ND>::MASKS >> (4 * (s < NPOS ? s : s - NPOS))) & 7u);
     const int dx = sg * (m & 1), dy = sg * ((m >> 1) & 1), dz = sg * ((m >> 2) & 1);
     const int X = x + dx, Y = y + dy, Z = z + dz;
     bool in = X >= 0 && X < F.G.nx && Y >= 0 && Y < F.G.ny;
     if (ND == 3) in = in && Z >= 0 && Z < F.G.nz;
-    us[s] = in ? a + dx + dy * F.G.nx + dz * F.G.nxny : -1;
-  }
-  uint8_t fl[R];
-#pragma unroll
-  for (int s = 0; s < R; ++s) fl[s] = (us[s] >= 0) ? F.flags[us[s]] : (uint8_t)FL_FROZEN;
-  uint32_t fresh = 0;
-#pragma unroll
-  for (int s = 0; s < R; ++s) {
-    if (fl[s] & FL_FROZEN) continue;
-    const int u = us[s];
-    const int sh = (u & 3) * 8;
-    const uint32_t old = atomicOr(reinterpret_cast<uint32_t*>(F.flags) + (u >> 2), (uint32_t)FL_FREEZE << sh);
-    if (((old >> sh) & (FL_DEC | FL_FREEZE)) == 0) fresh |= 1u << s;
-  }
-  if (fresh) {
-    uint32_t k = atomicAdd(&F.st->ntouch, (uint32_t)__popc(fresh));
-    for (; fresh; fresh &= fresh - 1) F.touched[k++] = (uint32_t)us[__ffs(fresh) - 1];
+    if (in) {
+      const int u = a + dx + dy * F.G.nx + dz * F.G.nxny;
+      if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE);
+    }
   }
 }
 

@@ -457,12 +457,14 @@ __global__ void __launch_bounds__(kThreads) k_mark(GroupArgs<T> A) {
   };
   UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_SPARSE, pre, i, active) {
-    tl.enter(A, K_SPARSE, i, none, done);
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
-    const uint32_t type = st->T;
     uint64_t b, e;
-    sparse_slice(st->ncase, F.units[K_SPARSE], u_ - pre[i], b, e);
+    const uint32_t act = sparse_slice(st->ncase, F.units[K_SPARSE], u_ - pre[i], b, e);
+    if ((uint32_t)(u_ - pre[i]) >= act) continue;  // left out: not counted
+    tl.enter(A, K_SPARSE, i, none, done);
+    tl.target = act;
+    const uint32_t type = st->T;
     if (threadIdx.x == 0) log_units(A, st, KID_MARK, e - b);
     for (uint64_t j = b + threadIdx.x; j < e; j += kThreads) {
       const int v = (int)F.cases[j];
@@ -491,7 +493,7 @@ __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
   auto active = [](const Field<T>& F) { return F.st->action == ACT_RECLASS; };
   uint32_t acc[4] = {0, 0, 0, 0};
   auto pre_flush = [&](DevState* st) {
-    block_add<4>(acc, st->counts);
+    block_add_striped<4>(acc, st);
     acc[0] = acc[1] = acc[2] = acc[3] = 0;
   };
   auto done = [&](DevState* st) {
@@ -500,13 +502,15 @@ __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
   };
   UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_SPARSE, pre, i, active) {
-    tl.enter(A, K_SPARSE, i, pre_flush, done);
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
+    uint64_t b, e;
+    const uint32_t act = sparse_slice((uint64_t)st->ntouch * R, F.units[K_SPARSE], u_ - pre[i], b, e);
+    if ((uint32_t)(u_ - pre[i]) >= act) continue;  // left out: not counted
+    tl.enter(A, K_SPARSE, i, pre_flush, done);
+    tl.target = act;
     const Geom G = F.G;
     const uint32_t stamp = (uint32_t)st->rounds;
-    uint64_t b, e;
-    sparse_slice((uint64_t)st->ntouch * R, F.units[K_SPARSE], u_ - pre[i], b, e);
     if (threadIdx.x == 0) log_units(A, st, KID_RECLASS, e - b);
     for (uint64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
       const int u = (int)F.touched[j / R];
@@ -935,7 +939,7 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
   auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_JUMP; };
   uint32_t open[1] = {0};
   auto pre_flush = [&](DevState* st) {
-    block_add<1>(open, &st->acc_changed);
+    block_add_striped<1>(open, st);
     open[0] = 0;
   };
   auto done = [&](DevState* st) {
@@ -1038,7 +1042,7 @@ __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
   auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_DONE; };
   uint32_t acc[4] = {0, 0, 0, 0};
   auto pre_flush = [&](DevState* st) {
-    block_add<4>(acc, st->acc_r);
+    block_add_striped<4>(acc, st);
     acc[0] = acc[1] = acc[2] = acc[3] = 0;
   };
   auto done = [&](DevState* st) {
@@ -1114,7 +1118,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
   auto active = [](const Field<T>& F) { return F.st->action == ACT_MARK_C || F.st->action == ACT_APPLY_R; };
   uint32_t acc[2] = {0, 0};
   auto pre_flush = [&](DevState* st) {
-    block_add<2>(acc, st->acc_ap);
+    block_add_striped<2>(acc, st);
     acc[0] = acc[1] = 0;
   };
   auto done = [&](DevState* st) {
@@ -1123,11 +1127,13 @@ __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
   };
   UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_SPARSE, pre, i, active) {
-    tl.enter(A, K_SPARSE, i, pre_flush, done);
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
     uint64_t b64, e64;
-    sparse_slice(st->ntouch, F.units[K_SPARSE], u_ - pre[i], b64, e64);
+    const uint32_t act = sparse_slice(st->ntouch, F.units[K_SPARSE], u_ - pre[i], b64, e64);
+    if ((uint32_t)(u_ - pre[i]) >= act) continue;  // left out: not counted
+    tl.enter(A, K_SPARSE, i, pre_flush, done);
+    tl.target = act;
     const uint32_t b = (uint32_t)b64, e = (uint32_t)e64;
     if (threadIdx.x == 0) log_units(A, st, KID_APPLY, e - b);
     for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) {
