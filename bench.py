@@ -114,8 +114,6 @@ def kernel_bytes(name, st, n, es):
                   read and table entry written (8) per exit;
     k_jump        4 bytes per exit-table access (entry read; gather and write
                   of the entries still holding a rank);
-    k_escatter    bitmaps and prefixes (n / 2 per launch) + table entry read
-                  and exit label written (8) per exit;
     k_rcheck      four label words per vertex (16)."""
     u, w = st["units"], st["work_launches"]
     if name == "k_csweep":
@@ -124,7 +122,7 @@ def kernel_bytes(name, st, n, es):
         return u * (es + 9)
     if name == "k_ecount":
         return u * 16
-    if name in ("k_efill", "k_escatter"):
+    if name == "k_efill":
         return w * n / 2 + u * 8
     if name == "k_jump":
         return u * 4

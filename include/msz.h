@@ -118,10 +118,10 @@ int msz_plan_destroy(msz_plan p);
  * completes a stage of the field's state machine (the others find the field
  * in another stage and return at once). units counts the work of the working
  * launches: vertices (k_csweep, k_rcheck, k_label_tile: vertices of the tiles
- * recomputed), bitmap words (k_ecount), exits (k_efill, k_escatter), exit-table
+ * recomputed), bitmap words (k_ecount), exits (k_efill), exit-table
  * accesses (k_jump), fields (k_escan), cases (k_gather, k_mark),
  * touched vertices (k_apply), ring items (k_reclass). */
-#define MSZ_NUM_KERNELS 12
+#define MSZ_NUM_KERNELS 11
 typedef struct {
   const char* name;        /* kernel name, static string */
   uint64_t launches;       /* launches inside the loop's steps */
@@ -133,7 +133,7 @@ typedef struct {
 
 /* Fills out[0 .. min(n, MSZ_NUM_KERNELS) - 1] in step order (k_csweep,
  * k_gather, k_mark, k_label_tile, k_ecount, k_escan, k_efill, k_jump,
- * k_escatter, k_rcheck, k_apply, k_reclass);
+ * k_rcheck, k_apply, k_reclass);
  * returns the number filled, or MSZ_ERR_ARG (no plan / out, or a plan made
  * without MSZ_OPT_TIME_KERNELS). Host memory only. */
 int msz_plan_kernel_stats(msz_plan p, msz_kernel_stat* out, int n);
@@ -226,8 +226,8 @@ int msz_directions(const void* field_dev, int ndim, const int64_t dims[3], int d
  * label_max_dev / label_min_dev hold N labels. out->edit_idx etc. point to
  * them. Every other array of the loop lives in one static device array of
  * 64 MiB that each GPU loading the library holds until exit; a field needs
- * about 45 bytes per vertex (float32) or 49 (float64) of it, so up to about
- * 1.5 M (float32) / 1.4 M (float64) vertices. Larger fields are rejected
+ * about 37 bytes per vertex (float32) or 41 (float64) of it, so up to about
+ * 1.8 M (float32) / 1.6 M (float64) vertices. Larger fields are rejected
  * with MSZ_ERR_TOO_LARGE before any work. The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture. All calls share

@@ -38,9 +38,9 @@ enum : uint32_t {
   ACT_NONE = 0, ACT_MARK_C = 1, ACT_LABELS = 2, ACT_APPLY_R = 3, ACT_GATHER = 4, ACT_RECLASS = 5, ACT_REQUEST = 6
 };
 // Stages of one label evaluation (job 0: f, job 1: g): tile terminals, exit
-// counts, exit ranks, compact exit table, pointer jumping on it, labels back
-// to the exit vertices, then f's labels in place (job 0) or the R-loop check.
-enum : uint32_t { L_INIT = 0, L_COUNT = 1, L_SCAN = 2, L_FILL = 3, L_JUMP = 4, L_SCATTER = 5, L_DONE = 6 };
+// counts, exit ranks, compact exit table, pointer jumping on it, then f's
+// labels in place (job 0) or the R-loop check.
+enum : uint32_t { L_INIT = 0, L_COUNT = 1, L_SCAN = 2, L_FILL = 3, L_JUMP = 4, L_DONE = 5 };
 // Tile terminal flag: the terminal is an extremum (else a tile exit).
 constexpr uint32_t kExt = 0x80000000u;
 // Compact exit table entry flag: the entry holds the exit's label (an
@@ -57,8 +57,8 @@ constexpr int kCaseTiles = kThreads / 32;          // case-count tiles per gathe
 
 // Kernels of a loop step, in launch order of their kinds (per-kernel timing).
 enum {
-  KID_SWEEP = 0, KID_GATHER, KID_MARK, KID_LABEL, KID_ECOUNT, KID_ESCAN, KID_EFILL, KID_JUMP, KID_ESCATTER,
-  KID_RCHECK, KID_APPLY, KID_RECLASS, NKID
+  KID_SWEEP = 0, KID_GATHER, KID_MARK, KID_LABEL, KID_ECOUNT, KID_ESCAN, KID_EFILL, KID_JUMP, KID_RCHECK,
+  KID_APPLY, KID_RECLASS, NKID
 };
 
 constexpr int kStripes = 16;
@@ -103,7 +103,6 @@ struct Field {
   uint32_t* ep[2];  // per bitmap word: exits before it within its dense unit
   uint32_t* ub[2];  // per dense unit: exits before it (after the scan; counts before)
   uint32_t* lc[2];  // compact exit table, indexed by exit rank
-  int32_t* lx[2];   // label of every exit vertex (scattered back from lc)
   uint8_t* tdirty;  // label tiles whose terminals must be recomputed
   uint8_t* cls;     // false-type bits of g per vertex (FPmax, FPmin, FNmax, FNmin), padded to kEmitTile
   uint32_t* cases;  // the round's cases of the current type
@@ -335,7 +334,7 @@ __device__ void ctrl_after_jump(DevState* st) {
   st->jump_rounds++;
   st->ticks++;
   if (c == 0) {
-    st->lstate = L_SCATTER;
+    st->lstate = L_DONE;
   } else if (st->jump_rounds > 64) {
     st->phase = PH_ERR;
     st->status = MSZ_ERR_TIMEOUT;

@@ -141,7 +141,6 @@ struct FieldBufs {
   uint32_t* ep[2] = {nullptr, nullptr};
   uint32_t* ub[2] = {nullptr, nullptr};
   uint32_t* lc[2] = {nullptr, nullptr};
-  int32_t* lx[2] = {nullptr, nullptr};
   uint8_t* tdirty = nullptr;
   uint8_t* cls = nullptr;
   uint32_t* cases = nullptr;
@@ -180,7 +179,6 @@ void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs
     B.ep[d] = (uint32_t*)b.take(nw * 4);
     B.ub[d] = (uint32_t*)b.take(nu * 4);
     B.lc[d] = (uint32_t*)b.take(n * 4);
-    B.lx[d] = (int32_t*)b.take(n * 4);
   }
   B.tdirty = (uint8_t*)b.take((size_t)label_tiles(G));
   B.cls = (uint8_t*)b.take(nt * kEmitTile);
@@ -201,17 +199,17 @@ void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs
 // One (dtype, dimension) group of an engine's fields.
 // ---------------------------------------------------------------------------
 constexpr int kJumpsPerStep = 4;
-constexpr int kStepSlots = 11 + kJumpsPerStep;  // launches per step
+constexpr int kStepSlots = 10 + kJumpsPerStep;  // launches per step
 constexpr int kStepEvents = kStepSlots + 1;
 // kernel of each launch slot of a step
-constexpr int kSlotKernel[kStepSlots] = {KID_SWEEP,  KID_GATHER, KID_MARK,     KID_LABEL,  KID_ECOUNT,
-                                         KID_ESCAN,  KID_EFILL,  KID_JUMP,     KID_JUMP,   KID_JUMP,
-                                         KID_JUMP,   KID_ESCATTER, KID_RCHECK, KID_APPLY, KID_RECLASS};
+constexpr int kSlotKernel[kStepSlots] = {KID_SWEEP, KID_GATHER, KID_MARK, KID_LABEL,  KID_ECOUNT,
+                                         KID_ESCAN, KID_EFILL,  KID_JUMP, KID_JUMP,   KID_JUMP,
+                                         KID_JUMP,  KID_RCHECK, KID_APPLY, KID_RECLASS};
 static_assert(kJumpsPerStep == 4, "slot table assumes four jump launches per step");
 static_assert(NKID == MSZ_NUM_KERNELS, "kernel table and ABI disagree");
-const char* const kKernelNames[NKID] = {"k_csweep", "k_gather", "k_mark",     "k_label_tile",
-                                        "k_ecount", "k_escan",  "k_efill",    "k_jump",
-                                        "k_escatter", "k_rcheck", "k_apply",  "k_reclass"};
+const char* const kKernelNames[NKID] = {"k_csweep", "k_gather", "k_mark",   "k_label_tile",
+                                        "k_ecount", "k_escan",  "k_efill",  "k_jump",
+                                        "k_rcheck", "k_apply",  "k_reclass"};
 
 template <class T, int ND>
 struct Group {
@@ -306,7 +304,6 @@ struct Group {
         F.ep[d] = B.ep[d];
         F.ub[d] = B.ub[d];
         F.lc[d] = B.lc[d];
-        F.lx[d] = B.lx[d];
       }
       F.tdirty = B.tdirty;
       F.cls = B.cls;
@@ -425,7 +422,6 @@ struct Group {
     k_escan<T><<<nf, 1024, 0, s>>>(a());
     k_efill<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
     for (int j = 0; j < kJumpsPerStep; ++j) k_jump<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
-    k_escatter<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
     k_rcheck<T, ND><<<grid[K_DENSE], kThreads, 0, s>>>(a());
   }
   template <class A>

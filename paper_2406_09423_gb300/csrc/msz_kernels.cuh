@@ -745,18 +745,20 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
 // the compact exit table: entry rank(e) holds e's label when e's tile
 // terminal is an extremum (flag kRes), else the rank of that terminal (an
 // exit of e's tile). k_jump does pointer jumping on the table, one thread per
-// entry, until every entry holds a label; k_escatter writes the labels back
-// to the exit vertices (lx), where label resolution reads them.
+// entry, until every entry holds a label, which label resolution then reads
+// by the exit's rank.
 __device__ __forceinline__ uint32_t exit_rank(const uint32_t* ex, const uint32_t* ep, const uint32_t* ub, int e) {
   const int w = e >> 5;
   return ub[e / kDenseChunk] + ep[w] + (uint32_t)__popc(ex[w] & ((1u << (e & 31)) - 1u));
 }
 
-// Label of v from its tile terminal: the extremum itself, or the label of the
-// exit its line leaves the tile through.
-__device__ __forceinline__ int resolve_label(const int32_t* Tt, const int32_t* lx, int v) {
+// Label of v (direction d) from its tile terminal: the extremum itself, or
+// the label the exit table holds for the exit its line leaves the tile
+// through.
+template <class T>
+__device__ __forceinline__ int resolve_label(const Field<T>& F, int d, const int32_t* Tt, int v) {
   const uint32_t t = (uint32_t)Tt[v];
-  return (t & kExt) ? (int)(t & ~kExt) : lx[t];
+  return (t & kExt) ? (int)(t & ~kExt) : (int)(F.lc[d][exit_rank(F.ex[d], F.ep[d], F.ub[d], (int)t)] & ~kRes);
 }
 
 template <class T>
@@ -982,56 +984,9 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
   tl.flush(A, K_DENSE, pre_flush, done);
 }
 
-template <class T>
-__global__ void __launch_bounds__(kThreads) k_escatter(GroupArgs<T> A) {
-  const int* pre = A.prefix + K_DENSE * (A.nf + 1);
-  auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_SCATTER; };
-  auto none = [](DevState*) {};
-  auto done = [&](DevState* st) {
-    st->lstate = L_DONE;
-    st->ticks++;
-    log_work(A);
-  };
-  UnitTally tl;
-  MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
-    tl.enter(A, K_DENSE, i, none, done);
-    const Field<T>& F = A.fields[i];
-    DevState* st = F.st;
-    const int u = u_ - pre[i];
-    const int nw = (F.G.n + 31) >> 5;
-    const int w = u * kThreads + threadIdx.x;
-    uint32_t nex = 0;
-    if (w < nw) {
-#pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        uint32_t r = F.ub[d][u] + F.ep[d][w];
-        uint32_t m = F.ex[d][w];
-        nex += __popc(m);
-        while (m) {
-          int e[kBatch];
-          uint32_t lab[kBatch];
-#pragma unroll
-          for (int j = 0; j < kBatch; ++j) {
-            e[j] = m ? (w << 5) + __ffs(m) - 1 : -1;
-            if (m) m &= m - 1;
-          }
-#pragma unroll
-          for (int j = 0; j < kBatch; ++j) lab[j] = (e[j] >= 0) ? F.lc[d][r + j] : 0u;
-#pragma unroll
-          for (int j = 0; j < kBatch; ++j)
-            if (e[j] >= 0) F.lx[d][e[j]] = (int32_t)(lab[j] & ~kRes);
-          r += kBatch;
-        }
-      }
-    }
-    log_units_warp(A, st, KID_ESCATTER, nex);
-  }
-  tl.flush(A, K_DENSE, none, done);
-}
-
 // Job 0: f's labels in place of its tile terminals (safe while other threads
-// resolve: a terminal that is an extremum keeps its value, and an exit's
-// label is read from lx). Job 1, the R-loop check (Sec. 4.2): count wrong
+// resolve: a vertex's resolution reads only its own terminal and the exit
+// tables). Job 1, the R-loop check (Sec. 4.2): count wrong
 // labels; a wrongly labelled vertex whose steepest neighbour in g differs
 // from f's is a troublemaker. Wrong max label: decrease its ascending
 // neighbour in g (Eq. 6). Wrong min label: decrease the descending neighbour
@@ -1059,8 +1014,8 @@ __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
     const int v1 = min(F.G.n, v0 + kDenseChunk);
     if (st->ljob == 0) {
       for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-        F.Mf[v] = resolve_label(F.Mf, F.lx[0], v);
-        F.mf[v] = resolve_label(F.mf, F.lx[1], v);
+        F.Mf[v] = resolve_label(F, 0, F.Mf, v);
+        F.mf[v] = resolve_label(F, 1, F.mf, v);
       }
       continue;
     }
@@ -1080,8 +1035,10 @@ __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
       }
 #pragma unroll
       for (int k = 0; k < kRB; ++k) {
-        tu[k] = (tu[k] & kExt) ? (tu[k] & ~kExt) : (uint32_t)F.lx[0][tu[k]];
-        td[k] = (td[k] & kExt) ? (td[k] & ~kExt) : (uint32_t)F.lx[1][td[k]];
+        tu[k] = (tu[k] & kExt) ? (tu[k] & ~kExt)
+                               : (F.lc[0][exit_rank(F.ex[0], F.ep[0], F.ub[0], (int)tu[k])] & ~kRes);
+        td[k] = (td[k] & kExt) ? (td[k] & ~kExt)
+                               : (F.lc[1][exit_rank(F.ex[1], F.ep[1], F.ub[1], (int)td[k])] & ~kRes);
       }
       uint32_t wrong = 0;  // bit 2k: max label wrong, bit 2k+1: min label wrong
 #pragma unroll
@@ -1200,8 +1157,8 @@ __global__ void __launch_bounds__(kThreads) k_emit_count(GroupArgs<T> A) {
     for (int k = 0; k < kEmitItems; ++k) {
       const int v = base + k;
       if (v < F.G.n) {
-        F.Pup[v] = resolve_label(F.Pup, F.lx[0], v);
-        F.Pdn[v] = resolve_label(F.Pdn, F.lx[1], v);
+        F.Pup[v] = resolve_label(F, 0, F.Pup, v);
+        F.Pdn[v] = resolve_label(F, 1, F.Pdn, v);
       }
     }
     __syncthreads();
