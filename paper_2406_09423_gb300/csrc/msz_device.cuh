@@ -157,6 +157,26 @@ __device__ __forceinline__ uint8_t direction_of(const T* __restrict__ g, const G
   const T gv = g[v];
   T hv = gv, lv = gv;
   int hi = v, lo = v, hs = kSelf, ls = kSelf;
+  // interior vertices (all neighbours in the grid) skip the bounds tests
+  const bool interior = x > 0 && x < G.nx - 1 && y > 0 && y < G.ny - 1 && (ND == 2 || (z > 0 && z < G.nz - 1));
+  if (interior) {
+    T gu[2 * NPOS];
+#pragma unroll
+    for (int s = 0; s < 2 * NPOS; ++s) {
+      const int sg = (s < NPOS) ? 1 : -1;
+      const int m = (int)((Slots<ND>::MASKS >> (4 * (s < NPOS ? s : s - NPOS))) & 7u);
+      gu[s] = g[v + sg * ((m & 1) + ((m >> 1) & 1) * G.nx + ((m >> 2) & 1) * G.nxny)];
+    }
+#pragma unroll
+    for (int s = 0; s < 2 * NPOS; ++s) {
+      const int sg = (s < NPOS) ? 1 : -1;
+      const int m = (int)((Slots<ND>::MASKS >> (4 * (s < NPOS ? s : s - NPOS))) & 7u);
+      const int u = v + sg * ((m & 1) + ((m >> 1) & 1) * G.nx + ((m >> 2) & 1) * G.nxny);
+      if (gu[s] > hv || (gu[s] == hv && u > hi)) { hv = gu[s]; hi = u; hs = s; }
+      if (gu[s] < lv || (gu[s] == lv && u < lo)) { lv = gu[s]; lo = u; ls = s; }
+    }
+    return (uint8_t)(hs | (ls << 4));
+  }
 #pragma unroll
   for (int s = 0; s < 2 * NPOS; ++s) {
     const int sg = (s < NPOS) ? 1 : -1;

@@ -174,14 +174,14 @@ __device__ __forceinline__ void log_units_warp(const GroupArgs<T>& A, DevState* 
 // field's completion), so short lists still spread over many blocks and idle
 // blocks report nothing. [b, e) is unit k's slice (empty for the others).
 __device__ __forceinline__ uint32_t sparse_slice(uint64_t items, int S, int k, uint64_t& b, uint64_t& e) {
-  const uint64_t want = (items + kThreads - 1) / kThreads;
+  const uint64_t want = (items + kThreads - 1) / kThreads;  // a shift
   const uint64_t act = want < (uint64_t)S ? (want ? want : 1) : (uint64_t)S;
-  if ((uint64_t)k >= act) {
-    b = e = 0;
-  } else {
-    b = items * (uint64_t)k / act;
-    e = items * (uint64_t)(k + 1) / act;
-  }
+  // slices of ceil(items / act) entries (the last one shorter); 32-bit
+  // division when the list allows (always in practice)
+  const uint64_t chunk = (items < (1ull << 32)) ? (uint64_t)(((uint32_t)items + (uint32_t)act - 1u) / (uint32_t)act)
+                                                : (items + act - 1) / act;
+  b = (uint64_t)k < act ? min(items, chunk * (uint64_t)k) : 0;
+  e = (uint64_t)k < act ? min(items, b + chunk) : 0;
   return (uint32_t)act;
 }
 

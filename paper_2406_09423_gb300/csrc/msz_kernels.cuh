@@ -959,8 +959,8 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
       // this unit's equal share of the direction's table
-      const uint64_t ne = st->nexit[d];
-      const uint32_t r0 = (uint32_t)(ne * u / U), re = (uint32_t)(ne * (u + 1) / U);
+      const uint32_t ne = st->nexit[d], chunk = (ne + (uint32_t)U - 1u) / (uint32_t)U;
+      const uint32_t r0 = min(ne, chunk * (uint32_t)u), re = min(ne, r0 + chunk);
       uint32_t* lc = F.lc[d];
       for (uint32_t rb = r0 + threadIdx.x; rb < re; rb += kJB * kThreads) {
         uint32_t x[kJB], y[kJB];
