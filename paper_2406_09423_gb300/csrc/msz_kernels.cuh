@@ -18,10 +18,10 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 template <int ND>
 struct LabelGeom {
-  static constexpr int TX = (ND == 3) ? 32 : 64;
-  static constexpr int TY = (ND == 3) ? 8 : 32;
-  static constexpr int TZ = (ND == 3) ? 8 : 1;
-  static constexpr int TV = TX * TY * TZ;  // 2048 vertices
+  static constexpr int TX = (ND == 3) ? 16 : 64;
+  static constexpr int TY = (ND == 3) ? 16 : 32;
+  static constexpr int TZ = (ND == 3) ? 16 : 1;
+  static constexpr int TV = TX * TY * TZ;  // 4096 (3D) / 2048 (2D) vertices
   static constexpr int SX = TX + 2, SY = TY + 2, SZ = (ND == 3) ? TZ + 2 : 1;
   static constexpr int HALO = SX * SY * SZ;  // < 65536: pointers fit in 16 bits
   static constexpr int PER_THREAD = TV / kThreads;
