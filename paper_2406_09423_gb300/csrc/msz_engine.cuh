@@ -102,6 +102,7 @@ struct Field {
   uint32_t* ex[2];  // bitmap of tile-exit vertices
   uint32_t* ep[2];  // per bitmap word: exits before it within its dense unit
   uint32_t* ub[2];  // per dense unit: exits before it (after the scan; counts before)
+  uint2* xr[2];     // per bitmap word: (bitmap word, exits before it): one load gives a rank
   uint32_t* lc[2];  // compact exit table, indexed by exit rank
   uint8_t* tdirty;  // label tiles whose terminals must be recomputed
   uint8_t* cls;     // false-type bits of g per vertex (FPmax, FPmin, FNmax, FNmin), padded to kEmitTile

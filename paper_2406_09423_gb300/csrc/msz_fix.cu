@@ -140,6 +140,7 @@ struct FieldBufs {
   uint32_t* ex[2] = {nullptr, nullptr};
   uint32_t* ep[2] = {nullptr, nullptr};
   uint32_t* ub[2] = {nullptr, nullptr};
+  uint2* xr[2] = {nullptr, nullptr};
   uint32_t* lc[2] = {nullptr, nullptr};
   uint8_t* tdirty = nullptr;
   uint8_t* cls = nullptr;
@@ -178,6 +179,7 @@ void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs
     B.ex[d] = (uint32_t*)b.take(nw * 4);
     B.ep[d] = (uint32_t*)b.take(nw * 4);
     B.ub[d] = (uint32_t*)b.take(nu * 4);
+    B.xr[d] = (uint2*)b.take(nw * 8);
     B.lc[d] = (uint32_t*)b.take(n * 4);
   }
   B.tdirty = (uint8_t*)b.take((size_t)label_tiles(G));
@@ -303,6 +305,7 @@ struct Group {
         F.ex[d] = B.ex[d];
         F.ep[d] = B.ep[d];
         F.ub[d] = B.ub[d];
+        F.xr[d] = B.xr[d];
         F.lc[d] = B.lc[d];
       }
       F.tdirty = B.tdirty;

@@ -752,13 +752,19 @@ __device__ __forceinline__ uint32_t exit_rank(const uint32_t* ex, const uint32_t
   return ub[e / kDenseChunk] + ep[w] + (uint32_t)__popc(ex[w] & ((1u << (e & 31)) - 1u));
 }
 
+// The same from the (bitmap word, exits before it) pairs that k_efill writes.
+__device__ __forceinline__ uint32_t exit_rank2(const uint2* xr, int e) {
+  const uint2 p = xr[e >> 5];
+  return p.y + (uint32_t)__popc(p.x & ((1u << (e & 31)) - 1u));
+}
+
 // Label of v (direction d) from its tile terminal: the extremum itself, or
 // the label the exit table holds for the exit its line leaves the tile
 // through.
 template <class T>
 __device__ __forceinline__ int resolve_label(const Field<T>& F, int d, const int32_t* Tt, int v) {
   const uint32_t t = (uint32_t)Tt[v];
-  return (t & kExt) ? (int)(t & ~kExt) : (int)(F.lc[d][exit_rank(F.ex[d], F.ep[d], F.ub[d], (int)t)] & ~kRes);
+  return (t & kExt) ? (int)(t & ~kExt) : (int)(F.lc[d][exit_rank2(F.xr[d], (int)t)] & ~kRes);
 }
 
 template <class T>
@@ -903,6 +909,7 @@ __global__ void __launch_bounds__(kThreads) k_efill(GroupArgs<T> A) {
         const int32_t* Tt = d ? (job ? F.Pdn : F.mf) : (job ? F.Pup : F.Mf);
         uint32_t r = F.ub[d][u] + F.ep[d][w];
         uint32_t m = F.ex[d][w];
+        F.xr[d][w] = make_uint2(m, r);  // for label resolution after the jumping
         nex += __popc(m);
         while (m) {
           int e[kBatch];
@@ -1035,10 +1042,8 @@ __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
       }
 #pragma unroll
       for (int k = 0; k < kRB; ++k) {
-        tu[k] = (tu[k] & kExt) ? (tu[k] & ~kExt)
-                               : (F.lc[0][exit_rank(F.ex[0], F.ep[0], F.ub[0], (int)tu[k])] & ~kRes);
-        td[k] = (td[k] & kExt) ? (td[k] & ~kExt)
-                               : (F.lc[1][exit_rank(F.ex[1], F.ep[1], F.ub[1], (int)td[k])] & ~kRes);
+        tu[k] = (tu[k] & kExt) ? (tu[k] & ~kExt) : (F.lc[0][exit_rank2(F.xr[0], (int)tu[k])] & ~kRes);
+        td[k] = (td[k] & kExt) ? (td[k] & ~kExt) : (F.lc[1][exit_rank2(F.xr[1], (int)td[k])] & ~kRes);
       }
       uint32_t wrong = 0;  // bit 2k: max label wrong, bit 2k+1: min label wrong
 #pragma unroll
