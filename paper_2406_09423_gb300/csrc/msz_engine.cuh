@@ -174,8 +174,9 @@ __device__ __forceinline__ void log_units_warp(const GroupArgs<T>& A, DevState* 
 // thread about one entry take part (returned; they alone count towards the
 // field's completion), so short lists still spread over many blocks and idle
 // blocks report nothing. [b, e) is unit k's slice (empty for the others).
-__device__ __forceinline__ uint32_t sparse_slice(uint64_t items, int S, int k, uint64_t& b, uint64_t& e) {
-  const uint64_t want = (items + kThreads - 1) / kThreads;  // a shift
+__device__ __forceinline__ uint32_t sparse_slice(uint64_t items, int S, int k, uint64_t& b, uint64_t& e,
+                                                 uint32_t per_unit = kThreads) {
+  const uint64_t want = (items + per_unit - 1) / per_unit;
   const uint64_t act = want < (uint64_t)S ? (want ? want : 1) : (uint64_t)S;
   // slices of ceil(items / act) entries (the last one shorter); 32-bit
   // division when the list allows (always in practice)
@@ -452,6 +453,35 @@ __device__ void request(const Field<T>& F, int a, int t) {
       if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE);
     }
   }
+}
+
+// request() by a whole warp (lane = the thread's lane): lane 0 decides;
+// a freeze marks the closed 1-ring with one lane per vertex.
+template <class T, int ND>
+__device__ __forceinline__ void request_warp(const Field<T>& F, int a, int t, int lane) {
+  int dec = 0;
+  if (lane == 0) dec = !(F.flags[t] & FL_FROZEN) && F.g[t] > lower_bound_of(F.f[t], F.xi);
+  dec = __shfl_sync(kFull, dec, 0);
+  if (dec) {
+    if (lane == 0) mark(F, t, FL_DEC);
+    return;
+  }
+  constexpr int NPOS = Slots<ND>::NPOS;
+  if (lane > 2 * NPOS) return;
+  int u = a;
+  if (lane < 2 * NPOS) {
+    int x, y, z;
+    coords(F.G, a, x, y, z);
+    const int sg = (lane < NPOS) ? 1 : -1;
+    const int m = (int)((Slots<ND>::MASKS >> (4 * (lane < NPOS ? lane : lane - NPOS))) & 7u);
+    const int dx = sg * (m & 1), dy = sg * ((m >> 1) & 1), dz = sg * ((m >> 2) & 1);
+    const int X = x + dx, Y = y + dy, Z = z + dz;
+    bool in = X >= 0 && X < F.G.nx && Y >= 0 && Y < F.G.ny;
+    if (ND == 3) in = in && Z >= 0 && Z < F.G.nz;
+    if (!in) return;
+    u = a + dx + dy * F.G.nx + dz * F.G.nxny;
+  }
+  if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE);
 }
 
 }  // namespace msz

@@ -441,8 +441,8 @@ __global__ void __launch_bounds__(kThreads) k_gather(GroupArgs<T> A) {
   tl.flush(A, K_CASE, pre_flush, done);
 }
 
-// C-loop requests for the listed cases (Eqs. 2-5), one case per thread over
-// the whole grid: FPmax and FNmin edit the false vertex itself; FPmin and
+// C-loop requests for the listed cases (Eqs. 2-5), one case per warp over
+// the whole grid (a freeze marks its ring one vertex per lane): FPmax and FNmin edit the false vertex itself; FPmin and
 // FNmax edit its neighbour that is maximal in g, which is its steepest ascent
 // since it is not a maximum of g's ring.
 template <class T, int ND>
@@ -460,19 +460,21 @@ __global__ void __launch_bounds__(kThreads) k_mark(GroupArgs<T> A) {
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
     uint64_t b, e;
-    const uint32_t act = sparse_slice(st->ncase, F.units[K_SPARSE], u_ - pre[i], b, e);
+    // one case per warp: kThreads / 32 cases per unit
+    const uint32_t act = sparse_slice(st->ncase, F.units[K_SPARSE], u_ - pre[i], b, e, kThreads / 32);
     if ((uint32_t)(u_ - pre[i]) >= act) continue;  // left out: not counted
     tl.enter(A, K_SPARSE, i, none, done);
     tl.target = act;
     const uint32_t type = st->T;
     if (threadIdx.x == 0) log_units(A, st, KID_MARK, e - b);
-    for (uint64_t j = b + threadIdx.x; j < e; j += kThreads) {
+    const int lane = threadIdx.x & 31;
+    for (uint64_t j = b + (threadIdx.x >> 5); j < e; j += kThreads / 32) {
       const int v = (int)F.cases[j];
       int x, y, z;
       coords(F.G, v, x, y, z);
       const uint8_t d = direction_of<T, ND>(F.g, F.G, v, x, y, z);
       const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny);
-      request<T, ND>(F, v, t);
+      request_warp<T, ND>(F, v, t, lane);
     }
   }
   tl.flush(A, K_SPARSE, none, done);
