@@ -53,7 +53,8 @@ enum { K_DENSE = 0, K_SWEEP = 1, K_LABEL = 2, K_SPARSE = 3, K_EMIT = 4, K_CASE =
 constexpr int kDenseChunk = 8192;  // vertices per dense unit
 constexpr int kEmitItems = 16;
 constexpr int kEmitTile = kThreads * kEmitItems;  // vertices per emission unit and per case-count tile
-constexpr int kCaseTiles = kThreads / 32;          // case-count tiles per gather unit (one per warp)
+constexpr int kTilesPerWarp = 4;                   // case-count tiles a gather warp checks at once
+constexpr int kCaseTiles = kTilesPerWarp * kThreads / 32;  // case-count tiles per gather unit
 
 // Kernels of a loop step, in launch order of their kinds (per-kernel timing).
 enum {

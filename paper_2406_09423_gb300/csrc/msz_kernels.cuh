@@ -389,8 +389,9 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
 
 // The round's cases of the field's current type, listed from the per-vertex
 // false-type bits; only tiles that hold cases of the type are read. A unit
-// is kCaseTiles case-count tiles, one per warp; each 512-byte chunk of a
-// tile appends its cases with one atomic per warp.
+// is kCaseTiles case-count tiles, kTilesPerWarp per warp (their counts read
+// together); each 512-byte chunk of a tile appends its cases with one atomic
+// per warp.
 template <class T, int ND>
 __global__ void __launch_bounds__(kThreads) k_gather(GroupArgs<T> A) {
   const int* pre = A.prefix + K_CASE * (A.nf + 1);
@@ -411,40 +412,46 @@ __global__ void __launch_bounds__(kThreads) k_gather(GroupArgs<T> A) {
     tl.enter(A, K_CASE, i, pre_flush, done);
     const Field<T>& F = A.fields[i];
     const uint32_t type = F.st->T;
-    const int tile = (u_ - pre[i]) * kCaseTiles + warp;
-    if (tile * kEmitTile >= F.G.n || F.ccnt[tile * 4 + type] == 0) continue;
+    // the warp's kTilesPerWarp tiles: their counts in one go, then the tiles with cases
+    const int t0 = (u_ - pre[i]) * kCaseTiles + warp * kTilesPerWarp;
+    const int tl_lane = t0 + lane;
+    const bool has = lane < kTilesPerWarp && tl_lane * kEmitTile < F.G.n && F.ccnt[tl_lane * 4 + type] != 0;
+    for (uint32_t hm = __ballot_sync(kFull, has); hm; hm &= hm - 1) {
+      const int tile = t0 + __ffs(hm) - 1;
 #pragma unroll 1
-    for (int r = 0; r < kEmitTile / (32 * 16); ++r) {
-      const int base = tile * kEmitTile + (r * 32 + lane) * 16;
-      const uint4 q = *reinterpret_cast<const uint4*>(F.cls + base);
-      const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
-      uint32_t hits = 0;  // bit k: byte k holds a case of the type
+      for (int r = 0; r < kEmitTile / (32 * 16); ++r) {
+        const int base = tile * kEmitTile + (r * 32 + lane) * 16;
+        const uint4 q = *reinterpret_cast<const uint4*>(F.cls + base);
+        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+        uint32_t hits = 0;  // bit k: byte k holds a case of the type
 #pragma unroll
-      for (int k = 0; k < 16; ++k) hits |= ((w4[k >> 2] >> (8 * (k & 3) + type)) & 1u) << k;
-      if (F.G.n - base < 16) hits &= (F.G.n - base > 0) ? (1u << (F.G.n - base)) - 1u : 0u;  // padding
-      const uint32_t c = __popc(hits);
-      uint32_t incl = c;
+        for (int k = 0; k < 16; ++k) hits |= ((w4[k >> 2] >> (8 * (k & 3) + type)) & 1u) << k;
+        if (F.G.n - base < 16) hits &= (F.G.n - base > 0) ? (1u << (F.G.n - base)) - 1u : 0u;  // padding
+        const uint32_t c = __popc(hits);
+        uint32_t incl = c;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        if (!total) continue;
+        uint32_t at = 0;
+        if (lane == 31) at = atomicAdd(&F.st->ncase, total);
+        at = __shfl_sync(kFull, at, 31) + incl - c;
+        for (; hits; hits &= hits - 1) F.cases[at++] = (uint32_t)(base + __ffs(hits) - 1);
+        ncases += c;
       }
-      const uint32_t total = __shfl_sync(kFull, incl, 31);
-      if (!total) continue;
-      uint32_t at = 0;
-      if (lane == 31) at = atomicAdd(&F.st->ncase, total);
-      at = __shfl_sync(kFull, at, 31) + incl - c;
-      for (; hits; hits &= hits - 1) F.cases[at++] = (uint32_t)(base + __ffs(hits) - 1);
-      ncases += c;
     }
   }
   tl.flush(A, K_CASE, pre_flush, done);
 }
 
 // C-loop requests for the listed cases (Eqs. 2-5), one case per warp over
-// the whole grid (a freeze marks its ring one vertex per lane): FPmax and FNmin edit the false vertex itself; FPmin and
-// FNmax edit its neighbour that is maximal in g, which is its steepest ascent
-// since it is not a maximum of g's ring.
+// the whole grid (a freeze marks its ring one vertex per lane): FPmax and
+// FNmin edit the false vertex itself; FPmin and FNmax edit its neighbour
+// that is maximal in g, which is its steepest ascent since it is not a
+// maximum of g's ring.
 template <class T, int ND>
 __global__ void __launch_bounds__(kThreads) k_mark(GroupArgs<T> A) {
   const int* pre = A.prefix + K_SPARSE * (A.nf + 1);
