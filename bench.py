@@ -110,8 +110,9 @@ def kernel_bytes(name, st, n, es):
                   of the tiles recomputed;
     k_ecount      per bitmap word: two exit-bitmap words read, two prefix
                   words written (16);
-    k_efill       bitmaps and prefixes (n / 2 bytes per launch) + terminal
-                  read and table entry written (8) per exit;
+    k_efill       bitmaps and prefixes read, (bitmap word, prefix) pairs
+                  written (n bytes per launch) + terminal read and table entry
+                  written (8) per exit;
     k_jump        4 bytes per exit-table access (entry read; gather and write
                   of the entries still holding a rank);
     k_rcheck      four label words per vertex (16)."""
@@ -123,7 +124,7 @@ def kernel_bytes(name, st, n, es):
     if name == "k_ecount":
         return u * 16
     if name == "k_efill":
-        return w * n / 2 + u * 8
+        return w * n + u * 8
     if name == "k_jump":
         return u * 4
     if name == "k_rcheck":

@@ -407,15 +407,17 @@ __device__ void ctrl_after_apply(DevState* st, uint32_t act) {
 // from one snapshot of g, applied afterwards; a freeze overrides a decrease.
 // ---------------------------------------------------------------------------
 // Slot in a list whose length counter is *ctr: one atomic per group of
-// lanes that arrive together (the field is the same for all of them).
+// lanes that arrive together with the same counter (lanes that arrive
+// together with different counters form one group per counter).
 __device__ __forceinline__ uint32_t list_slot(uint32_t* ctr) {
   const uint32_t active = __activemask();
+  const uint32_t peers = __match_any_sync(active, (unsigned long long)(uintptr_t)ctr);
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(active) - 1;
+  const int leader = __ffs(peers) - 1;
   uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(ctr, (uint32_t)__popc(active));
+  if (lane == leader) base = atomicAdd(ctr, (uint32_t)__popc(peers));
   base = __shfl_sync(active, base, leader);
-  return base + (uint32_t)__popc(active & ((1u << lane) - 1u));
+  return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
 }
 
 template <class T>
