@@ -106,8 +106,10 @@ def kernel_bytes(name, st, n, es):
     3D field of n vertices) from its work units, or None for the sparse
     kernels whose traffic is dominated by scattered L2 accesses:
     k_csweep      g (es) + f's direction byte per vertex swept;
-    k_label_tile  g (es) + direction byte + two tile terminals (8) per vertex
-                  of the tiles recomputed;
+    k_label_tile  g's direction byte read + two tile terminals (8) written per
+                  vertex of the tiles recomputed (f's evaluation, once per fix,
+                  also reads f and g and writes both direction bytes: not
+                  counted);
     k_ecount      per bitmap word: two exit-bitmap words read, two prefix
                   words written (16);
     k_efill       bitmaps and prefixes read, (bitmap word, prefix) pairs
@@ -120,7 +122,7 @@ def kernel_bytes(name, st, n, es):
     if name == "k_csweep":
         return u * (es + 1)
     if name == "k_label_tile":
-        return u * (es + 9)
+        return u * 9
     if name == "k_ecount":
         return u * 16
     if name == "k_efill":

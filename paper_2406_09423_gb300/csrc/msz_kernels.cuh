@@ -477,9 +477,7 @@ __global__ void __launch_bounds__(kThreads) k_mark(GroupArgs<T> A) {
     const int lane = threadIdx.x & 31;
     for (uint64_t j = b + (threadIdx.x >> 5); j < e; j += kThreads / 32) {
       const int v = (int)F.cases[j];
-      int x, y, z;
-      coords(F.G, v, x, y, z);
-      const uint8_t d = direction_of<T, ND>(F.g, F.G, v, x, y, z);
+      const uint8_t d = F.gdir[v];  // exact: reclassified after every apply
       const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny);
       request_warp<T, ND>(F, v, t, lane);
     }
@@ -492,8 +490,8 @@ __global__ void __launch_bounds__(kThreads) k_mark(GroupArgs<T> A) {
 // vertices the apply touched can change: the result equals a full sweep of
 // the new g. Items are (touched vertex, ring slot) pairs; the first item to
 // reach a vertex in this round claims it (epoch stamp = round number) and
-// recomputes its bits with the direction test of the requests; the field and
-// tile type counts move by the difference. Units are slices of the items.
+// recomputes its bits and its direction byte in g; the field and tile type
+// counts move by the difference. Units are slices of the items.
 template <class T, int ND>
 __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
   const int* pre = A.prefix + K_SPARSE * (A.nf + 1);
@@ -538,7 +536,9 @@ __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
         v = u + dx + dy * G.nx + dz * G.nxny;
       }
       if (atomicExch(&F.epoch[v], stamp) == stamp) continue;
-      const unsigned nb = case_bits(direction_of<T, ND>(F.g, G, v, x, y, z), F.fdir[v]);
+      const uint8_t dv = direction_of<T, ND>(F.g, G, v, x, y, z);
+      F.gdir[v] = dv;  // g's direction bytes stay exact for the requests and the labels
+      const unsigned nb = case_bits(dv, F.fdir[v]);
       const unsigned ob = F.cls[v];
       if (nb != ob) {
         F.cls[v] = (uint8_t)nb;
@@ -572,6 +572,73 @@ size_t label_smem_bytes() {
   return ((LG::HALO * sizeof(T) + 15) / 16) * 16 + (size_t)LG::HALO * sizeof(uint32_t);
 }
 
+// A tile's values with a one-cell halo: every in-grid cell by an
+// asynchronous global -> shared copy (all of the block's copies in flight at
+// once), the others NaN. init_pp: halo pointers start as self pointers.
+template <class T, int ND>
+__device__ __forceinline__ void load_halo(T* val, uint32_t* PP, const T* src, const Geom& G, int x0, int y0, int z0,
+                                          bool init_pp) {
+  using LG = LabelGeom<ND>;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int row = warp; row < LG::ROWS; row += kThreads / 32) {
+    const int hy = row % LG::SY, hz = row / LG::SY;
+    const int gy = y0 - 1 + hy, gz = (ND == 3) ? z0 - 1 + hz : 0;
+    const bool rin = gy >= 0 && gy < G.ny && gz >= 0 && gz < G.nz;
+    const size_t rbase = rin ? (size_t)G.nx * ((size_t)gy + (size_t)G.ny * gz) : 0;
+    for (int hx = lane; hx < LG::SX; hx += 32) {
+      const int gx = x0 - 1 + hx;
+      const int h = hx + LG::SX * row;
+      if (rin && gx >= 0 && gx < G.nx) cp_async_elem(&val[h], src + rbase + gx);
+      else val[h] = qnan<T>();
+      if (init_pp) PP[h] = (uint32_t)h | ((uint32_t)h << 16);
+    }
+  }
+}
+
+// Direction byte (ascending slot | descending slot << 4) of tile cell c from
+// the halo values: candidates in ascending index order, so ties go to the
+// larger index for the maximum and to the smaller for the minimum (Sec. 3
+// SoS); NaN cells never win.
+template <class T, int ND>
+__device__ __forceinline__ uint32_t halo_dir(const T* val, int c) {
+  using LG = LabelGeom<ND>;
+  constexpr int HS = LG::SX, HSS = LG::SX * LG::SY;
+  constexpr int NC = (ND == 3) ? 15 : 7;
+  T hv = -INFINITY, lv = INFINITY;
+  int hs = kSelf, ls = kSelf;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    int o, slot;
+    if (ND == 3) {
+      constexpr int tab[15][2] = {{-1 - HS - HSS, 13}, {-HS - HSS, 12}, {-1 - HSS, 11}, {-HSS, 9},
+                                  {-1 - HS, 10},       {-HS, 8},        {-1, 7},        {0, kSelf},
+                                  {1, 0},              {HS, 1},         {1 + HS, 3},    {HSS, 2},
+                                  {1 + HSS, 4},        {HS + HSS, 5},   {1 + HS + HSS, 6}};
+      o = tab[j][0];
+      slot = tab[j][1];
+    } else {
+      constexpr int tab[7][2] = {{-1 - HS, 5}, {-HS, 4}, {-1, 3}, {0, kSelf}, {1, 0}, {HS, 1}, {1 + HS, 2}};
+      o = tab[j][0];
+      slot = tab[j][1];
+    }
+    const T u = val[c + o];
+    if (u >= hv) { hv = u; hs = slot; }
+    if (u < lv) { lv = u; ls = slot; }
+  }
+  return (uint32_t)hs | ((uint32_t)ls << 4);
+}
+
+// Whether the neighbour in slot s of a tile cell lies outside the tile. bhi /
+// blo: the cell's axes (bit 0 x, 1 y, 2 z) on the tile's upper / lower face.
+template <int ND>
+__device__ __forceinline__ bool leaves_tile(int s, uint32_t bhi, uint32_t blo) {
+  if (s == kSelf) return false;
+  constexpr int npos = Slots<ND>::NPOS;
+  const bool neg = s >= npos;
+  const uint32_t m = (uint32_t)slot_mask(ND, neg ? s - npos : s);
+  return (m & (neg ? blo : bhi)) != 0u;
+}
+
 template <class T, int ND>
 __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
   using LG = LabelGeom<ND>;
@@ -582,9 +649,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
   // ascending pointer (low 16 bits) and descending pointer (high 16 bits)
   uint32_t* PP = reinterpret_cast<uint32_t*>(lsm + ((LG::HALO * sizeof(T) + 15) / 16) * 16);
   const int* pre = A.prefix + K_LABEL * (A.nf + 1);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int HS = LG::SX, HSS = LG::SX * LG::SY;
-  constexpr int NC = (ND == 3) ? 15 : 7;
   // halo-cell exit bits (ascending, descending); padded for the two-word reads
   constexpr int kExWords = (LG::HALO + 31) / 32 + 2;
   constexpr int kSegs = (LG::SX + 31) / 32;
@@ -602,8 +667,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
     const Field<T>& F = A.fields[fi];
     DevState* st = F.st;
     const bool job = st->ljob != 0;
-    const T* src = job ? F.g : F.f;
-    uint8_t* dir = job ? F.gdir : F.fdir;
     int32_t* OA = job ? F.Pup : F.Mf;
     int32_t* OB = job ? F.Pdn : F.mf;
     const Geom G = F.G;
@@ -619,55 +682,49 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
     const int z0 = (tile / (tiles_x * tiles_y)) * LG::TZ;
     __syncthreads();
     for (int k = threadIdx.x; k < 2 * kExWords; k += kThreads) exs[k / kExWords][k % kExWords] = 0u;
-    // halo values: every in-grid cell by an asynchronous global -> shared
-    // copy (all of the block's copies in flight at once), the others NaN
-    for (int row = warp; row < LG::ROWS; row += kThreads / 32) {
-      const int hy = row % LG::SY, hz = row / LG::SY;
-      const int gy = y0 - 1 + hy, gz = (ND == 3) ? z0 - 1 + hz : 0;
-      const bool rin = gy >= 0 && gy < G.ny && gz >= 0 && gz < G.nz;
-      const size_t rbase = rin ? (size_t)G.nx * ((size_t)gy + (size_t)G.ny * gz) : 0;
-      for (int hx = lane; hx < LG::SX; hx += 32) {
-        const int gx = x0 - 1 + hx;
-        const int h = hx + HS * row;
-        if (rin && gx >= 0 && gx < G.nx) cp_async_elem(&val[h], src + rbase + gx);
-        else val[h] = qnan<T>();
-        PP[h] = (uint32_t)h | ((uint32_t)h << 16);
-      }
-    }
+    // Halo cells are terminals. Job 0 reads f's values with the halo; job 1
+    // needs no values: g's direction bytes are kept exact by the
+    // classification that follows every apply.
+    if (!job) load_halo<T, ND>(val, PP, F.f, G, x0, y0, z0, true);
+    else
+      for (int h = threadIdx.x; h < LG::HALO; h += kThreads) PP[h] = (uint32_t)h | ((uint32_t)h << 16);
     cp_async_wait_all();
     __syncthreads();
-    uint8_t dbyte[LG::PER_THREAD];
+    // Pointers of the tile cells. A pointer that leaves the tile marks its
+    // halo cell as a tile exit: the first halo cell on an integral line is
+    // the steepest neighbour of the line's last tile cell, so the marked
+    // cells are exactly the terminals in the halo.
 #pragma unroll
     for (int k = 0; k < LG::PER_THREAD; ++k) {
       const int i = threadIdx.x + k * kThreads;
       const int lx = i % LG::TX, ly = (i / LG::TX) % LG::TY, lz = i / (LG::TX * LG::TY);
+      const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+      if (x >= G.nx || y >= G.ny || z >= G.nz) continue;  // outside the grid: keeps its self pointer
       const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
-      // best candidate so far as (offset * 16 + slot): one select per winner
-      T hv = -INFINITY, lv = INFINITY;
-      int hp = kSelf, lp = kSelf;
-#pragma unroll
-      for (int j = 0; j < NC; ++j) {
-        int o, slot;
-        if (ND == 3) {
-          constexpr int tab[15][2] = {{-1 - HS - HSS, 13}, {-HS - HSS, 12}, {-1 - HSS, 11}, {-HSS, 9},
-                                      {-1 - HS, 10},       {-HS, 8},        {-1, 7},        {0, kSelf},
-                                      {1, 0},              {HS, 1},         {1 + HS, 3},    {HSS, 2},
-                                      {1 + HSS, 4},        {HS + HSS, 5},   {1 + HS + HSS, 6}};
-          o = tab[j][0];
-          slot = tab[j][1];
-        } else {
-          constexpr int tab[7][2] = {{-1 - HS, 5}, {-HS, 4}, {-1, 3}, {0, kSelf}, {1, 0}, {HS, 1}, {1 + HS, 2}};
-          o = tab[j][0];
-          slot = tab[j][1];
-        }
-        const int pk = o * 16 + slot;
-        const T uval = val[c + o];
-        if (uval >= hv) { hv = uval; hp = pk; }
-        if (uval < lv) { lv = uval; lp = pk; }
+      const int v = x + G.nx * (y + G.ny * z);
+      uint32_t db;
+      if (!job) {
+        db = halo_dir<T, ND>(val, c);
+        F.fdir[v] = (uint8_t)db;
+      } else {
+        db = F.gdir[v];
       }
-      dbyte[k] = (uint8_t)((hp & 15) | ((lp & 15) << 4));
-      if (val[c] == val[c])  // cells outside the grid are NaN and keep self pointers
-        PP[c] = (uint32_t)(c + (hp >> 4)) | ((uint32_t)(c + (lp >> 4)) << 16);
+      const int sa = (int)(db & 15u), sd = (int)(db >> 4);
+      const int ca = c + slot_offset(sa, ND, HS, HSS), cd = c + slot_offset(sd, ND, HS, HSS);
+      PP[c] = (uint32_t)ca | ((uint32_t)cd << 16);
+      const uint32_t bhi = (uint32_t)(lx == LG::TX - 1) | ((uint32_t)(ly == LG::TY - 1) << 1) |
+                           ((uint32_t)(ND == 3 && lz == LG::TZ - 1) << 2);
+      const uint32_t blo = (uint32_t)(lx == 0) | ((uint32_t)(ly == 0) << 1) | ((uint32_t)(ND == 3 && lz == 0) << 2);
+      if (bhi | blo) {
+        if (leaves_tile<ND>(sa, bhi, blo)) atomicOr(&exs[0][ca >> 5], 1u << (ca & 31));
+        if (leaves_tile<ND>(sd, bhi, blo)) atomicOr(&exs[1][cd >> 5], 1u << (cd & 31));
+      }
+    }
+    if (!job) {
+      // g's values (f-hat at this point) for g's first direction bytes,
+      // copied in while the pointers double
+      __syncthreads();
+      load_halo<T, ND>(val, PP, F.g, G, x0, y0, z0, false);
     }
     __syncthreads();
     // pointer doubling; a cell whose two pointers reach terminals is done
@@ -701,20 +758,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
         const int v = x + G.nx * (y + G.ny * z);
         const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
         // terminal cell -> global index; a terminal in the halo is a tile
-        // exit, noted in the block's halo bitmap (flushed below); one inside
-        // the tile is an extremum (flag kExt)
-        auto global_of = [&](int h, uint32_t* exb) -> int {
+        // exit (its bit is set in the block's halo bitmap, flushed below);
+        // one inside the tile is an extremum (flag kExt)
+        auto global_of = [&](int h) -> int {
           const int hx = h % LG::SX, hy = (h / LG::SX) % LG::SY, hz = h / HSS;
           const int e = (x0 - 1 + hx) + G.nx * ((y0 - 1 + hy) + G.ny * ((ND == 3) ? (z0 - 1 + hz) : 0));
           const bool halo = hx == 0 || hx == LG::SX - 1 || hy == 0 || hy == LG::SY - 1 ||
                             (ND == 3 && (hz == 0 || hz == LG::SZ - 1));
-          if (halo) atomicOr(&exb[h >> 5], 1u << (h & 31));
           return (int)((uint32_t)e | (halo ? 0u : kExt));
         };
-        dir[v] = dbyte[k];
         const uint32_t p = PP[c];
-        OA[v] = global_of((int)(p & 0xffffu), exs[0]);
-        OB[v] = global_of((int)(p >> 16), exs[1]);
+        OA[v] = global_of((int)(p & 0xffffu));
+        OB[v] = global_of((int)(p >> 16));
       }
     }
     __syncthreads();
@@ -739,6 +794,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
       uint32_t* ex = F.ex[d];
       if ((uint32_t)M) atomicOr(&ex[w], (uint32_t)M);
       if ((uint32_t)(M >> 32)) atomicOr(&ex[w + 1], (uint32_t)(M >> 32));
+    }
+    if (!job) {
+      // g's first direction bytes; from here on the classification after
+      // every apply keeps them exact
+      cp_async_wait_all();
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < LG::PER_THREAD; ++k) {
+        const int i = threadIdx.x + k * kThreads;
+        const int lx = i % LG::TX, ly = (i / LG::TX) % LG::TY, lz = i / (LG::TX * LG::TY);
+        const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+        if (x >= G.nx || y >= G.ny || z >= G.nz) continue;
+        const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
+        F.gdir[x + G.nx * (y + G.ny * z)] = (uint8_t)halo_dir<T, ND>(val, c);
+      }
     }
     if (job && threadIdx.x == 0) F.tdirty[tile] = 0;  // f's pass leaves every tile dirty for g's first
     if (threadIdx.x == 0)
@@ -1167,13 +1237,12 @@ __global__ void __launch_bounds__(kThreads) k_emit_count(GroupArgs<T> A) {
     const Field<T>& F = A.fields[i];
     const int tile = u_ - pre[i];
     const int base = tile * kEmitTile + threadIdx.x * kEmitItems;
-    // final labels of g (in place: exits and extrema keep their label)
-    for (int k = 0; k < kEmitItems; ++k) {
-      const int v = base + k;
-      if (v < F.G.n) {
-        F.Pup[v] = resolve_label(F, 0, F.Pup, v);
-        F.Pdn[v] = resolve_label(F, 1, F.Pdn, v);
-      }
+    // final labels of g: the loop ends only after an R-check found every
+    // vertex's g labels equal to f's, whose labels are resolved in Mf / mf
+    const int v1 = min(F.G.n, (tile + 1) * kEmitTile);
+    for (int v = tile * kEmitTile + threadIdx.x; v < v1; v += kThreads) {
+      F.Pup[v] = F.Mf[v];
+      F.Pdn[v] = F.mf[v];
     }
     __syncthreads();
     if (threadIdx.x == 0) s = 0;
