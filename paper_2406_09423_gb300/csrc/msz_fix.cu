@@ -200,7 +200,7 @@ void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs
 // ---------------------------------------------------------------------------
 // One (dtype, dimension) group of an engine's fields.
 // ---------------------------------------------------------------------------
-constexpr int kJumpsPerStep = 4;
+constexpr int kJumpsPerStep = 2;
 // A step holds two C-loop rounds (gather, mark, apply, reclassify): most
 // steps of a fix are C-loop rounds, and every launch of a stage that no field
 // is in still costs a few microseconds.
@@ -208,10 +208,10 @@ constexpr int kStepSlots = 14 + kJumpsPerStep;  // launches per step
 constexpr int kStepEvents = kStepSlots + 1;
 static_assert(kStepSlots <= 32, "the step log holds one bit per launch slot");
 // kernel of each launch slot of a step
-constexpr int kSlotKernel[kStepSlots] = {KID_SWEEP,  KID_GATHER, KID_MARK,  KID_APPLY, KID_RECLASS, KID_GATHER,
-                                         KID_MARK,   KID_LABEL,  KID_ECOUNT, KID_ESCAN, KID_EFILL,  KID_JUMP,
-                                         KID_JUMP,   KID_JUMP,   KID_JUMP,  KID_RCHECK, KID_APPLY,  KID_RECLASS};
-static_assert(kJumpsPerStep == 4, "slot table assumes four jump launches per step");
+constexpr int kSlotKernel[kStepSlots] = {KID_SWEEP, KID_GATHER, KID_MARK,   KID_APPLY,  KID_RECLASS, KID_GATHER,
+                                         KID_MARK,  KID_LABEL,  KID_ECOUNT, KID_ESCAN,  KID_EFILL,   KID_JUMP,
+                                         KID_JUMP,  KID_RCHECK, KID_APPLY,  KID_RECLASS};
+static_assert(kJumpsPerStep == 2, "slot table assumes two jump launches per step");
 static_assert(NKID == MSZ_NUM_KERNELS, "kernel table and ABI disagree");
 const char* const kKernelNames[NKID] = {"k_csweep", "k_gather", "k_mark",   "k_label_tile",
                                         "k_ecount", "k_escan",  "k_efill",  "k_jump",

@@ -1018,9 +1018,15 @@ __global__ void __launch_bounds__(kThreads) k_efill(GroupArgs<T> A) {
   tl.flush(A, K_DENSE, none, done);
 }
 
-// One round of pointer jumping on the compact exit tables: an entry that
-// holds a rank takes the entry it points to. Each dense unit takes an equal
-// share of both tables. A round that finds no rank left ends the jumping.
+// One round of label propagation on the compact exit tables. Each entry
+// that holds a rank follows its line through the exits of the tiles it
+// crosses until it reaches a label (or kChase steps), storing every pointer
+// it reaches in its own entry. All entries do so at once: a value read is the
+// entry of an exit further along the same line, or the line's label, whether
+// it was read before or after its owner advanced it, so every step makes
+// progress and the other entries' stores shorten the walk. Loads bypass L1 to
+// see those stores. A round that leaves no rank ends the labelling.
+constexpr int kChase = 32;
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
@@ -1041,7 +1047,7 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
     DevState* st = F.st;
     const uint64_t u = (uint64_t)(u_ - pre[i]), U = (uint64_t)F.units[K_DENSE];
     uint32_t acc = 0;
-    constexpr int kJB = 4;  // entries per thread and iteration, loads issued together
+    constexpr int kJB = 4;  // entries per thread and iteration, their walks advanced together
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
       // this unit's equal share of the direction's table
@@ -1049,20 +1055,30 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
       const uint32_t r0 = min(ne, chunk * (uint32_t)u), re = min(ne, r0 + chunk);
       uint32_t* lc = F.lc[d];
       for (uint32_t rb = r0 + threadIdx.x; rb < re; rb += kJB * kThreads) {
-        uint32_t x[kJB], y[kJB];
-#pragma unroll
-        for (int k = 0; k < kJB; ++k) x[k] = (rb + k * kThreads < re) ? lc[rb + k * kThreads] : kRes;
-#pragma unroll
-        for (int k = 0; k < kJB; ++k) y[k] = (x[k] & kRes) ? 0u : lc[x[k]];
+        uint32_t x[kJB];
 #pragma unroll
         for (int k = 0; k < kJB; ++k) {
-          if (rb + k * kThreads >= re) continue;
-          ++acc;
-          if (x[k] & kRes) continue;
-          lc[rb + k * kThreads] = y[k];
-          ++open[0];
-          acc += 2;
+          const bool in = rb + k * kThreads < re;
+          x[k] = in ? lc[rb + k * kThreads] : kRes;
+          acc += in ? 1u : 0u;
         }
+        for (int h = 0; h < kChase; ++h) {
+          uint32_t walk = 0;  // bit k: entry k still holds a rank
+#pragma unroll
+          for (int k = 0; k < kJB; ++k) walk |= (x[k] & kRes) ? 0u : (1u << k);
+          if (!walk) break;
+#pragma unroll
+          for (int k = 0; k < kJB; ++k)
+            if ((walk >> k) & 1u) x[k] = __ldcg(lc + x[k]);
+#pragma unroll
+          for (int k = 0; k < kJB; ++k)
+            if ((walk >> k) & 1u) {
+              lc[rb + k * kThreads] = x[k];
+              acc += 2;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kJB; ++k) open[0] += (x[k] & kRes) ? 0u : 1u;
       }
     }
     log_units_warp(A, st, KID_JUMP, acc);
