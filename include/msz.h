@@ -120,8 +120,10 @@ int msz_plan_destroy(msz_plan p);
  * launches: vertices (k_csweep, k_rcheck, k_label_tile: vertices of the tiles
  * recomputed), bitmap words (k_ecount), exits (k_efill), exit-table
  * accesses (k_jump), fields (k_escan), cases (k_gather, k_mark),
- * touched vertices (k_apply), ring items (k_reclass). */
-#define MSZ_NUM_KERNELS 11
+ * touched vertices (k_apply), ring items (k_reclass), C-loop rounds run
+ * whole in one block per field (k_csmall: requests, apply and
+ * reclassification of rounds with few cases). */
+#define MSZ_NUM_KERNELS 12
 typedef struct {
   const char* name;        /* kernel name, static string */
   uint64_t launches;       /* launches inside the loop's steps */
@@ -131,9 +133,9 @@ typedef struct {
   uint64_t units;          /* work units of the working launches (see above) */
 } msz_kernel_stat;
 
-/* Fills out[0 .. min(n, MSZ_NUM_KERNELS) - 1] in step order (k_csweep,
+/* Fills out[0 .. min(n, MSZ_NUM_KERNELS) - 1] in the order k_csweep,
  * k_gather, k_mark, k_label_tile, k_ecount, k_escan, k_efill, k_jump,
- * k_rcheck, k_apply, k_reclass);
+ * k_rcheck, k_apply, k_reclass, k_csmall;
  * returns the number filled, or MSZ_ERR_ARG (no plan / out, or a plan made
  * without MSZ_OPT_TIME_KERNELS). Host memory only. */
 int msz_plan_kernel_stats(msz_plan p, msz_kernel_stat* out, int n);

@@ -59,7 +59,7 @@ constexpr int kCaseTiles = kTilesPerWarp * kThreads / 32;  // case-count tiles p
 // Kernels of a loop step, in launch order of their kinds (per-kernel timing).
 enum {
   KID_SWEEP = 0, KID_GATHER, KID_MARK, KID_LABEL, KID_ECOUNT, KID_ESCAN, KID_EFILL, KID_JUMP, KID_RCHECK,
-  KID_APPLY, KID_RECLASS, NKID
+  KID_APPLY, KID_RECLASS, KID_CSMALL, NKID
 };
 
 constexpr int kStripes = 16;
@@ -420,12 +420,15 @@ __device__ __forceinline__ uint32_t list_slot(uint32_t* ctr) {
   return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
 }
 
+// Flags vertex u; its first flag of the round adds it to the touched list,
+// whose length is st->ntouch, or *ln (a block's own count) when given.
 template <class T>
-__device__ __forceinline__ void mark(const Field<T>& F, int u, uint8_t bit) {
+__device__ __forceinline__ void mark(const Field<T>& F, int u, uint8_t bit, uint32_t* ln = nullptr) {
   uint32_t* w = reinterpret_cast<uint32_t*>(F.flags) + (u >> 2);
   const int sh = (u & 3) * 8;
   const uint32_t old = atomicOr(w, (uint32_t)bit << sh);
-  if (((old >> sh) & (FL_DEC | FL_FREEZE)) == 0) F.touched[list_slot(&F.st->ntouch)] = (uint32_t)u;
+  if (((old >> sh) & (FL_DEC | FL_FREEZE)) == 0)
+    F.touched[ln ? atomicAdd(ln, 1u) : list_slot(&F.st->ntouch)] = (uint32_t)u;
 }
 
 // A false case anchored at a asks for a decreasing edit of t. If t is frozen
@@ -433,15 +436,15 @@ __device__ __forceinline__ void mark(const Field<T>& F, int u, uint8_t bit) {
 // frozen instead (termination guard; the paper argues convergence in the
 // reals, Sec. 4.3).
 template <class T, int ND>
-__device__ void request(const Field<T>& F, int a, int t) {
+__device__ void request(const Field<T>& F, int a, int t, uint32_t* ln = nullptr) {
   const uint8_t ft = F.flags[t];
   if (!(ft & FL_FROZEN) && F.g[t] > lower_bound_of(F.f[t], F.xi)) {
-    mark(F, t, FL_DEC);
+    mark(F, t, FL_DEC, ln);
     return;
   }
   int x, y, z;
   coords(F.G, a, x, y, z);
-  if (!(F.flags[a] & FL_FROZEN)) mark(F, a, FL_FREEZE);
+  if (!(F.flags[a] & FL_FROZEN)) mark(F, a, FL_FREEZE, ln);
   constexpr int NPOS = Slots<ND>::NPOS;
 #pragma unroll
   for (int s = 0; s < 2 * NPOS; ++s) {
@@ -453,7 +456,7 @@ __device__ void request(const Field<T>& F, int a, int t) {
     if (ND == 3) in = in && Z >= 0 && Z < F.G.nz;
     if (in) {
       const int u = a + dx + dy * F.G.nx + dz * F.G.nxny;
-      if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE);
+      if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE, ln);
     }
   }
 }

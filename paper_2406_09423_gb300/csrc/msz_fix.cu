@@ -204,18 +204,18 @@ constexpr int kJumpsPerStep = 2;
 // A step holds two C-loop rounds (gather, mark, apply, reclassify): most
 // steps of a fix are C-loop rounds, and every launch of a stage that no field
 // is in still costs a few microseconds.
-constexpr int kStepSlots = 14 + kJumpsPerStep;  // launches per step
+constexpr int kStepSlots = 15 + kJumpsPerStep;  // launches per step
 constexpr int kStepEvents = kStepSlots + 1;
 static_assert(kStepSlots <= 32, "the step log holds one bit per launch slot");
 // kernel of each launch slot of a step
-constexpr int kSlotKernel[kStepSlots] = {KID_SWEEP, KID_GATHER, KID_MARK,   KID_APPLY,  KID_RECLASS, KID_GATHER,
-                                         KID_MARK,  KID_LABEL,  KID_ECOUNT, KID_ESCAN,  KID_EFILL,   KID_JUMP,
-                                         KID_JUMP,  KID_RCHECK, KID_APPLY,  KID_RECLASS};
+constexpr int kSlotKernel[kStepSlots] = {KID_SWEEP,  KID_GATHER, KID_CSMALL, KID_MARK,   KID_APPLY,  KID_RECLASS,
+                                         KID_GATHER, KID_MARK,   KID_LABEL,  KID_ECOUNT, KID_ESCAN,  KID_EFILL,
+                                         KID_JUMP,   KID_JUMP,   KID_RCHECK, KID_APPLY,  KID_RECLASS};
 static_assert(kJumpsPerStep == 2, "slot table assumes two jump launches per step");
 static_assert(NKID == MSZ_NUM_KERNELS, "kernel table and ABI disagree");
 const char* const kKernelNames[NKID] = {"k_csweep", "k_gather", "k_mark",   "k_label_tile",
                                         "k_ecount", "k_escan",  "k_efill",  "k_jump",
-                                        "k_rcheck", "k_apply",  "k_reclass"};
+                                        "k_rcheck", "k_apply",  "k_reclass", "k_csmall"};
 
 template <class T, int ND>
 struct Group {
@@ -379,8 +379,8 @@ struct Group {
     return MSZ_OK;
   }
 
-  // csweep, (gather, mark, apply, reclass), gather, mark, label_tile, ecount,
-  // escan, efill, jump x kJumpsPerStep, rcheck, apply, reclass
+  // csweep, (gather, csmall, mark, apply, reclass), gather, mark, label_tile,
+  // ecount, escan, efill, jump x kJumpsPerStep, rcheck, apply, reclass
   int launches_per_step() const { return empty() ? 0 : kStepSlots; }
 
   void init(cudaStream_t s) {
@@ -407,9 +407,9 @@ struct Group {
       return x;
     };
     sweep(s, a());
-    gather(s, a);
+    gather(s, a, true);
     tail(s, a);
-    gather(s, a);
+    gather(s, a, false);
     labels(s, a);
     tail(s, a);
     if (e) cudaEventRecord(e[slot], s);
@@ -420,9 +420,11 @@ struct Group {
     if (tma) k_csweep<T, ND, true><<<grid[K_SWEEP], SG::NTP, 0, s>>>(x);
     else k_csweep<T, ND, false><<<grid[K_SWEEP], SG::NT, 0, s>>>(x);
   }
+  // small: the listed round may run in k_csmall (with the rounds after it)
   template <class A>
-  void gather(cudaStream_t s, A&& a) {
+  void gather(cudaStream_t s, A&& a, bool small) {
     k_gather<T, ND><<<grid[K_CASE], kThreads, 0, s>>>(a());
+    if (small) k_csmall<T, ND><<<nf, kSmallThreads, 0, s>>>(a());
     k_mark<T, ND><<<grid[K_SPARSE], kThreads, 0, s>>>(a());
   }
   template <class A>
@@ -711,7 +713,7 @@ void collect_times(msz_engine_s* E, int steps) {
         E->ks_work_ms[kid] += dt;
       }
       const int kind = (kid == KID_SWEEP || kid == KID_RECLASS)         ? 0
-                       : (kid == KID_GATHER || kid == KID_MARK || kid == KID_APPLY) ? 3
+                       : (kid == KID_GATHER || kid == KID_MARK || kid == KID_APPLY || kid == KID_CSMALL) ? 3
                        : (kid == KID_RCHECK)                             ? 2
                                                                          : 1;  // label stages
       E->kernel_ms[kind] += dt;

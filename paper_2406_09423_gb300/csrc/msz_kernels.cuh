@@ -485,6 +485,48 @@ __global__ void __launch_bounds__(kThreads) k_mark(GroupArgs<T> A) {
   tl.flush(A, K_SPARSE, none, done);
 }
 
+// One reclassification item: ring slot s of touched vertex u (slot 2 * NPOS:
+// u itself). The first item to reach a vertex in the round claims it (epoch
+// stamp) and recomputes its false-type bits and its direction byte in g; the
+// tile counts and acc move by the difference. When the bits change it
+// returns 0x10000 | (old << 8) | new and sets vc to the vertex, else 0.
+template <class T, int ND>
+__device__ __forceinline__ uint32_t reclass_item(const Field<T>& F, int u, int s, uint32_t stamp, uint32_t (&acc)[4],
+                                                 int& vc) {
+  constexpr int NPOS = Slots<ND>::NPOS;
+  const Geom& G = F.G;
+  int x, y, z;
+  coords(G, u, x, y, z);
+  int v = u;
+  if (s < 2 * NPOS) {
+    const int sg = (s < NPOS) ? 1 : -1;
+    const int m = (int)((Slots<ND>::MASKS >> (4 * (s < NPOS ? s : s - NPOS))) & 7u);
+    const int dx = sg * (m & 1), dy = sg * ((m >> 1) & 1), dz = sg * ((m >> 2) & 1);
+    x += dx;
+    y += dy;
+    z += dz;
+    if (x < 0 || x >= G.nx || y < 0 || y >= G.ny || z < 0 || z >= G.nz) return 0;
+    v = u + dx + dy * G.nx + dz * G.nxny;
+  }
+  if (atomicExch(&F.epoch[v], stamp) == stamp) return 0;
+  const uint8_t dv = direction_of<T, ND>(F.g, G, v, x, y, z);
+  F.gdir[v] = dv;  // g's direction bytes stay exact for the requests and the labels
+  const unsigned nb = case_bits(dv, F.fdir[v]);
+  const unsigned ob = F.cls[v];
+  if (nb == ob) return 0;
+  F.cls[v] = (uint8_t)nb;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const uint32_t d = ((nb >> c) & 1u) - ((ob >> c) & 1u);  // +1, 0 or -1 (mod 2^32)
+    if (d) {
+      atomicAdd(&F.ccnt[(v / kEmitTile) * 4 + c], d);
+      acc[c] += d;
+    }
+  }
+  vc = v;
+  return (ob << 8) | nb | 0x10000u;
+}
+
 // Incremental classification after an apply. A vertex's false-type bits
 // depend only on g over its closed 1-ring, so only the closed 1-rings of the
 // vertices the apply touched can change: the result equals a full sweep of
@@ -516,42 +558,11 @@ __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
     if ((uint32_t)(u_ - pre[i]) >= act) continue;  // left out: not counted
     tl.enter(A, K_SPARSE, i, pre_flush, done);
     tl.target = act;
-    const Geom G = F.G;
     const uint32_t stamp = (uint32_t)st->rounds;
     if (threadIdx.x == 0) log_units(A, st, KID_RECLASS, e - b);
-    for (uint64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
-      const int u = (int)F.touched[j / R];
-      const int s = (int)(j % R);
-      int x, y, z;
-      coords(G, u, x, y, z);
-      int v = u;
-      if (s < 2 * NPOS) {
-        const int sg = (s < NPOS) ? 1 : -1;
-        const int m = (int)((Slots<ND>::MASKS >> (4 * (s < NPOS ? s : s - NPOS))) & 7u);
-        const int dx = sg * (m & 1), dy = sg * ((m >> 1) & 1), dz = sg * ((m >> 2) & 1);
-        x += dx;
-        y += dy;
-        z += dz;
-        if (x < 0 || x >= G.nx || y < 0 || y >= G.ny || z < 0 || z >= G.nz) continue;
-        v = u + dx + dy * G.nx + dz * G.nxny;
-      }
-      if (atomicExch(&F.epoch[v], stamp) == stamp) continue;
-      const uint8_t dv = direction_of<T, ND>(F.g, G, v, x, y, z);
-      F.gdir[v] = dv;  // g's direction bytes stay exact for the requests and the labels
-      const unsigned nb = case_bits(dv, F.fdir[v]);
-      const unsigned ob = F.cls[v];
-      if (nb != ob) {
-        F.cls[v] = (uint8_t)nb;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const uint32_t d = ((nb >> c) & 1u) - ((ob >> c) & 1u);  // +1, 0 or -1 (mod 2^32)
-          if (d) {
-            atomicAdd(&F.ccnt[(v / kEmitTile) * 4 + c], d);
-            acc[c] += d;
-          }
-        }
-      }
-    }
+    int vc;
+    for (uint64_t j = b + threadIdx.x; j < e; j += blockDim.x)
+      reclass_item<T, ND>(F, (int)F.touched[j / R], (int)(j % R), stamp, acc, vc);
   }
   tl.flush(A, K_SPARSE, pre_flush, done);
 }
@@ -1167,6 +1178,26 @@ __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
   tl.flush(A, K_DENSE, pre_flush, done);
 }
 
+// Applies the flags of touched vertex u: a freeze sets g = f and freezes u
+// (acc[1]), a decrease halves g towards the lower bound (acc[0]); the label
+// tiles around u are marked dirty.
+template <class T>
+__device__ __forceinline__ void apply_vertex(const Field<T>& F, int u, uint32_t (&acc)[2]) {
+  uint8_t bb = F.flags[u];
+  if (bb & FL_FREEZE) {
+    F.g[u] = F.f[u];
+    bb = (uint8_t)((bb & ~(FL_DEC | FL_FREEZE)) | FL_FROZEN | FL_EDITED);
+    ++acc[1];
+  } else if (bb & FL_DEC) {
+    F.g[u] = decrease(F.g[u], lower_bound_of(F.f[u], F.xi));
+    bb = (uint8_t)((bb & ~FL_DEC) | FL_EDITED);
+    ++acc[0];
+  }
+  F.flags[u] = bb;
+  if (F.G.nd == 3) mark_dirty_tiles<3>(F.tdirty, F.G, u);
+  else mark_dirty_tiles<2>(F.tdirty, F.G, u);
+}
+
 // Applies a round's requests to the touched vertices only. Units are slices
 // of the touched list.
 template <class T>
@@ -1193,24 +1224,131 @@ __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
     tl.target = act;
     const uint32_t b = (uint32_t)b64, e = (uint32_t)e64;
     if (threadIdx.x == 0) log_units(A, st, KID_APPLY, e - b);
-    for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) {
-      const int u = (int)F.touched[j];
-      uint8_t bb = F.flags[u];
-      if (bb & FL_FREEZE) {
-        F.g[u] = F.f[u];
-        bb = (uint8_t)((bb & ~(FL_DEC | FL_FREEZE)) | FL_FROZEN | FL_EDITED);
-        ++acc[1];
-      } else if (bb & FL_DEC) {
-        F.g[u] = decrease(F.g[u], lower_bound_of(F.f[u], F.xi));
-        bb = (uint8_t)((bb & ~FL_DEC) | FL_EDITED);
-        ++acc[0];
-      }
-      F.flags[u] = bb;
-      if (F.G.nd == 3) mark_dirty_tiles<3>(F.tdirty, F.G, u);
-      else mark_dirty_tiles<2>(F.tdirty, F.G, u);
-    }
+    for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) apply_vertex(F, (int)F.touched[j], acc);
   }
   tl.flush(A, K_SPARSE, pre_flush, done);
+}
+
+// ---------------------------------------------------------------------------
+// Small C-loop rounds (Sec. 4.1) in one block per field. Most rounds of a fix
+// hold a few thousand cases or fewer, where four grid-wide launches per round
+// are mostly latency. This kernel takes a field whose listed round is small
+// and runs whole rounds - requests, apply, reclassification, the next
+// round's case list - with block barriers between the steps, through the
+// same state transitions and counters as the grid kernels. The next list is
+// the current one without the vertices that lost the type plus those the
+// reclassification gave it: every vertex of the type, the set a gather
+// lists. The field goes back to the grid kernels (with its cases listed, a
+// type to gather, or the R-loop) when a round outgrows the block, the type
+// changes, or after kSmallRounds rounds.
+// ---------------------------------------------------------------------------
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallPer = 4;  // cases per thread
+constexpr uint32_t kSmallCases = kSmallThreads * kSmallPer;
+constexpr int kSmallRounds = 64;
+
+// Adds each thread's n counters into s[0 .. n-1] (shared), one atomic per warp.
+template <int N>
+__device__ __forceinline__ void warp_add_shared(const uint32_t (&v)[N], uint32_t* s) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    uint32_t x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s[k], x);
+  }
+}
+
+template <class T, int ND>
+__global__ void __launch_bounds__(kSmallThreads) k_csmall(GroupArgs<T> A) {
+  if ((int)blockIdx.x >= A.nf) return;
+  const Field<T>& F = A.fields[blockIdx.x];
+  DevState* st = F.st;
+  if (!(st->phase == PH_C && st->action == ACT_REQUEST && st->ncase <= kSmallCases)) return;
+  constexpr int R = 2 * Slots<ND>::NPOS + 1;
+  __shared__ uint32_t s_nt, s_nn, s_len, s_go;
+  __shared__ uint32_t s_acc[6];
+  uint32_t rounds = 0;
+  for (int it = 0; it < kSmallRounds; ++it) {
+    if (threadIdx.x == 0) {
+      s_nt = s_nn = s_len = 0;
+      for (int k = 0; k < 6; ++k) s_acc[k] = 0;
+    }
+    __syncthreads();
+    const uint32_t type = st->T, nc = st->ncase;
+    // requests (Eqs. 2-5) for this thread's cases, all from one snapshot of g
+    int cv[kSmallPer];
+#pragma unroll
+    for (int k = 0; k < kSmallPer; ++k) {
+      const uint32_t j = threadIdx.x + (uint32_t)k * kSmallThreads;
+      cv[k] = j < nc ? (int)F.cases[j] : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kSmallPer; ++k) {
+      if (cv[k] < 0) continue;
+      const int v = cv[k];
+      const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(F.gdir[v] & 15, ND, F.G.nx, F.G.nxny);
+      request<T, ND>(F, v, t, &s_nt);
+    }
+    __syncthreads();
+    const uint32_t nt = s_nt;
+    {
+      uint32_t acc[2] = {0, 0};
+      for (uint32_t j = threadIdx.x; j < nt; j += kSmallThreads) apply_vertex(F, (int)F.touched[j], acc);
+      warp_add_shared<2>(acc, s_acc);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      st->stripe[0][0] += s_acc[0];
+      st->stripe[0][1] += s_acc[1];
+      st->ntouch = nt;
+      ctrl_after_apply(st, ACT_MARK_C);
+      s_go = st->action == ACT_RECLASS;
+    }
+    __syncthreads();
+    if (!s_go) break;
+    {
+      const uint32_t stamp = (uint32_t)st->rounds;
+      uint32_t acc[4] = {0, 0, 0, 0};
+      for (uint32_t j = threadIdx.x; j < nt * R; j += kSmallThreads) {
+        int vc = 0;
+        const uint32_t ch = reclass_item<T, ND>(F, (int)F.touched[j / R], (int)(j % R), stamp, acc, vc);
+        // a vertex that gained the type joins the next round's cases
+        if (((ch >> type) & 1u) && !((ch >> (8 + type)) & 1u)) F.lc[1][atomicAdd(&s_nn, 1u)] = (uint32_t)vc;
+      }
+      warp_add_shared<4>(acc, s_acc + 2);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int c = 0; c < 4; ++c) st->stripe[0][c] += s_acc[2 + c];
+      ctrl_after_classify(st);
+      s_go = st->phase == PH_C && st->action == ACT_GATHER && st->T == type && st->counts[type] <= kSmallCases;
+    }
+    __syncthreads();
+    ++rounds;
+    if (!s_go) break;
+    // the next round's cases: this round's that kept the type, then the new
+#pragma unroll
+    for (int k = 0; k < kSmallPer; ++k)
+      if (cv[k] >= 0 && ((F.cls[cv[k]] >> type) & 1u)) F.cases[atomicAdd(&s_len, 1u)] = (uint32_t)cv[k];
+    __syncthreads();
+    const uint32_t base = s_len, nn = s_nn;
+    for (uint32_t j = threadIdx.x; j < nn; j += kSmallThreads) F.cases[base + j] = F.lc[1][j];
+    if (threadIdx.x == 0) {
+      // the list holds every vertex of the type; otherwise the grid's gather lists them
+      if (base + nn == st->counts[type]) {
+        st->ncase = base + nn;
+        st->action = ACT_REQUEST;
+      }
+      s_go = st->action == ACT_REQUEST;
+    }
+    __syncthreads();
+    if (!s_go) break;
+  }
+  if (threadIdx.x == 0 && rounds) {
+    log_units(A, st, KID_CSMALL, rounds);
+    log_work(A);
+  }
 }
 
 // ---------------------------------------------------------------------------
