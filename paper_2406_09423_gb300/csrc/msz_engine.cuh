@@ -299,9 +299,10 @@ __device__ void ctrl_after_init(DevState* st) {
 // incremental one after an apply; Sec. 4.1): the next sub-loop type with
 // cases, the end of a pass after FNmin, or the R-loop when a whole pass is
 // clean. The type counts are those of the current g, so advancing the type
-// needs no new sweep.
-__device__ void ctrl_after_classify(DevState* st) {
-  fold_stripes(st, st->counts, 4);  // the reclassification's count changes
+// needs no new sweep. _counted: the classification's count changes are
+// already in st->counts (a single writer); the other form first folds them
+// in from the stripes.
+__device__ void ctrl_after_classify_counted(DevState* st) {
   uint32_t c[4];
   for (int t = 0; t < 4; ++t) c[t] = vload(&st->counts[t]);
   st->ntouch = st->ncase = 0;
@@ -328,6 +329,11 @@ __device__ void ctrl_after_classify(DevState* st) {
   }
   st->T = T_;
   st->ticks++;
+}
+
+__device__ void ctrl_after_classify(DevState* st) {
+  fold_stripes(st, st->counts, 4);  // the reclassification's count changes
+  ctrl_after_classify_counted(st);
 }
 
 __device__ void ctrl_after_jump(DevState* st) {
@@ -374,8 +380,10 @@ __device__ void ctrl_after_rcheck(DevState* st) {
   }
 }
 
-__device__ void ctrl_after_apply(DevState* st, uint32_t act) {
-  fold_stripes(st, st->acc_ap, 2);
+// Round bookkeeping after an apply (act: the C-loop's requests or the
+// R-loop's). _counted: the apply's sums are already in st->acc_ap (a single
+// writer); the other form first folds them in from the stripes.
+__device__ void ctrl_after_apply_counted(DevState* st, uint32_t act) {
   st->cnt.dec_edits += vload(&st->acc_ap[0]);
   st->cnt.freezes += vload(&st->acc_ap[1]);
   st->ticks++;
@@ -400,6 +408,11 @@ __device__ void ctrl_after_apply(DevState* st, uint32_t act) {
   }
   st->acc_ap[0] = st->acc_ap[1] = 0;
   st->acc_r[2] = st->acc_r[3] = 0;
+}
+
+__device__ void ctrl_after_apply(DevState* st, uint32_t act) {
+  fold_stripes(st, st->acc_ap, 2);
+  ctrl_after_apply_counted(st, act);
 }
 
 // ---------------------------------------------------------------------------

@@ -232,6 +232,7 @@ struct Group {
   GroupArgs<T> args{};
   bool tma = false;
   int grid[NKIND] = {};
+  bool small_ok = false;  // a k_csmall cluster fits on the device
   size_t label_smem = 0;
 
   // Host arrays for nf fields (null pointers while measuring).
@@ -358,7 +359,22 @@ struct Group {
         cudaSuccess)
       return MSZ_ERR_CUDA;
     grid[K_LABEL] = occ_grid((const void*)k_label_tile<T, ND>, kThreads, label_smem, args.total[K_LABEL]);
-    return cudaGetLastError() == cudaSuccess ? MSZ_OK : MSZ_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return MSZ_ERR_CUDA;
+    {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(kSmallCluster);
+      cfg.blockDim = dim3(kSmallThreads);
+      cudaLaunchAttribute at;
+      at.id = cudaLaunchAttributeClusterDimension;
+      at.val.clusterDim.x = kSmallCluster;
+      at.val.clusterDim.y = at.val.clusterDim.z = 1;
+      cfg.attrs = &at;
+      cfg.numAttrs = 1;
+      int ncl = 0;
+      small_ok = cudaOccupancyMaxActiveClusters(&ncl, k_csmall<T, ND>, &cfg) == cudaSuccess && ncl > 0;
+      cudaGetLastError();  // a device without clusters of this size runs every round on the grid kernels
+    }
+    return MSZ_OK;
   }
 
   // Uploads the descriptors with this run's inputs and bounds.
@@ -424,7 +440,10 @@ struct Group {
   template <class A>
   void gather(cudaStream_t s, A&& a, bool small) {
     k_gather<T, ND><<<grid[K_CASE], kThreads, 0, s>>>(a());
-    if (small) k_csmall<T, ND><<<nf, kSmallThreads, 0, s>>>(a());
+    if (small) {
+      const GroupArgs<T> x = a();  // the slot counts even when the kernel is left out
+      if (small_ok) k_csmall<T, ND><<<nf * kSmallCluster, kSmallThreads, 0, s>>>(x);
+    }
     k_mark<T, ND><<<grid[K_SPARSE], kThreads, 0, s>>>(a());
   }
   template <class A>

@@ -1,6 +1,7 @@
 // Work-unit kernels of the MSz correction loop (see msz_engine.cuh).
 #pragma once
 
+#include <cooperative_groups.h>
 #include "msz_engine.cuh"
 
 namespace msz {
@@ -1230,24 +1231,44 @@ __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
 }
 
 // ---------------------------------------------------------------------------
-// Small C-loop rounds (Sec. 4.1) in one block per field. Most rounds of a fix
-// hold a few thousand cases or fewer, where four grid-wide launches per round
-// are mostly latency. This kernel takes a field whose listed round is small
-// and runs whole rounds - requests, apply, reclassification, the next
-// round's case list - with block barriers between the steps, through the
-// same state transitions and counters as the grid kernels. The next list is
-// the current one without the vertices that lost the type plus those the
-// reclassification gave it: every vertex of the type, the set a gather
-// lists. The field goes back to the grid kernels (with its cases listed, a
-// type to gather, or the R-loop) when a round outgrows the block, the type
-// changes, or after kSmallRounds rounds.
+// Small C-loop rounds (Sec. 4.1) in one thread-block cluster per field. Most
+// rounds of a fix hold a few thousand cases or fewer, where four grid-wide
+// launches per round are mostly latency. This kernel takes a field whose
+// listed round is small and runs whole rounds - requests, apply,
+// reclassification, the next round's case list - with cluster barriers
+// between the steps, through the same state transitions and counters as the
+// grid kernels. The next list is the current one without the vertices that
+// lost the type plus those the reclassification gave it: every vertex of the
+// type, the set a gather lists. The field goes back to the grid kernels (with
+// its cases listed, a type to gather, or the R-loop) when a round outgrows
+// the cluster, the type changes, or after kSmallRounds rounds. The cluster's
+// counters live in the shared memory of its block 0.
 // ---------------------------------------------------------------------------
 constexpr int kSmallThreads = 1024;
+constexpr int kSmallCluster = 8;  // blocks per field
+constexpr uint32_t kSmallSpan = (uint32_t)kSmallThreads * kSmallCluster;
 constexpr int kSmallPer = 4;  // cases per thread
-constexpr uint32_t kSmallCases = kSmallThreads * kSmallPer;
+constexpr uint32_t kSmallCases = kSmallSpan * kSmallPer;
 constexpr int kSmallRounds = 64;
 
-// Adds each thread's n counters into s[0 .. n-1] (shared), one atomic per warp.
+// Barrier of the cluster, release / acquire at cluster scope: every memory
+// access (global or shared) before it happens before those after it in all
+// of the cluster's threads.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// The address of shared variable p in the cluster's block 0.
+__device__ __forceinline__ uint32_t* in_block0(uint32_t* p) {
+  return cooperative_groups::this_cluster().map_shared_rank(p, 0);
+}
+
+// Adds each thread's n counters into s[0 .. n-1] (shared memory of this or
+// another block of the cluster), one atomic per warp.
 template <int N>
 __device__ __forceinline__ void warp_add_shared(const uint32_t (&v)[N], uint32_t* s) {
 #pragma unroll
@@ -1260,27 +1281,33 @@ __device__ __forceinline__ void warp_add_shared(const uint32_t (&v)[N], uint32_t
 }
 
 template <class T, int ND>
-__global__ void __launch_bounds__(kSmallThreads) k_csmall(GroupArgs<T> A) {
-  if ((int)blockIdx.x >= A.nf) return;
-  const Field<T>& F = A.fields[blockIdx.x];
+__global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallThreads) k_csmall(GroupArgs<T> A) {
+  const int fi = (int)blockIdx.x / kSmallCluster;  // a cluster per field
+  if (fi >= A.nf) return;
+  const Field<T>& F = A.fields[fi];
   DevState* st = F.st;
+  // the same for the whole cluster: nothing writes the state before the first barrier
   if (!(st->phase == PH_C && st->action == ACT_REQUEST && st->ncase <= kSmallCases)) return;
   constexpr int R = 2 * Slots<ND>::NPOS + 1;
-  __shared__ uint32_t s_nt, s_nn, s_len, s_go;
-  __shared__ uint32_t s_acc[6];
+  // block 0's: touched count, -, next list length, go, apply sums (2), count changes (4)
+  __shared__ uint32_t s_ctl[10];
+  uint32_t* const C = in_block0(s_ctl);
+  const uint32_t gt = cluster_rank() * kSmallThreads + threadIdx.x;
+  if (gt == 0) {
+    for (int k = 0; k < 10; ++k) C[k] = 0;
+    C[3] = 1;
+  }
   uint32_t rounds = 0;
   for (int it = 0; it < kSmallRounds; ++it) {
-    if (threadIdx.x == 0) {
-      s_nt = s_nn = s_len = 0;
-      for (int k = 0; k < 6; ++k) s_acc[k] = 0;
-    }
-    __syncthreads();
+    cluster_barrier();  // the round's case list, state and counters are in place
+    if (!C[3]) break;
     const uint32_t type = st->T, nc = st->ncase;
+    const uint64_t r1 = st->rounds + 1;  // the round's number once applied
     // requests (Eqs. 2-5) for this thread's cases, all from one snapshot of g
     int cv[kSmallPer];
 #pragma unroll
     for (int k = 0; k < kSmallPer; ++k) {
-      const uint32_t j = threadIdx.x + (uint32_t)k * kSmallThreads;
+      const uint32_t j = gt + (uint32_t)k * kSmallSpan;
       cv[k] = j < nc ? (int)F.cases[j] : -1;
     }
 #pragma unroll
@@ -1288,64 +1315,63 @@ __global__ void __launch_bounds__(kSmallThreads) k_csmall(GroupArgs<T> A) {
       if (cv[k] < 0) continue;
       const int v = cv[k];
       const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(F.gdir[v] & 15, ND, F.G.nx, F.G.nxny);
-      request<T, ND>(F, v, t, &s_nt);
+      request<T, ND>(F, v, t, &C[0]);
     }
-    __syncthreads();
-    const uint32_t nt = s_nt;
+    cluster_barrier();
+    const uint32_t nt = C[0];
     {
       uint32_t acc[2] = {0, 0};
-      for (uint32_t j = threadIdx.x; j < nt; j += kSmallThreads) apply_vertex(F, (int)F.touched[j], acc);
-      warp_add_shared<2>(acc, s_acc);
+      for (uint32_t j = gt; j < nt; j += kSmallSpan) apply_vertex(F, (int)F.touched[j], acc);
+      warp_add_shared<2>(acc, C + 4);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      st->stripe[0][0] += s_acc[0];
-      st->stripe[0][1] += s_acc[1];
+    cluster_barrier();
+    if (gt == 0) {
+      st->acc_ap[0] += C[4];
+      st->acc_ap[1] += C[5];
       st->ntouch = nt;
-      ctrl_after_apply(st, ACT_MARK_C);
-      s_go = st->action == ACT_RECLASS;
+      ctrl_after_apply_counted(st, ACT_MARK_C);
     }
-    __syncthreads();
-    if (!s_go) break;
+    if (r1 > st->max_rounds) break;  // the round cap: the bookkeeping above ends the fix
     {
-      const uint32_t stamp = (uint32_t)st->rounds;
+      // The old cases are in registers, so the next list can be written over
+      // them: first the vertices the reclassification gives the type.
+      const uint32_t stamp = (uint32_t)r1;
       uint32_t acc[4] = {0, 0, 0, 0};
-      for (uint32_t j = threadIdx.x; j < nt * R; j += kSmallThreads) {
+      for (uint32_t j = gt; j < nt * R; j += kSmallSpan) {
         int vc = 0;
         const uint32_t ch = reclass_item<T, ND>(F, (int)F.touched[j / R], (int)(j % R), stamp, acc, vc);
-        // a vertex that gained the type joins the next round's cases
-        if (((ch >> type) & 1u) && !((ch >> (8 + type)) & 1u)) F.lc[1][atomicAdd(&s_nn, 1u)] = (uint32_t)vc;
+        if (((ch >> type) & 1u) && !((ch >> (8 + type)) & 1u)) F.cases[atomicAdd(&C[2], 1u)] = (uint32_t)vc;
       }
-      warp_add_shared<4>(acc, s_acc + 2);
+      warp_add_shared<4>(acc, C + 6);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int c = 0; c < 4; ++c) st->stripe[0][c] += s_acc[2 + c];
-      ctrl_after_classify(st);
-      s_go = st->phase == PH_C && st->action == ACT_GATHER && st->T == type && st->counts[type] <= kSmallCases;
-    }
-    __syncthreads();
-    ++rounds;
-    if (!s_go) break;
-    // the next round's cases: this round's that kept the type, then the new
+    cluster_barrier();
+    // then this round's cases that kept the type
 #pragma unroll
     for (int k = 0; k < kSmallPer; ++k)
-      if (cv[k] >= 0 && ((F.cls[cv[k]] >> type) & 1u)) F.cases[atomicAdd(&s_len, 1u)] = (uint32_t)cv[k];
-    __syncthreads();
-    const uint32_t base = s_len, nn = s_nn;
-    for (uint32_t j = threadIdx.x; j < nn; j += kSmallThreads) F.cases[base + j] = F.lc[1][j];
-    if (threadIdx.x == 0) {
-      // the list holds every vertex of the type; otherwise the grid's gather lists them
-      if (base + nn == st->counts[type]) {
-        st->ncase = base + nn;
+      if (cv[k] >= 0 && ((F.cls[cv[k]] >> type) & 1u)) F.cases[atomicAdd(&C[2], 1u)] = (uint32_t)cv[k];
+    if (gt == 0) {
+      for (int c = 0; c < 4; ++c) st->counts[c] += C[6 + c];
+      ctrl_after_classify_counted(st);
+    }
+    cluster_barrier();
+    ++rounds;
+    if (gt == 0) {
+      // go on with the same type while its round stays small and the list
+      // holds every vertex of the type; otherwise the grid's gather lists it
+      const uint32_t len = C[2];
+      const bool go = st->phase == PH_C && st->action == ACT_GATHER && st->T == type &&
+                      st->counts[type] <= kSmallCases && len == st->counts[type];
+      if (go) {
+        st->ncase = len;
         st->action = ACT_REQUEST;
       }
-      s_go = st->action == ACT_REQUEST;
+      for (int k = 0; k < 10; ++k) C[k] = 0;
+      C[3] = go;
     }
-    __syncthreads();
-    if (!s_go) break;
   }
-  if (threadIdx.x == 0 && rounds) {
+  // block 0's shared memory stays until every block is done with it
+  cluster_barrier();
+  if (gt == 0 && rounds) {
     log_units(A, st, KID_CSMALL, rounds);
     log_work(A);
   }
