@@ -444,14 +444,19 @@ __device__ __forceinline__ void mark(const Field<T>& F, int u, uint8_t bit, uint
     F.touched[ln ? atomicAdd(ln, 1u) : list_slot(&F.st->ntouch)] = (uint32_t)u;
 }
 
+// Whether a request for target t decreases t (else its anchor's ring freezes).
+template <class T>
+__device__ __forceinline__ bool request_decreases(const Field<T>& F, int t) {
+  return !(F.flags[t] & FL_FROZEN) && F.g[t] > lower_bound_of(F.f[t], F.xi);
+}
+
 // A false case anchored at a asks for a decreasing edit of t. If t is frozen
 // or already at its lower bound, the non-frozen part of a's closed 1-ring is
 // frozen instead (termination guard; the paper argues convergence in the
 // reals, Sec. 4.3).
 template <class T, int ND>
 __device__ void request(const Field<T>& F, int a, int t, uint32_t* ln = nullptr) {
-  const uint8_t ft = F.flags[t];
-  if (!(ft & FL_FROZEN) && F.g[t] > lower_bound_of(F.f[t], F.xi)) {
+  if (request_decreases(F, t)) {
     mark(F, t, FL_DEC, ln);
     return;
   }
@@ -474,17 +479,10 @@ __device__ void request(const Field<T>& F, int a, int t, uint32_t* ln = nullptr)
   }
 }
 
-// request() by a whole warp (lane = the thread's lane): lane 0 decides;
-// a freeze marks the closed 1-ring with one lane per vertex.
+// The freeze of anchor a's closed 1-ring by a whole warp, one lane per
+// vertex (lane = the thread's lane); touched-list slots as in mark().
 template <class T, int ND>
-__device__ __forceinline__ void request_warp(const Field<T>& F, int a, int t, int lane) {
-  int dec = 0;
-  if (lane == 0) dec = !(F.flags[t] & FL_FROZEN) && F.g[t] > lower_bound_of(F.f[t], F.xi);
-  dec = __shfl_sync(kFull, dec, 0);
-  if (dec) {
-    if (lane == 0) mark(F, t, FL_DEC);
-    return;
-  }
+__device__ __forceinline__ void freeze_ring_warp(const Field<T>& F, int a, int lane, uint32_t* ln = nullptr) {
   constexpr int NPOS = Slots<ND>::NPOS;
   if (lane > 2 * NPOS) return;
   int u = a;
@@ -500,7 +498,22 @@ __device__ __forceinline__ void request_warp(const Field<T>& F, int a, int t, in
     if (!in) return;
     u = a + dx + dy * F.G.nx + dz * F.G.nxny;
   }
-  if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE);
+  if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE, ln);
 }
+
+// request() by a whole warp (lane = the thread's lane): lane 0 decides;
+// a freeze marks the closed 1-ring with one lane per vertex.
+template <class T, int ND>
+__device__ __forceinline__ void request_warp(const Field<T>& F, int a, int t, int lane) {
+  int dec = 0;
+  if (lane == 0) dec = request_decreases(F, t);
+  dec = __shfl_sync(kFull, dec, 0);
+  if (dec) {
+    if (lane == 0) mark(F, t, FL_DEC);
+    return;
+  }
+  freeze_ring_warp<T, ND>(F, a, lane);
+}
+
 
 }  // namespace msz

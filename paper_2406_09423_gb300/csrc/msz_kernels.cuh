@@ -1289,7 +1289,7 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
   // the same for the whole cluster: nothing writes the state before the first barrier
   if (!(st->phase == PH_C && st->action == ACT_REQUEST && st->ncase <= kSmallCases)) return;
   constexpr int R = 2 * Slots<ND>::NPOS + 1;
-  // block 0's: touched count, -, next list length, go, apply sums (2), count changes (4)
+  // block 0's: touched count, freezes, next list length, go, apply sums (2), count changes (4)
   __shared__ uint32_t s_ctl[10];
   uint32_t* const C = in_block0(s_ctl);
   const uint32_t gt = cluster_rank() * kSmallThreads + threadIdx.x;
@@ -1303,7 +1303,9 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
     if (!C[3]) break;
     const uint32_t type = st->T, nc = st->ncase;
     const uint64_t r1 = st->rounds + 1;  // the round's number once applied
-    // requests (Eqs. 2-5) for this thread's cases, all from one snapshot of g
+    // requests (Eqs. 2-5) for this thread's cases, all from one snapshot of
+    // g: decreases at once; freezes are listed (lc[0], idle in the C-loop)
+    // for the warps below, since a freeze marks a whole ring
     int cv[kSmallPer];
 #pragma unroll
     for (int k = 0; k < kSmallPer; ++k) {
@@ -1315,9 +1317,16 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
       if (cv[k] < 0) continue;
       const int v = cv[k];
       const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(F.gdir[v] & 15, ND, F.G.nx, F.G.nxny);
-      request<T, ND>(F, v, t, &C[0]);
+      if (request_decreases(F, t)) mark(F, t, FL_DEC, &C[0]);
+      else F.lc[0][atomicAdd(&C[1], 1u)] = (uint32_t)v;
     }
     cluster_barrier();
+    if (const uint32_t nfz = C[1]) {
+      // a warp per freeze, a lane per vertex of the anchor's closed ring
+      for (uint32_t q = gt >> 5; q < nfz; q += kSmallSpan >> 5)
+        freeze_ring_warp<T, ND>(F, (int)F.lc[0][q], (int)(threadIdx.x & 31), &C[0]);
+      cluster_barrier();
+    }
     const uint32_t nt = C[0];
     {
       uint32_t acc[2] = {0, 0};
