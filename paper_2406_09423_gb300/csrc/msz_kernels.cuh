@@ -1106,7 +1106,7 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
 // neighbour in g (Eq. 6). Wrong min label: decrease the descending neighbour
 // that f prescribes.
 template <class T, int ND>
-__global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
+__global__ void __launch_bounds__(kThreads, 6) k_rcheck(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
   auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_DONE; };
   uint32_t acc[4] = {0, 0, 0, 0};
@@ -1119,6 +1119,14 @@ __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
     else ctrl_after_rcheck(st);
     log_work(A);
   };
+  // Troublemakers whose request freezes a ring: their anchors, marked by
+  // the block's warps at the end of the unit (a lane per ring vertex)
+  // instead of vertex by vertex in one thread.
+  constexpr uint32_t kRFreeze = 1024;
+  __shared__ uint32_t s_fz[kRFreeze];
+  __shared__ uint32_t s_nfz;
+  if (threadIdx.x == 0) s_nfz = 0;
+  __syncthreads();
   UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
     tl.enter(A, K_DENSE, i, pre_flush, done);
@@ -1126,6 +1134,16 @@ __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
     DevState* st = F.st;
     const int v0 = (u_ - pre[i]) * kDenseChunk;
     const int v1 = min(F.G.n, v0 + kDenseChunk);
+    // the request of troublemaker a for target t (Eq. 6)
+    auto trouble = [&](int a, int t) {
+      if (request_decreases(F, t)) {
+        mark(F, t, FL_DEC);
+        return;
+      }
+      const uint32_t q = atomicAdd(&s_nfz, 1u);
+      if (q < kRFreeze) s_fz[q] = (uint32_t)a;
+      else request<T, ND>(F, a, t);  // list full: the same freeze, vertex by vertex
+    };
     if (st->ljob == 0) {
       for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
         F.Mf[v] = resolve_label(F, 0, F.Mf, v);
@@ -1164,16 +1182,25 @@ __global__ void __launch_bounds__(kThreads) k_rcheck(GroupArgs<T> A) {
           ++acc[0];
           if ((d & 15) != (fd & 15)) {
             ++acc[2];
-            request<T, ND>(F, v, v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny));
+            trouble(v, v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny));
           }
         } else {
           ++acc[1];
           if ((d >> 4) != (fd >> 4)) {
             ++acc[3];
-            request<T, ND>(F, v, v + slot_offset(fd >> 4, ND, F.G.nx, F.G.nxny));
+            trouble(v, v + slot_offset(fd >> 4, ND, F.G.nx, F.G.nxny));
           }
         }
       }
+    }
+    __syncthreads();
+    const uint32_t nfz = min(s_nfz, kRFreeze);
+    if (nfz) {
+      __syncthreads();  // every thread has read the count
+      if (threadIdx.x == 0) s_nfz = 0;
+      for (uint32_t q = threadIdx.x >> 5; q < nfz; q += kThreads / 32)
+        freeze_ring_warp<T, ND>(F, (int)s_fz[q], (int)(threadIdx.x & 31));
+      __syncthreads();  // the list is free for the next unit
     }
   }
   tl.flush(A, K_DENSE, pre_flush, done);
