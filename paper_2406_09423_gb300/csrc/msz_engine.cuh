@@ -433,15 +433,35 @@ __device__ __forceinline__ uint32_t list_slot(uint32_t* ctr) {
   return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
 }
 
-// Flags vertex u; its first flag of the round adds it to the touched list,
-// whose length is st->ntouch, or *ln (a block's own count) when given.
+// Where a vertex's first flag of the round adds it to the touched list:
+// by default a slot from st->ntouch; with n alone, slot *n (a block or
+// cluster that owns the whole list counts it itself); with buf, the block's
+// staging buffer (buf[*n], flushed to the list later; a full buffer sends the
+// vertex straight to the list).
+struct TouchSink {
+  uint32_t* n = nullptr;
+  uint32_t* buf = nullptr;
+  uint32_t cap = 0;
+};
+
+// Flags vertex u; its first flag of the round puts it on the touched list.
 template <class T>
-__device__ __forceinline__ void mark(const Field<T>& F, int u, uint8_t bit, uint32_t* ln = nullptr) {
+__device__ __forceinline__ void mark(const Field<T>& F, int u, uint8_t bit, const TouchSink& ts = TouchSink()) {
   uint32_t* w = reinterpret_cast<uint32_t*>(F.flags) + (u >> 2);
   const int sh = (u & 3) * 8;
   const uint32_t old = atomicOr(w, (uint32_t)bit << sh);
-  if (((old >> sh) & (FL_DEC | FL_FREEZE)) == 0)
-    F.touched[ln ? atomicAdd(ln, 1u) : list_slot(&F.st->ntouch)] = (uint32_t)u;
+  if (((old >> sh) & (FL_DEC | FL_FREEZE)) != 0) return;
+  if (ts.buf) {
+    const uint32_t q = atomicAdd(ts.n, 1u);
+    if (q < ts.cap) {
+      ts.buf[q] = (uint32_t)u;
+      return;
+    }
+  } else if (ts.n) {
+    F.touched[atomicAdd(ts.n, 1u)] = (uint32_t)u;
+    return;
+  }
+  F.touched[list_slot(&F.st->ntouch)] = (uint32_t)u;
 }
 
 // Whether a request for target t decreases t (else its anchor's ring freezes).
@@ -455,14 +475,14 @@ __device__ __forceinline__ bool request_decreases(const Field<T>& F, int t) {
 // frozen instead (termination guard; the paper argues convergence in the
 // reals, Sec. 4.3).
 template <class T, int ND>
-__device__ void request(const Field<T>& F, int a, int t, uint32_t* ln = nullptr) {
+__device__ void request(const Field<T>& F, int a, int t, const TouchSink& ts = TouchSink()) {
   if (request_decreases(F, t)) {
-    mark(F, t, FL_DEC, ln);
+    mark(F, t, FL_DEC, ts);
     return;
   }
   int x, y, z;
   coords(F.G, a, x, y, z);
-  if (!(F.flags[a] & FL_FROZEN)) mark(F, a, FL_FREEZE, ln);
+  if (!(F.flags[a] & FL_FROZEN)) mark(F, a, FL_FREEZE, ts);
   constexpr int NPOS = Slots<ND>::NPOS;
 #pragma unroll
   for (int s = 0; s < 2 * NPOS; ++s) {
@@ -474,15 +494,16 @@ __device__ void request(const Field<T>& F, int a, int t, uint32_t* ln = nullptr)
     if (ND == 3) in = in && Z >= 0 && Z < F.G.nz;
     if (in) {
       const int u = a + dx + dy * F.G.nx + dz * F.G.nxny;
-      if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE, ln);
+      if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE, ts);
     }
   }
 }
 
 // The freeze of anchor a's closed 1-ring by a whole warp, one lane per
-// vertex (lane = the thread's lane); touched-list slots as in mark().
+// vertex (lane = the thread's lane); touched list as in mark().
 template <class T, int ND>
-__device__ __forceinline__ void freeze_ring_warp(const Field<T>& F, int a, int lane, uint32_t* ln = nullptr) {
+__device__ __forceinline__ void freeze_ring_warp(const Field<T>& F, int a, int lane,
+                                                 const TouchSink& ts = TouchSink()) {
   constexpr int NPOS = Slots<ND>::NPOS;
   if (lane > 2 * NPOS) return;
   int u = a;
@@ -498,7 +519,7 @@ __device__ __forceinline__ void freeze_ring_warp(const Field<T>& F, int a, int l
     if (!in) return;
     u = a + dx + dy * F.G.nx + dz * F.G.nxny;
   }
-  if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE, ln);
+  if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE, ts);
 }
 
 // request() by a whole warp (lane = the thread's lane): lane 0 decides;

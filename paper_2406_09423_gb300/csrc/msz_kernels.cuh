@@ -1125,7 +1125,16 @@ __global__ void __launch_bounds__(kThreads, 6) k_rcheck(GroupArgs<T> A) {
   constexpr uint32_t kRFreeze = 1024;
   __shared__ uint32_t s_fz[kRFreeze];
   __shared__ uint32_t s_nfz;
-  if (threadIdx.x == 0) s_nfz = 0;
+  // The unit's touched vertices, staged here and added to the field's list
+  // with one atomic per unit (a single counter for the whole grid otherwise).
+  constexpr uint32_t kRStage = 2048;
+  __shared__ uint32_t s_tv[kRStage];
+  __shared__ uint32_t s_ntv, s_base;
+  TouchSink ts;
+  ts.n = &s_ntv;
+  ts.buf = s_tv;
+  ts.cap = kRStage;
+  if (threadIdx.x == 0) s_nfz = s_ntv = 0;
   __syncthreads();
   UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
@@ -1137,12 +1146,12 @@ __global__ void __launch_bounds__(kThreads, 6) k_rcheck(GroupArgs<T> A) {
     // the request of troublemaker a for target t (Eq. 6)
     auto trouble = [&](int a, int t) {
       if (request_decreases(F, t)) {
-        mark(F, t, FL_DEC);
+        mark(F, t, FL_DEC, ts);
         return;
       }
       const uint32_t q = atomicAdd(&s_nfz, 1u);
       if (q < kRFreeze) s_fz[q] = (uint32_t)a;
-      else request<T, ND>(F, a, t);  // list full: the same freeze, vertex by vertex
+      else request<T, ND>(F, a, t, ts);  // list full: the same freeze, vertex by vertex
     };
     if (st->ljob == 0) {
       for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
@@ -1199,8 +1208,19 @@ __global__ void __launch_bounds__(kThreads, 6) k_rcheck(GroupArgs<T> A) {
       __syncthreads();  // every thread has read the count
       if (threadIdx.x == 0) s_nfz = 0;
       for (uint32_t q = threadIdx.x >> 5; q < nfz; q += kThreads / 32)
-        freeze_ring_warp<T, ND>(F, (int)s_fz[q], (int)(threadIdx.x & 31));
+        freeze_ring_warp<T, ND>(F, (int)s_fz[q], (int)(threadIdx.x & 31), ts);
       __syncthreads();  // the list is free for the next unit
+    }
+    const uint32_t ntv = min(s_ntv, kRStage);
+    if (ntv) {
+      __syncthreads();  // every thread has read the count
+      if (threadIdx.x == 0) {
+        s_base = atomicAdd(&st->ntouch, ntv);
+        s_ntv = 0;
+      }
+      __syncthreads();
+      for (uint32_t j = threadIdx.x; j < ntv; j += kThreads) F.touched[s_base + j] = s_tv[j];
+      __syncthreads();  // the buffer is free for the next unit
     }
   }
   tl.flush(A, K_DENSE, pre_flush, done);
@@ -1319,6 +1339,8 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
   // block 0's: touched count, freezes, next list length, go, apply sums (2), count changes (4)
   __shared__ uint32_t s_ctl[10];
   uint32_t* const C = in_block0(s_ctl);
+  TouchSink ts;
+  ts.n = &C[0];  // the cluster counts the round's touched list itself
   const uint32_t gt = cluster_rank() * kSmallThreads + threadIdx.x;
   if (gt == 0) {
     for (int k = 0; k < 10; ++k) C[k] = 0;
@@ -1344,14 +1366,14 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
       if (cv[k] < 0) continue;
       const int v = cv[k];
       const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(F.gdir[v] & 15, ND, F.G.nx, F.G.nxny);
-      if (request_decreases(F, t)) mark(F, t, FL_DEC, &C[0]);
+      if (request_decreases(F, t)) mark(F, t, FL_DEC, ts);
       else F.lc[0][atomicAdd(&C[1], 1u)] = (uint32_t)v;
     }
     cluster_barrier();
     if (const uint32_t nfz = C[1]) {
       // a warp per freeze, a lane per vertex of the anchor's closed ring
       for (uint32_t q = gt >> 5; q < nfz; q += kSmallSpan >> 5)
-        freeze_ring_warp<T, ND>(F, (int)F.lc[0][q], (int)(threadIdx.x & 31), &C[0]);
+        freeze_ring_warp<T, ND>(F, (int)F.lc[0][q], (int)(threadIdx.x & 31), ts);
       cluster_barrier();
     }
     const uint32_t nt = C[0];
