@@ -101,6 +101,20 @@ def peaks():
         return None
 
 
+# Kernels whose bound is HBM streaming (the roofline object picks the one
+# with the most working time among them); k_label_tile is bound by
+# instruction issue in its shared-memory pointer doubling, the sparse
+# C-loop kernels by L2 latency.
+HBM_BOUND = ("k_csweep", "k_ecount", "k_efill", "k_jump", "k_rcheck")
+
+# DRAM bytes per work unit from one ncu capture of a working launch on the
+# 320^3 field of the same workload (dram__bytes_read.sum +
+# dram__bytes_write.sum of the launch / its units; profiles/k_*_turb320_f32.md),
+# scaled to the bench's launches by their units. Only kernels unchanged since
+# their capture are listed.
+PROFILED_TRAFFIC = {"k_rcheck": 584.953344e6 / 320 ** 3}
+
+
 def kernel_bytes(name, st, n, es):
     """Algorithmic DRAM bytes of a kernel's working launches (element size es,
     3D field of n vertices) from its work units, or None for the sparse
@@ -525,12 +539,17 @@ def main():
             row["frac"] = row["achieved_gbs"] / peak_gbs
         kernels.append(row)
     roofline = None
-    hbm_rows = [k for k in kernels if "achieved_gbs" in k]
+    hbm_rows = [k for k in kernels if "achieved_gbs" in k and k["name"] in HBM_BOUND]
     if hbm_rows:
         top = max(hbm_rows, key=lambda k: k["work_ms"])
         avg_ms = top["work_ms"] / top["work_launches"]
+        per_unit = PROFILED_TRAFFIC.get(top["name"])
+        traffic = per_unit * top["units"] / top["work_launches"] if per_unit else None
+        longest = max(kernels, key=lambda k: k["work_ms"])
         roofline = {"bound": "hbm", "achieved": top["achieved_gbs"], "peak": peak_gbs, "unit": "GB/s",
-                    "frac": top["frac"], "traffic": None, "kernel": top["name"],
+                    "frac": top["frac"], "traffic": traffic, "kernel": top["name"],
+                    "note": ("the HBM-bound kernel with the most working time; the longest kernel, "
+                             f"{longest['name']}, is not bound by HBM bandwidth") if longest is not top else None,
                     "avg_launch_ms": avg_ms, "bytes_per_launch": top["algorithmic_bytes"] / top["work_launches"],
                     "work_launches": top["work_launches"], "peak_source": peak_src,
                     "share_of_kernel_time": top["ms"] / sum(k["ms"] for k in kernels)}
