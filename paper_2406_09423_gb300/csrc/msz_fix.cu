@@ -204,13 +204,13 @@ constexpr int kJumpsPerStep = 2;
 // A step holds two C-loop rounds (gather, mark, apply, reclassify): most
 // steps of a fix are C-loop rounds, and every launch of a stage that no field
 // is in still costs a few microseconds.
-constexpr int kStepSlots = 15 + kJumpsPerStep;  // launches per step
+constexpr int kStepSlots = 16 + kJumpsPerStep;  // launches per step
 constexpr int kStepEvents = kStepSlots + 1;
 static_assert(kStepSlots <= 32, "the step log holds one bit per launch slot");
 // kernel of each launch slot of a step
-constexpr int kSlotKernel[kStepSlots] = {KID_SWEEP,  KID_GATHER, KID_CSMALL, KID_MARK,   KID_APPLY,  KID_RECLASS,
-                                         KID_GATHER, KID_MARK,   KID_LABEL,  KID_ECOUNT, KID_ESCAN,  KID_EFILL,
-                                         KID_JUMP,   KID_JUMP,   KID_RCHECK, KID_APPLY,  KID_RECLASS};
+constexpr int kSlotKernel[kStepSlots] = {KID_SWEEP,  KID_GATHER, KID_CSMALL, KID_MARK,  KID_APPLY,  KID_RECLASS,
+                                         KID_GATHER, KID_MARK,   KID_LABEL,  KID_LABEL, KID_ECOUNT, KID_ESCAN,
+                                         KID_EFILL,  KID_JUMP,   KID_JUMP,   KID_RCHECK, KID_APPLY, KID_RECLASS};
 static_assert(kJumpsPerStep == 2, "slot table assumes two jump launches per step");
 static_assert(NKID == MSZ_NUM_KERNELS, "kernel table and ABI disagree");
 const char* const kKernelNames[NKID] = {"k_csweep", "k_gather", "k_mark",   "k_label_tile",
@@ -233,7 +233,8 @@ struct Group {
   bool tma = false;
   int grid[NKIND] = {};
   bool small_ok = false;  // a k_csmall cluster fits on the device
-  size_t label_smem = 0;
+  size_t label_smem[2] = {0, 0};  // f's pass, g's passes
+  int grid_label[2] = {0, 0};
 
   // Host arrays for nf fields (null pointers while measuring).
   void host_carve(HostArena& h) {
@@ -354,11 +355,15 @@ struct Group {
     grid[K_CASE] = occ_grid((const void*)k_gather<T, ND>, kThreads, 0, args.total[K_CASE]);
     grid[K_SWEEP] = tma ? occ_grid((const void*)k_csweep<T, ND, true>, SG::NTP, 0, args.total[K_SWEEP])
                         : occ_grid((const void*)k_csweep<T, ND, false>, SG::NT, 0, args.total[K_SWEEP]);
-    label_smem = label_smem_bytes<T, ND>();
-    if (cudaFuncSetAttribute(k_label_tile<T, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)label_smem) !=
-        cudaSuccess)
+    label_smem[0] = label_smem_bytes<T, ND, false>();
+    label_smem[1] = label_smem_bytes<T, ND, true>();
+    if (cudaFuncSetAttribute(k_label_tile<T, ND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)label_smem[0]) != cudaSuccess ||
+        cudaFuncSetAttribute(k_label_tile<T, ND, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)label_smem[1]) != cudaSuccess)
       return MSZ_ERR_CUDA;
-    grid[K_LABEL] = occ_grid((const void*)k_label_tile<T, ND>, kThreads, label_smem, args.total[K_LABEL]);
+    grid_label[0] = occ_grid((const void*)k_label_tile<T, ND, false>, kThreads, label_smem[0], args.total[K_LABEL]);
+    grid_label[1] = occ_grid((const void*)k_label_tile<T, ND, true>, kThreads, label_smem[1], args.total[K_LABEL]);
     if (cudaGetLastError() != cudaSuccess) return MSZ_ERR_CUDA;
     {
       cudaLaunchConfig_t cfg = {};
@@ -395,8 +400,9 @@ struct Group {
     return MSZ_OK;
   }
 
-  // csweep, (gather, csmall, mark, apply, reclass), gather, mark, label_tile,
-  // ecount, escan, efill, jump x kJumpsPerStep, rcheck, apply, reclass
+  // csweep, (gather, csmall, mark, apply, reclass), gather, mark, label_tile
+  // (f's, g's), ecount, escan, efill, jump x kJumpsPerStep, rcheck, apply,
+  // reclass
   int launches_per_step() const { return empty() ? 0 : kStepSlots; }
 
   void init(cudaStream_t s) {
@@ -448,7 +454,8 @@ struct Group {
   }
   template <class A>
   void labels(cudaStream_t s, A&& a) {
-    k_label_tile<T, ND><<<grid[K_LABEL], kThreads, label_smem, s>>>(a());
+    k_label_tile<T, ND, false><<<grid_label[0], kThreads, label_smem[0], s>>>(a());
+    k_label_tile<T, ND, true><<<grid_label[1], kThreads, label_smem[1], s>>>(a());
     k_ecount<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
     k_escan<T><<<nf, 1024, 0, s>>>(a());
     k_efill<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());

@@ -578,10 +578,12 @@ __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
 // vertex outside the tile on its integral line, or to the extremum it reaches
 // inside. Job 0: f (fdir, Mf, mf). Job 1: g (gdir, Pup, Pdn).
 // ---------------------------------------------------------------------------
-template <class T, int ND>
+// Dynamic shared memory of k_label_tile: f's pass holds the halo values and
+// the pointers, g's passes the pointers only.
+template <class T, int ND, bool JOB>
 size_t label_smem_bytes() {
   using LG = LabelGeom<ND>;
-  return ((LG::HALO * sizeof(T) + 15) / 16) * 16 + (size_t)LG::HALO * sizeof(uint32_t);
+  return (JOB ? 0 : ((LG::HALO * sizeof(T) + 15) / 16) * 16) + (size_t)LG::HALO * sizeof(uint32_t);
 }
 
 // A tile's values with a one-cell halo: every in-grid cell by an
@@ -651,22 +653,26 @@ __device__ __forceinline__ bool leaves_tile(int s, uint32_t bhi, uint32_t blo) {
   return (m & (neg ? blo : bhi)) != 0u;
 }
 
-template <class T, int ND>
-__global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
+// JOB: the fields in f's pass (false) or in g's (true); the two are launched
+// side by side, each doing nothing for the other's fields.
+template <class T, int ND, bool JOB>
+__global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<T> A) {
   using LG = LabelGeom<ND>;
   extern __shared__ __align__(16) unsigned char lsm[];
   T* val = reinterpret_cast<T*>(lsm);
   // Pointers in halo coordinates: halo cells and extrema point to themselves
   // (terminal); interior cells to their steepest neighbour.
   // ascending pointer (low 16 bits) and descending pointer (high 16 bits)
-  uint32_t* PP = reinterpret_cast<uint32_t*>(lsm + ((LG::HALO * sizeof(T) + 15) / 16) * 16);
+  uint32_t* PP = reinterpret_cast<uint32_t*>(lsm + (JOB ? 0 : ((LG::HALO * sizeof(T) + 15) / 16) * 16));
   const int* pre = A.prefix + K_LABEL * (A.nf + 1);
   constexpr int HS = LG::SX, HSS = LG::SX * LG::SY;
   // halo-cell exit bits (ascending, descending); padded for the two-word reads
   constexpr int kExWords = (LG::HALO + 31) / 32 + 2;
   constexpr int kSegs = (LG::SX + 31) / 32;
   __shared__ uint32_t exs[2][kExWords];
-  auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_INIT; };
+  auto active = [](const Field<T>& F) {
+    return F.st->action == ACT_LABELS && F.st->lstate == L_INIT && (F.st->ljob != 0) == JOB;
+  };
   auto none = [](DevState*) {};
   auto done = [&](DevState* st) {
     st->lstate = L_COUNT;
@@ -678,7 +684,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_label_tile(GroupArgs<T> A) {
     tl.enter(A, K_LABEL, fi, none, done);
     const Field<T>& F = A.fields[fi];
     DevState* st = F.st;
-    const bool job = st->ljob != 0;
+    constexpr bool job = JOB;
     int32_t* OA = job ? F.Pup : F.Mf;
     int32_t* OB = job ? F.Pdn : F.mf;
     const Geom G = F.G;

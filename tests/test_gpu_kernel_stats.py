@@ -40,7 +40,7 @@ def test_kernel_stats_consistent(shape):
                         "k_jump", "k_rcheck", "k_apply", "k_reclass", "k_csmall"]
     steps = st["k_csweep"]["launches"]
     assert steps > 0
-    per_step = {"k_jump": 2, "k_gather": 2, "k_mark": 2, "k_apply": 2, "k_reclass": 2}
+    per_step = {"k_jump": 2, "k_gather": 2, "k_mark": 2, "k_apply": 2, "k_reclass": 2, "k_label_tile": 2}
     for name, s in st.items():
         assert s["launches"] == per_step.get(name, 1) * steps
         assert 0 <= s["work_launches"] <= s["launches"]
