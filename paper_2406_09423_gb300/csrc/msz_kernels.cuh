@@ -486,6 +486,10 @@ __global__ void __launch_bounds__(kThreads) k_mark(GroupArgs<T> A) {
   tl.flush(A, K_SPARSE, none, done);
 }
 
+template <class T, int ND>
+__device__ __forceinline__ uint32_t reclass_vertex(const Field<T>& F, int v, int x, int y, int z, uint32_t (&acc)[4],
+                                                   int& vc);
+
 // One reclassification item: ring slot s of touched vertex u (slot 2 * NPOS:
 // u itself). The first item to reach a vertex in the round claims it (epoch
 // stamp) and recomputes its false-type bits and its direction byte in g; the
@@ -510,6 +514,14 @@ __device__ __forceinline__ uint32_t reclass_item(const Field<T>& F, int u, int s
     v = u + dx + dy * G.nx + dz * G.nxny;
   }
   if (atomicExch(&F.epoch[v], stamp) == stamp) return 0;
+  return reclass_vertex<T, ND>(F, v, x, y, z, acc, vc);
+}
+
+// Reclassification of vertex v at (x, y, z), the part after the claim.
+template <class T, int ND>
+__device__ __forceinline__ uint32_t reclass_vertex(const Field<T>& F, int v, int x, int y, int z, uint32_t (&acc)[4],
+                                                   int& vc) {
+  const Geom& G = F.G;
   const uint8_t dv = direction_of<T, ND>(F.g, G, v, x, y, z);
   F.gdir[v] = dv;  // g's direction bytes stay exact for the requests and the labels
   const unsigned nb = case_bits(dv, F.fdir[v]);
@@ -554,16 +566,27 @@ __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
   MSZ_ACTIVE_UNITS(A, K_SPARSE, pre, i, active) {
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
+    // more ring items than vertices: every vertex once, in order, unclaimed
+    const bool dense = (uint64_t)st->ntouch * R > (uint64_t)F.G.n;
     uint64_t b, e;
-    const uint32_t act = sparse_slice((uint64_t)st->ntouch * R, F.units[K_SPARSE], u_ - pre[i], b, e);
+    const uint32_t act =
+        sparse_slice(dense ? (uint64_t)F.G.n : (uint64_t)st->ntouch * R, F.units[K_SPARSE], u_ - pre[i], b, e);
     if ((uint32_t)(u_ - pre[i]) >= act) continue;  // left out: not counted
     tl.enter(A, K_SPARSE, i, pre_flush, done);
     tl.target = act;
     const uint32_t stamp = (uint32_t)st->rounds;
     if (threadIdx.x == 0) log_units(A, st, KID_RECLASS, e - b);
     int vc;
-    for (uint64_t j = b + threadIdx.x; j < e; j += blockDim.x)
-      reclass_item<T, ND>(F, (int)F.touched[j / R], (int)(j % R), stamp, acc, vc);
+    if (dense) {
+      for (uint64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
+        int x, y, z;
+        coords(F.G, (int)j, x, y, z);
+        reclass_vertex<T, ND>(F, (int)j, x, y, z, acc, vc);
+      }
+    } else {
+      for (uint64_t j = b + threadIdx.x; j < e; j += blockDim.x)
+        reclass_item<T, ND>(F, (int)F.touched[j / R], (int)(j % R), stamp, acc, vc);
+    }
   }
   tl.flush(A, K_SPARSE, pre_flush, done);
 }
