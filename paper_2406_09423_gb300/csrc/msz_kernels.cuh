@@ -486,9 +486,9 @@ __global__ void __launch_bounds__(kThreads) k_mark(GroupArgs<T> A) {
   tl.flush(A, K_SPARSE, none, done);
 }
 
-template <class T, int ND>
-__device__ __forceinline__ uint32_t reclass_vertex(const Field<T>& F, int v, int x, int y, int z, uint32_t (&acc)[4],
-                                                   int& vc);
+template <class T>
+__device__ __forceinline__ uint32_t reclass_update(const Field<T>& F, int v, uint8_t dv, uint8_t fd, unsigned ob,
+                                                   uint32_t (&acc)[4], int& vc);
 
 // One reclassification item: ring slot s of touched vertex u (slot 2 * NPOS:
 // u itself). The first item to reach a vertex in the round claims it (epoch
@@ -513,19 +513,30 @@ __device__ __forceinline__ uint32_t reclass_item(const Field<T>& F, int u, int s
     if (x < 0 || x >= G.nx || y < 0 || y >= G.ny || z < 0 || z >= G.nz) return 0;
     v = u + dx + dy * G.nx + dz * G.nxny;
   }
-  if (atomicExch(&F.epoch[v], stamp) == stamp) return 0;
-  return reclass_vertex<T, ND>(F, v, x, y, z, acc, vc);
+  // The class inputs load while the claim is in flight (g does not change
+  // during a reclassification); only the claimer uses them.
+  const uint32_t prev = atomicExch(&F.epoch[v], stamp);
+  const uint8_t dv = direction_of<T, ND>(F.g, G, v, x, y, z);
+  const uint8_t fd = F.fdir[v];
+  const unsigned ob = F.cls[v];
+  if (prev == stamp) return 0;
+  return reclass_update(F, v, dv, fd, ob, acc, vc);
 }
 
-// Reclassification of vertex v at (x, y, z), the part after the claim.
+// The same for vertex v at (x, y, z) without a claim (a pass over every vertex).
 template <class T, int ND>
 __device__ __forceinline__ uint32_t reclass_vertex(const Field<T>& F, int v, int x, int y, int z, uint32_t (&acc)[4],
                                                    int& vc) {
-  const Geom& G = F.G;
-  const uint8_t dv = direction_of<T, ND>(F.g, G, v, x, y, z);
+  return reclass_update(F, v, direction_of<T, ND>(F.g, F.G, v, x, y, z), F.fdir[v], F.cls[v], acc, vc);
+}
+
+// Vertex v's new direction byte dv in g, f's direction byte fd and its old
+// false-type bits ob: the byte and the bits are stored, the counts move.
+template <class T>
+__device__ __forceinline__ uint32_t reclass_update(const Field<T>& F, int v, uint8_t dv, uint8_t fd, unsigned ob,
+                                                   uint32_t (&acc)[4], int& vc) {
   F.gdir[v] = dv;  // g's direction bytes stay exact for the requests and the labels
-  const unsigned nb = case_bits(dv, F.fdir[v]);
-  const unsigned ob = F.cls[v];
+  const unsigned nb = case_bits(dv, fd);
   if (nb == ob) return 0;
   F.cls[v] = (uint8_t)nb;
 #pragma unroll
