@@ -376,6 +376,7 @@ struct Group {
       cfg.attrs = &at;
       cfg.numAttrs = 1;
       int ncl = 0;
+      if (kSmallCluster > 8) cudaFuncSetAttribute(k_csmall<T, ND>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       small_ok = cudaOccupancyMaxActiveClusters(&ncl, k_csmall<T, ND>, &cfg) == cudaSuccess && ncl > 0;
       cudaGetLastError();  // a device without clusters of this size runs every round on the grid kernels
     }

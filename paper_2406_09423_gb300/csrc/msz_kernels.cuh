@@ -1332,7 +1332,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
 // counters live in the shared memory of its block 0.
 // ---------------------------------------------------------------------------
 constexpr int kSmallThreads = 1024;
-constexpr int kSmallCluster = 8;  // blocks per field
+constexpr int kSmallCluster = 16;  // blocks per field (a non-portable cluster size)
 constexpr uint32_t kSmallSpan = (uint32_t)kSmallThreads * kSmallCluster;
 constexpr int kSmallPer = 4;  // cases per thread
 constexpr uint32_t kSmallCases = kSmallSpan * kSmallPer;
