@@ -408,6 +408,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-metrics", action="store_true", help="skip the Appendix B metrics per bound")
     ap.add_argument("--arrivals", type=int, default=32, help="served form: number of Poisson arrivals")
     ap.add_argument("--profile-fix", type=float, default=None, metavar="REL",
                     help="run one fix of the --size workload at xi = REL * range and exit (for ncu captures)")
@@ -562,6 +563,28 @@ def main():
         cpu = {"value": v, "unit": "Mvertices/s", "cores": 1, "kind": "oracle", "sample": desc,
                "seconds": s, "host_cores": multiprocessing.cpu_count()}
 
+    # Appendix B metrics of each bound (outside the timed region): right
+    # labelled ratio and PSNR of f-hat before and of the edited field after
+    # the correction, the edit ratio, and the time of one metrics call.
+    quality = {}
+    if rank == 0 and not args.no_metrics:
+        for rel, xi, fh in cases:
+            before = msz.field_metrics(f, fh)
+            r = plan.fix(f, fh, xi)
+            g = fh.clone()
+            msz.apply(g, r.edit_idx, r.edit_val)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            after = msz.field_metrics(f, g)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            quality[str(rel)] = {"right_labelled_before": before["right_labelled"],
+                                 "right_labelled_after": after["right_labelled"],
+                                 "psnr_before": before["psnr"], "psnr_after": after["psnr"],
+                                 "edit_ratio": r.n_edits / n, "metrics_call_ms": e0.elapsed_time(e1)}
+            del g
+
     batched = served = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = run_batched(torch, msz, dev)
@@ -573,8 +596,10 @@ def main():
         d = per_xi.setdefault(str(rel), {"ms": [], "sweeps": c["sweeps"], "label_evals": c["label_evals"],
                                          "edits": ne, "freezes": c["freezes"]})
         d["ms"].append(ms)
-    for d in per_xi.values():
+    for rel_s, d in per_xi.items():
         d["mvps"] = n / (statistics.median(d["ms"]) / 1e3) / 1e6
+        if rel_s in quality:
+            d["quality"] = quality[rel_s]
     step_rates = sorted(n / (ms / 1e3) / 1e6 for ms in step_ms)
     p50 = statistics.median(step_ms)
     p99 = sorted(step_ms)[max(0, int(round(0.99 * len(step_ms))) - 1)]

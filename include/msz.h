@@ -121,7 +121,7 @@ int msz_plan_destroy(msz_plan p);
  * recomputed), bitmap words (k_ecount), exits (k_efill), exit-table
  * accesses (k_jump), fields (k_escan), cases (k_gather, k_mark),
  * touched vertices (k_apply), ring items (k_reclass), C-loop rounds run
- * whole in one block per field (k_csmall: requests, apply and
+ * whole in one thread-block cluster per field (k_csmall: requests, apply and
  * reclassification of rounds with few cases). */
 #define MSZ_NUM_KERNELS 12
 typedef struct {
@@ -217,6 +217,32 @@ int msz_apply(void* decomp_dev, int ndim, const int64_t dims[3], int dtype,
  * itself (a maximum, resp. minimum). */
 int msz_directions(const void* field_dev, int ndim, const int64_t dims[3], int dtype,
                    uint8_t* dir_dev, void* stream);
+
+/* Evaluation metrics of a field g against the original f (the paper's
+ * Appendix B: PSNR and the right labelled ratio; no counterpart in the
+ * correction loop). f_dev and g_dev are device arrays of one shape and dtype,
+ * x fastest. In double precision:
+ *   mse            = (1/N) sum_i (f_i - g_i)^2
+ *   value_range    = max_i f_i - min_i f_i          (the peak signal value)
+ *   psnr           = 20 log10(value_range / sqrt(mse)), +inf when mse = 0
+ *   wrong          = vertices whose maximum or minimum label (Sec. 3) under g
+ *                    differs from the one under f
+ *   right_labelled = 1 - wrong / N
+ * The labels come from dense pointer doubling over the field, independent of
+ * the correction loop's labelling. Allocates 16 bytes per vertex of stream-
+ * ordered scratch for the call and returns once the results are in *out.
+ * Returns MSZ_OK, MSZ_ERR_ARG (shape, NULL pointer), MSZ_ERR_DTYPE,
+ * MSZ_ERR_OOM, MSZ_ERR_TIMEOUT (no fixed point within 64 rounds: cannot
+ * happen for finite fields) or MSZ_ERR_CUDA. */
+typedef struct {
+  double mse;
+  double value_range;
+  double psnr;
+  double right_labelled;
+  uint64_t wrong;
+} msz_metric_values;
+int msz_field_metrics(const void* f_dev, const void* g_dev, int ndim, const int64_t dims[3], int dtype,
+                      void* stream, msz_metric_values* out);
 
 /* msz_fix without any device allocation. The paper has no counterpart: this
  * entry point serves callers that cannot call cudaMalloc (a framework whose

@@ -11,6 +11,8 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
   * directions / labels / false_bits: brute force on tiny grids, hand grids,
     closed forms (monotone ramps, single bumps).
   * bounds / decrease: exact rational arithmetic.
+  * metrics: identical fields, exact shifts and single-vertex changes (closed
+    forms), wrong-label counts against brute-force walks on tiny grids.
   * fix: invariants (bound, extremum sets, labels), special cases, hand
     worked rounds, the paper's Fig. 5 event chain. The particular edit values
     follow this restatement's readings and are otherwise "parity unpinned".
@@ -127,6 +129,31 @@ def labels(shape, direction: np.ndarray) -> np.ndarray:
     lab = np.empty(direction.size, dtype=np.int32)
     assert lib.oracle_labels(ndim, _ptr(d), _ptr(direction), _ptr(lab)) == 0
     return lab
+
+
+def metrics(f: np.ndarray, g: np.ndarray) -> dict:
+    """Evaluation metrics of g against f (Appendix B), the plain definitions:
+    mse = (1/N) sum (f_i - g_i)^2, the sum of the float64 squares rounded once
+    (math.fsum); value_range = max f - min f; psnr = 20 log10(value_range /
+    sqrt(mse)) (+inf for mse = 0); wrong = vertices whose maximum or minimum
+    label (the fixed point of the steepest-neighbour walk, Sec. 3) differs
+    between g and f; right_labelled = 1 - wrong / N."""
+    import math
+
+    f = np.ascontiguousarray(f)
+    g = np.ascontiguousarray(g)
+    assert f.shape == g.shape and f.dtype == g.dtype
+    n = f.size
+    f64 = f.astype(np.float64).ravel()
+    d = f64 - g.astype(np.float64).ravel()
+    mse = math.fsum((d * d).tolist()) / n
+    rng = float(f64.max() - f64.min())
+    psnr = math.inf if mse == 0.0 else 20.0 * math.log10(rng / math.sqrt(mse))
+    uf, df = directions(f)
+    ug, dg = directions(g)
+    wrong = int(np.count_nonzero((labels(f.shape, uf) != labels(g.shape, ug)) |
+                                 (labels(f.shape, df) != labels(g.shape, dg))))
+    return {"mse": mse, "value_range": rng, "psnr": psnr, "wrong": wrong, "right_labelled": 1.0 - wrong / n}
 
 
 def false_bits(f: np.ndarray, g: np.ndarray) -> np.ndarray:

@@ -16,7 +16,7 @@ from dataclasses import dataclass
 
 from . import native
 
-__all__ = ["Plan", "Batch", "Server", "FixResult", "fix", "apply", "directions", "native"]
+__all__ = ["Plan", "Batch", "Server", "FixResult", "fix", "apply", "directions", "field_metrics", "native"]
 
 
 def _torch():
@@ -226,6 +226,21 @@ def apply(decomp, edit_idx, edit_val) -> None:
     st = native.msz_apply(decomp.data_ptr(), tuple(decomp.shape), decomp.dtype, idx.data_ptr(),
                           val.data_ptr(), int(idx.numel()), torch.cuda.current_stream().cuda_stream)
     native.check(st, "msz_apply")
+
+
+def field_metrics(f, g) -> dict:
+    """Appendix B metrics of g against f (CUDA tensors of one shape and
+    dtype): mse, value_range, psnr, wrong (vertices with a wrong maximum or
+    minimum label) and right_labelled (msz_field_metrics)."""
+    torch = _torch()
+    if f.shape != g.shape or f.dtype != g.dtype:
+        raise ValueError("f and g must have one shape and dtype")
+    f, g = f.contiguous(), g.contiguous()
+    st, m = native.msz_field_metrics(f.data_ptr(), g.data_ptr(), tuple(f.shape), f.dtype,
+                                     torch.cuda.current_stream().cuda_stream)
+    native.check(st, "msz_field_metrics")
+    return {"mse": m.mse, "value_range": m.value_range, "psnr": m.psnr, "wrong": int(m.wrong),
+            "right_labelled": m.right_labelled}
 
 
 def directions(field):

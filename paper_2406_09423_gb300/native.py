@@ -89,6 +89,16 @@ class MszKernelStat(ctypes.Structure):
     ]
 
 
+class MszMetricValues(ctypes.Structure):
+    _fields_ = [
+        ("mse", ctypes.c_double),
+        ("value_range", ctypes.c_double),
+        ("psnr", ctypes.c_double),
+        ("right_labelled", ctypes.c_double),
+        ("wrong", ctypes.c_uint64),
+    ]
+
+
 _lib = None
 
 
@@ -116,6 +126,8 @@ def lib() -> ctypes.CDLL:
         L.msz_apply.restype = I
         L.msz_directions.argtypes = [P, I, P, I, P, P]
         L.msz_directions.restype = I
+        L.msz_field_metrics.argtypes = [P, P, I, P, I, P, ctypes.POINTER(MszMetricValues)]
+        L.msz_field_metrics.restype = I
         L.msz_batch_bytes.argtypes = [I, P, P, P]
         L.msz_batch_bytes.restype = I64
         L.msz_batch_create.argtypes = [ctypes.POINTER(P), I, P, P, P, P]
@@ -316,6 +328,15 @@ def msz_directions(field_ptr: int, shape, dtype, dir_ptr: int, stream: int = 0) 
     ndim, d = dims_of(shape)
     return lib().msz_directions(ctypes.c_void_p(field_ptr), ndim, d, dtype_code(dtype),
                                 ctypes.c_void_p(dir_ptr), ctypes.c_void_p(stream))
+
+
+def msz_field_metrics(f_ptr: int, g_ptr: int, shape, dtype, stream: int = 0):
+    """(status, MszMetricValues) of g against f (device pointers)."""
+    ndim, d = dims_of(shape)
+    out = MszMetricValues()
+    st = lib().msz_field_metrics(ctypes.c_void_p(f_ptr), ctypes.c_void_p(g_ptr), ndim, d, dtype_code(dtype),
+                                 ctypes.c_void_p(stream), ctypes.byref(out))
+    return st, out
 
 
 def msz_strerror(status: int) -> str:
