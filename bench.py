@@ -252,6 +252,40 @@ def profile_fix(args):
     return 0
 
 
+def edit_coding(torch, msz, stream, f, fh, xi, r):
+    """Sec. 5.3 coding of one fix's edit list: sizes, device encode / decode
+    times, and the overall compression ratio with the quantiser's codes at
+    their empirical entropy standing in for the lossy compressor's output
+    (zlib on the host standing in for the final GZIP / ZSTD stage)."""
+    import math
+    import zlib
+
+    enc = msz.encode_edits(r.edit_idx, r.edit_val, fh)  # warm
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    enc = msz.encode_edits(r.edit_idx, r.edit_val, fh)
+    ev[1].record(stream)
+    i2, v2 = msz.decode_edits(enc, fh)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    ok = bool(torch.equal(i2.long(), r.edit_idx.long()) and torch.equal(v2, r.edit_val))
+    blob = bytes(enc.cpu().numpy())
+    zl = len(zlib.compress(blob, 6))
+    ne = int(r.edit_idx.numel())
+    q = torch.round(fh.double() / (2.0 * xi)).long().flatten()
+    _, counts = torch.unique(q, return_counts=True)
+    p = counts.double() / q.numel()
+    data_bytes = float(-(p * torch.log2(p)).sum().item()) * q.numel() / 8.0
+    orig = f.numel() * f.element_size()
+    return {"edits_raw_bytes": ne * (4 + f.element_size()), "edits_coded_bytes": len(blob),
+            "edits_zlib_bytes": zl, "bits_per_edit": 8.0 * zl / max(ne, 1),
+            "encode_ms": ev[0].elapsed_time(ev[1]), "decode_ms": ev[1].elapsed_time(ev[2]),
+            "round_trip_exact": ok,
+            "cr_quantiser_entropy": orig / data_bytes if data_bytes > 0 else math.inf,
+            "ocr": orig / (data_bytes + zl)}
+
+
 def run_batched(torch, msz, dev, count=64):
     """Batched form: 64 fields of uneven sizes (2D sides 64..1024, 3D sides
     32..192; float32 for even i, float64 for odd i; xi log-uniform in
@@ -583,6 +617,7 @@ def main():
                                  "right_labelled_after": after["right_labelled"],
                                  "psnr_before": before["psnr"], "psnr_after": after["psnr"],
                                  "edit_ratio": r.n_edits / n, "metrics_call_ms": e0.elapsed_time(e1)}
+            quality[str(rel)].update(edit_coding(torch, msz, stream, f, fh, xi, r))
             del g
 
     batched = served = None

@@ -244,6 +244,49 @@ typedef struct {
 int msz_field_metrics(const void* f_dev, const void* g_dev, int ndim, const int64_t dims[3], int dtype,
                       void* stream, msz_metric_values* out);
 
+/* Lossless coding of an edit list (Sec. 5.3: the ascending indices as
+ * differences with run-length and Huffman coding; the values coded
+ * separately). Encoding and decoding run on the device. Format
+ * (little-endian bytes):
+ *   header, 14 u32 words: magic 0x45535A4D ('MSZE'), version 1, dtype,
+ *     bytes per value, n_edits (u64), index tokens, index chunks, value
+ *     chunks, 0, index payload bits (u64), value payload bits (u64);
+ *   256 code lengths of the index symbols, 256 of the value symbols (u8,
+ *     0 = unused, at most 15);
+ *   per index chunk: bit offset (u64), first edit (u32), index before it
+ *     (u32, 0xffffffff for none); per value chunk: bit offset (u64);
+ *   the index payload, then the value payload, in u32 words, bits most
+ *     significant first.
+ * Index symbols, per edit k with delta d = idx[k] - idx[k-1] (idx[-1] = -1),
+ * within aligned groups of 32 edits: a maximal run of L >= 2 deltas equal to
+ * 1 in the group is symbol 252 followed by 5 raw bits (L - 2); otherwise
+ * symbol d - 1 (d <= 252), symbol 253 + 16 raw bits (d - 253, d <= 65788) or
+ * symbol 254 + 32 raw bits (d). Value symbols: the bytes of bits(value) XOR
+ * bits(fhat[idx]), little-endian, per edit. Each stream has a canonical
+ * code (symbols ordered by (length, symbol)) with lengths from package-merge
+ * (optimal among codes of at most 15 bits; leaves sorted by (count, symbol),
+ * a leaf before a package of equal weight). A chunk starts at every 4096th
+ * symbol of a stream.
+ *
+ * msz_edits_encoded_bound: bytes that suffice for any list of n_edits.
+ * msz_encode_edits: edit_idx_dev strictly ascending and below the field's N,
+ *   edit_val_dev the new values, fhat_dev the field they replace (device);
+ *   writes at most out_cap bytes to out_dev and their count to *out_bytes.
+ *   MSZ_ERR_ARG for unsorted or out-of-field indices or too small a buffer.
+ * msz_decode_edits: the inverse, given the same fhat; writes *n_edits
+ *   indices and values (at most cap_edits). MSZ_ERR_ARG for a stream that is
+ *   malformed, of another type or field size, or longer than cap_edits; the
+ *   decoder bounds every index it writes or reads.
+ * Both return when the results are in place (they allocate stream-ordered
+ * scratch: about 36 bytes per edit plus 13 per value byte to encode). */
+int64_t msz_edits_encoded_bound(uint64_t n_edits, int dtype);
+int msz_encode_edits(const uint32_t* edit_idx_dev, const void* edit_val_dev, uint64_t n_edits, const void* fhat_dev,
+                     int ndim, const int64_t dims[3], int dtype, void* out_dev, uint64_t out_cap,
+                     uint64_t* out_bytes, void* stream);
+int msz_decode_edits(const void* in_dev, uint64_t in_bytes, const void* fhat_dev, int ndim, const int64_t dims[3],
+                     int dtype, uint32_t* edit_idx_dev, void* edit_val_dev, uint64_t cap_edits, uint64_t* n_edits,
+                     void* stream);
+
 /* msz_fix without any device allocation. The paper has no counterpart: this
  * entry point serves callers that cannot call cudaMalloc (a framework whose
  * allocator must not grow, a real-time loop where an allocation may block or

@@ -16,7 +16,7 @@ from dataclasses import dataclass
 
 from . import native
 
-__all__ = ["Plan", "Batch", "Server", "FixResult", "fix", "apply", "directions", "field_metrics", "native"]
+__all__ = ["Plan", "Batch", "Server", "FixResult", "fix", "apply", "directions", "field_metrics", "encode_edits", "decode_edits", "native"]
 
 
 def _torch():
@@ -241,6 +241,38 @@ def field_metrics(f, g) -> dict:
     native.check(st, "msz_field_metrics")
     return {"mse": m.mse, "value_range": m.value_range, "psnr": m.psnr, "wrong": int(m.wrong),
             "right_labelled": m.right_labelled}
+
+
+def encode_edits(edit_idx, edit_val, fhat):
+    """Lossless coding of an edit list (Sec. 5.3; msz_encode_edits): a uint8
+    CUDA tensor holding the encoded bytes. edit_idx ascending, edit_val the
+    new values, fhat the field they replace (CUDA tensors)."""
+    torch = _torch()
+    idx = edit_idx.to(device=fhat.device, dtype=torch.int32).contiguous()
+    val = edit_val.to(device=fhat.device, dtype=fhat.dtype).contiguous()
+    fh = fhat.contiguous()
+    n = int(idx.numel())
+    cap = native.msz_edits_encoded_bound(n, fh.dtype)
+    native.check(cap if cap < 0 else 0, "msz_edits_encoded_bound")
+    out = torch.empty(cap, dtype=torch.uint8, device=fh.device)
+    st, nb = native.msz_encode_edits(idx.data_ptr(), val.data_ptr(), n, fh.data_ptr(), tuple(fh.shape), fh.dtype,
+                                     out.data_ptr(), cap, torch.cuda.current_stream().cuda_stream)
+    native.check(st, "msz_encode_edits")
+    return out[:nb]
+
+
+def decode_edits(data, fhat, cap_edits=None):
+    """(edit_idx int32, edit_val) of an encoded edit list (msz_decode_edits)."""
+    torch = _torch()
+    data = data.to(device=fhat.device, dtype=torch.uint8).contiguous()
+    fh = fhat.contiguous()
+    cap = fh.numel() if cap_edits is None else int(cap_edits)
+    idx = torch.empty(cap, dtype=torch.int32, device=fh.device)
+    val = torch.empty(cap, dtype=fh.dtype, device=fh.device)
+    st, n = native.msz_decode_edits(data.data_ptr(), int(data.numel()), fh.data_ptr(), tuple(fh.shape), fh.dtype,
+                                    idx.data_ptr(), val.data_ptr(), cap, torch.cuda.current_stream().cuda_stream)
+    native.check(st, "msz_decode_edits")
+    return idx[:n], val[:n]
 
 
 def directions(field):

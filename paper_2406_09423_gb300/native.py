@@ -128,6 +128,12 @@ def lib() -> ctypes.CDLL:
         L.msz_directions.restype = I
         L.msz_field_metrics.argtypes = [P, P, I, P, I, P, ctypes.POINTER(MszMetricValues)]
         L.msz_field_metrics.restype = I
+        L.msz_edits_encoded_bound.argtypes = [U64, I]
+        L.msz_edits_encoded_bound.restype = I64
+        L.msz_encode_edits.argtypes = [P, P, U64, P, I, P, I, P, U64, ctypes.POINTER(U64), P]
+        L.msz_encode_edits.restype = I
+        L.msz_decode_edits.argtypes = [P, U64, P, I, P, I, P, P, U64, ctypes.POINTER(U64), P]
+        L.msz_decode_edits.restype = I
         L.msz_batch_bytes.argtypes = [I, P, P, P]
         L.msz_batch_bytes.restype = I64
         L.msz_batch_create.argtypes = [ctypes.POINTER(P), I, P, P, P, P]
@@ -337,6 +343,32 @@ def msz_field_metrics(f_ptr: int, g_ptr: int, shape, dtype, stream: int = 0):
     st = lib().msz_field_metrics(ctypes.c_void_p(f_ptr), ctypes.c_void_p(g_ptr), ndim, d, dtype_code(dtype),
                                  ctypes.c_void_p(stream), ctypes.byref(out))
     return st, out
+
+
+def msz_edits_encoded_bound(n_edits: int, dtype) -> int:
+    return lib().msz_edits_encoded_bound(int(n_edits), dtype_code(dtype))
+
+
+def msz_encode_edits(idx_ptr: int, val_ptr: int, n_edits: int, fhat_ptr: int, shape, dtype, out_ptr: int,
+                     out_cap: int, stream: int = 0):
+    """(status, encoded bytes)."""
+    ndim, d = dims_of(shape)
+    nb = ctypes.c_uint64(0)
+    st = lib().msz_encode_edits(ctypes.c_void_p(idx_ptr), ctypes.c_void_p(val_ptr), int(n_edits),
+                                ctypes.c_void_p(fhat_ptr), ndim, d, dtype_code(dtype), ctypes.c_void_p(out_ptr),
+                                int(out_cap), ctypes.byref(nb), ctypes.c_void_p(stream))
+    return st, int(nb.value)
+
+
+def msz_decode_edits(in_ptr: int, in_bytes: int, fhat_ptr: int, shape, dtype, idx_ptr: int, val_ptr: int,
+                     cap_edits: int, stream: int = 0):
+    """(status, number of edits)."""
+    ndim, d = dims_of(shape)
+    n = ctypes.c_uint64(0)
+    st = lib().msz_decode_edits(ctypes.c_void_p(in_ptr), int(in_bytes), ctypes.c_void_p(fhat_ptr), ndim, d,
+                                dtype_code(dtype), ctypes.c_void_p(idx_ptr), ctypes.c_void_p(val_ptr),
+                                int(cap_edits), ctypes.byref(n), ctypes.c_void_p(stream))
+    return st, int(n.value)
 
 
 def msz_strerror(status: int) -> str:
