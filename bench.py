@@ -38,6 +38,20 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
+def job_rate(pg, total_ms, steps, n, world, device=None):
+    """Whole-job throughput of `world` replicas, each fixing `steps` fields
+    of n vertices in total_ms on its own device: the slowest rank's time
+    (all_reduce MAX over the process group, None for one rank) bounds the
+    job. Returns (max total_ms, Mvertices/s of all ranks together)."""
+    if pg is not None:
+        import torch
+
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * steps * n / (total_ms / 1e3) / 1e6
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -506,11 +520,7 @@ def main():
     clocks = sampler.stop()
     total_ms = ev[0].elapsed_time(ev[-1])
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    if pg is not None:
-        t = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * n / (total_ms / 1e3) / 1e6
+    total_ms, value = job_rate(pg, total_ms, args.steps, n, world, dev)
 
     # End to end through the host-buffer entry point (msz_fix_host): every step
     # copies f and fhat from pinned host memory and the edit list back.
