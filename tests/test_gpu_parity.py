@@ -2,6 +2,10 @@
 directions, edited values, edit lists, labels and counters (the method's
 floating-point tolerance is 0 ulp), on seeded inputs with several tiles and
 ragged tails, degenerate shapes and the error paths."""
+import glob
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -117,6 +121,26 @@ def test_fix_matches_oracle(name, make, rel):
     fhat = synth.quantise(f, xi)
     res, ref = _compare(msz, f, fhat, xi)
     check_result(f, fhat, xi, ref.g, ref.edit_idx, ref.edit_val, ref.label_max, ref.label_min)
+
+
+GOLDEN = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "*.json")))
+
+
+@pytest.mark.parametrize("path", GOLDEN, ids=[os.path.basename(p) for p in GOLDEN])
+def test_golden_hand_worked(path):
+    # the hand-worked cases of Sec. 4 (one per false type and per R-loop
+    # direction): the same edits, values and counters on the device
+    msz = _msz()
+    case = json.load(open(path))
+    dt = np.dtype(case["dtype"])
+    shape = tuple(case["shape"])
+    f = np.array(case["f"], dtype=dt).reshape(shape)
+    fhat = np.array(case["fhat"], dtype=dt).reshape(shape)
+    res, ref = _compare(msz, f, fhat, case["xi"])
+    assert res.edit_idx.cpu().tolist() == case["edit_idx"]
+    assert np.array_equal(bits_of(ref.g.reshape(-1)), bits_of(np.array(case["g"], dtype=dt)))
+    for k, v in case["counts"].items():
+        assert res.counts[k] == v, k
 
 
 @pytest.mark.parametrize("name,make,rel", [c for c in CASES if c[0] in ("bumps128", "bumps-f64", "turb-48", "ocean-crop", "turb-f64")],
