@@ -87,6 +87,34 @@ def test_signed_zero_compares_equal():
     assert list(dn) == [0, 0, 1]
 
 
+def test_hand_worked_3x3_plateau():
+    # g (rows are y, x fastest):  1 1 0 / 1 2 1 / 0 1 1.  The centre is the
+    # only maximum. Vertex 0 lies on a plateau of 1s with its neighbours 1
+    # and 3; the index breaks the tie, so vertex 0 is a minimum, and vertex 8
+    # descends to 5, the lowest-indexed of its equal neighbours 5 and 7.
+    g = np.array([[1, 1, 0], [1, 2, 1], [0, 1, 1]], dtype=np.float32)
+    up, dn = oracle.directions(g)
+    assert list(up) == [4, 4, 5, 4, 4, 4, 7, 4, 4]
+    assert list(dn) == [0, 2, 2, 6, 0, 2, 6, 6, 5]
+    assert list(oracle.labels(g.shape, up)) == [4] * 9
+    assert list(oracle.labels(g.shape, dn)) == [0, 2, 2, 6, 0, 2, 6, 6, 2]
+
+
+def test_hand_worked_2x2x2_cube():
+    # Freudenthal cube: 0 and 7 touch every vertex, the others four each.
+    # Vertex 5 (value 6) is a maximum beside the global maximum 3 (value 7)
+    # because 3 and 5 differ by (0, -1, 1) and share no edge.
+    g = np.array([3, 5, 1, 7, 2, 6, 0, 4], dtype=np.float64).reshape(2, 2, 2)
+    assert [sorted(oracle.neighbours(g.shape, v)) for v in range(8)] == [
+        [1, 2, 3, 4, 5, 6, 7], [0, 3, 5, 7], [0, 3, 6, 7], [0, 1, 2, 7],
+        [0, 5, 6, 7], [0, 1, 4, 7], [0, 2, 4, 7], [0, 1, 2, 3, 4, 5, 6]]
+    up, dn = oracle.directions(g)
+    assert list(up) == [3, 3, 3, 3, 5, 5, 7, 3]
+    assert list(dn) == [6, 0, 6, 2, 6, 4, 6, 6]
+    assert list(oracle.labels(g.shape, up)) == [3, 3, 3, 3, 5, 5, 3, 3]
+    assert list(oracle.labels(g.shape, dn)) == [6] * 8
+
+
 @pytest.mark.parametrize("shape", SHAPES_2D + SHAPES_3D + [(8, 9), (4, 5, 6)])
 @pytest.mark.parametrize("ties", [False, True])
 def test_labels_match_walks(shape, ties):
