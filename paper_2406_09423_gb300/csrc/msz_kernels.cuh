@@ -1014,7 +1014,7 @@ __global__ void __launch_bounds__(1024) k_escan(GroupArgs<T> A) {
 // handled in batches of kBatch so that their loads are in flight together.
 constexpr int kBatch = 8;
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_efill(GroupArgs<T> A) {
+__global__ void __launch_bounds__(kThreads, 6) k_efill(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
   auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_FILL; };
   auto none = [](DevState*) {};
@@ -1035,11 +1035,19 @@ __global__ void __launch_bounds__(kThreads) k_efill(GroupArgs<T> A) {
     const int w = u * kThreads + threadIdx.x;
     uint32_t nex = 0;
     if (w < nw) {
+      uint32_t m2[2], r2[2];  // both directions' words, loaded before any table store
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        m2[d] = F.ex[d][w];
+        r2[d] = F.ub[d][u] + F.ep[d][w];
+      }
 #pragma unroll
       for (int d = 0; d < 2; ++d) {
         const int32_t* Tt = d ? (job ? F.Pdn : F.mf) : (job ? F.Pup : F.Mf);
-        uint32_t r = F.ub[d][u] + F.ep[d][w];
-        uint32_t m = F.ex[d][w];
+        const uint32_t *ex = F.ex[d], *ep = F.ep[d], *ub = F.ub[d];
+        uint32_t* lc = F.lc[d];
+        uint32_t r = r2[d];
+        uint32_t m = m2[d];
         F.xr[d][w] = make_uint2(m, r);  // for label resolution after the jumping
         nex += __popc(m);
         while (m) {
@@ -1056,11 +1064,15 @@ __global__ void __launch_bounds__(kThreads) k_efill(GroupArgs<T> A) {
           }
 #pragma unroll
           for (int j = 0; j < kBatch; ++j) t[j] = (e[j] >= 0) ? (uint32_t)Tt[e[j]] : kExt;
+          // every entry of the batch before any store: a store to the table
+          // may alias the bitmap and prefix words as far as the compiler
+          // knows, so interleaving them would run the rank loads one by one
 #pragma unroll
           for (int j = 0; j < kBatch; ++j)
-            if (j < c)
-              F.lc[d][r + j] =
-                  (t[j] & kExt) ? ((t[j] & ~kExt) | kRes) : exit_rank(F.ex[d], F.ep[d], F.ub[d], (int)t[j]);
+            t[j] = (t[j] & kExt) ? ((t[j] & ~kExt) | kRes) : exit_rank(ex, ep, ub, (int)t[j]);
+#pragma unroll
+          for (int j = 0; j < kBatch; ++j)
+            if (j < c) lc[r + j] = t[j];
           r += c;
         }
       }
