@@ -1205,15 +1205,38 @@ __global__ void __launch_bounds__(kThreads, 6) k_rcheck(GroupArgs<T> A) {
       if (q < kRFreeze) s_fz[q] = (uint32_t)a;
       else request<T, ND>(F, a, t, ts);  // list full: the same freeze, vertex by vertex
     };
+    // kRB vertices per thread and iteration, their loads issued together
+    constexpr int kRB = 4;
     if (st->ljob == 0) {
-      for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-        F.Mf[v] = resolve_label(F, 0, F.Mf, v);
-        F.mf[v] = resolve_label(F, 1, F.mf, v);
+      // every label of the batch before any store, which the compiler could
+      // not move the next loads past
+      int32_t* Mf = F.Mf;
+      int32_t* mf = F.mf;
+      for (int vb = v0 + threadIdx.x; vb < v1; vb += kRB * kThreads) {
+        uint32_t tu[kRB], td[kRB];
+#pragma unroll
+        for (int k = 0; k < kRB; ++k) {
+          const int v = vb + k * kThreads;
+          const bool in = v < v1;
+          tu[k] = in ? (uint32_t)Mf[v] : kExt;
+          td[k] = in ? (uint32_t)mf[v] : kExt;
+        }
+#pragma unroll
+        for (int k = 0; k < kRB; ++k) {
+          tu[k] = (tu[k] & kExt) ? (tu[k] & ~kExt) : (F.lc[0][exit_rank2(F.xr[0], (int)tu[k])] & ~kRes);
+          td[k] = (td[k] & kExt) ? (td[k] & ~kExt) : (F.lc[1][exit_rank2(F.xr[1], (int)td[k])] & ~kRes);
+        }
+#pragma unroll
+        for (int k = 0; k < kRB; ++k) {
+          const int v = vb + k * kThreads;
+          if (v < v1) {
+            Mf[v] = (int32_t)tu[k];
+            mf[v] = (int32_t)td[k];
+          }
+        }
       }
       continue;
     }
-    // kRB vertices per thread and iteration, their loads issued together
-    constexpr int kRB = 4;
     for (int vb = v0 + threadIdx.x; vb < v1; vb += kRB * kThreads) {
       uint32_t tu[kRB], td[kRB];
       int32_t M[kRB], m[kRB];
