@@ -12,7 +12,7 @@ import pytest
 import oracle
 from paper_2406_09423_gb300 import synth
 from tests import bruteforce as bf
-from tests.invariants import check_result
+from tests.invariants import bits_of, check_result, within_bound
 
 GOLDEN = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "*.json")))
 
@@ -132,6 +132,50 @@ def test_lower_bound_collision_forces_freezes():
     assert r.status == 0
     assert r.counts["freezes"] > 0
     check_result(f, fhat, xi, r.g, r.edit_idx, r.edit_val)
+
+
+def _rounds_case(name):
+    if name == "bumps":
+        f = synth.bumps2d(24, 20, 3)
+        xi = synth.xi_for(f, 1e-2)
+        return f, synth.quantise(f, xi), xi
+    if name == "turb3d":
+        f = synth.turbulence3d(12, 2, kmax=3.0, shape=(9, 10, 12))
+        xi = synth.xi_for(f, 3e-2)
+        return f, synth.quantise(f, xi), xi
+    rng = np.random.default_rng(5)  # constant decompression: freezes
+    f = rng.uniform(0, 1, (7, 8)).astype(np.float32)
+    return f, np.full(f.shape, 0.5, dtype=np.float32), 1.0
+
+
+@pytest.mark.parametrize("name", ["bumps", "turb3d", "constant"])
+def test_every_round_lowers_or_freezes(name):
+    # The convergence argument with the freeze guard (Sec. 4.3): after every
+    # round g stays within the bound (Eq. 1), each vertex's value only
+    # decreases or is reset to f once and then never changes, and a round
+    # changes every vertex it decreases plus at most the ones it freezes.
+    # g after k rounds is the result of a run capped at k rounds.
+    f, fhat, xi = _rounds_case(name)
+    full = oracle.fix(f, fhat, xi, max_rounds=5000, trace_cap=100000)  # these cases need < 100
+    assert full.status == 0
+    trace = full.trace
+    assert len(trace) > 1
+    prev = fhat.reshape(-1)
+    reset = np.zeros(prev.size, dtype=bool)
+    fb = bits_of(f)
+    for k in range(1, len(trace) + 1):
+        gk = oracle.fix(f, fhat, xi, max_rounds=k - 1).g.reshape(-1)
+        assert within_bound(f.reshape(-1), gk, xi)
+        changed = bits_of(gk) != bits_of(prev)
+        up = gk > prev
+        assert not (changed & reset).any(), "a reset vertex changed again"
+        assert ((gk < prev) | (bits_of(gk) == fb))[changed].all(), "a value rose above its previous one"
+        assert (bits_of(gk) == fb)[up].all(), "a rise that is not a reset to f"
+        _, _, _, nd, nf = trace[k - 1]
+        assert nd <= changed.sum() <= nd + nf
+        reset |= up
+        prev = gk
+    assert np.array_equal(bits_of(prev), bits_of(full.g))
 
 
 def test_troublemakers_are_first_discrepancies():
