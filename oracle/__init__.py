@@ -13,9 +13,12 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
   * bounds / decrease: exact rational arithmetic.
   * metrics: identical fields, exact shifts and single-vertex changes (closed
     forms), wrong-label counts against brute-force walks on tiny grids.
-  * fix: invariants (bound, extremum sets, labels), special cases, hand
-    worked rounds, the paper's Fig. 5 event chain. The particular edit values
-    follow this restatement's readings and are otherwise "parity unpinned".
+  * fix: invariants (bound, extremum sets, labels), special cases, six hand
+    worked cases with their exact edits, counters and round trace (each of
+    the targets of Eqs. (2)-(5) and both of Eq. (6), the paper's Fig. 5
+    event chain), and the convergence argument of Sec. 4.3 checked round by
+    round. Beyond those cases the particular edit values follow this
+    restatement's readings and are otherwise "parity unpinned".
 """
 from __future__ import annotations
 

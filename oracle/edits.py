@@ -24,6 +24,12 @@ values are coded separately. This restatement fixes the unstated details:
   and 256 value code lengths (bytes); per index chunk (bit offset u64, first
   edit u32, index before it u32, 0xffffffff for none); per value chunk (bit
   offset u64); the index payload, then the value payload, in words.
+
+Pins (tests/test_oracle_edits.py): tokenisations worked by hand (runs,
+group boundaries, both escapes); package-merge lengths complete (Kraft
+equality) and at the Huffman cost when the limit does not bind, within 15
+bits when it does; canonical codes by hand and prefix-free; exact round
+trips; payload bits equal to the code lengths plus raw bits.
 """
 from __future__ import annotations
 
