@@ -178,6 +178,49 @@ def test_every_round_lowers_or_freezes(name):
     assert np.array_equal(bits_of(prev), bits_of(full.g))
 
 
+def test_fig5_event_chain():
+    # Sec. 4.2, Fig. 5: f_i > f_j > f_k with g_j > g_i > g_k at first. The
+    # FNmax at i is fixed by lowering j; i then descends through j in g but
+    # through k in f, a troublemaker fixed by lowering k; k becomes an FPmin,
+    # fixed (Eq. 3, the neighbour maximal in g) by lowering i, which brings
+    # back an FNmax at i. Rebuilt on a 5x3 grid (x fastest, xi = 8, so
+    # lb = f - 8): i = 7 at the centre, j = 6 to its left, k = 8 to its
+    # right; f has maxima {0, 7} and minima {5, 9}. Every value worked by hand.
+    f = np.array([[12, 9, 8, 6, 3], [1, 7, 10, 4, 0], [2, 5, 9, 6, 2]], dtype=np.float64)
+    fhat = f.copy()
+    fhat.flat[[6, 7, 8, 9, 12]] = [9.5, 9, 5, 1, 8]
+    xi, i, j, k = 8.0, 7, 6, 8
+    assert f.flat[i] > f.flat[j] > f.flat[k] and fhat.flat[j] > fhat.flat[i] > fhat.flat[k]
+    up_f, dn_f = oracle.directions(f)
+    assert dn_f[i] == k
+    g = [fhat.reshape(-1)] + [oracle.fix(f, fhat, xi, max_rounds=q).g.reshape(-1) for q in range(3)]
+
+    def edits(q):
+        return {int(v): float(g[q + 1][v]) for v in np.flatnonzero(g[q + 1] != g[q])}
+
+    # round 1 (C): the FNmax at i is the only false case; j: 9.5 -> (9.5 + -1) / 2
+    b0 = oracle.false_bits(f, fhat)
+    assert {int(v): int(b0[v]) for v in np.flatnonzero(b0)} == {i: 4}
+    assert edits(0) == {j: 4.25}
+    # round 2 (R): no false case; i is the only troublemaker, a descending
+    # one (g: 7 -> 6 -> 5, f: 7 -> 8 -> 9); k: 5 -> (5 + -4) / 2
+    assert not oracle.false_bits(f, g[1].reshape(f.shape)).any()
+    t1 = oracle.troublemakers(f, g[1].reshape(f.shape))
+    assert {int(v): int(t1[v]) for v in np.flatnonzero(t1)} == {i: 2}
+    assert edits(1) == {k: 0.5}
+    # round 3 (C): k is an FPmin (and its neighbour 9 an FNmin); the FPmin
+    # sub-loop lowers i, k's highest neighbour: 9 -> (9 + 2) / 2
+    b2 = oracle.false_bits(f, g[2].reshape(f.shape))
+    assert {int(v): int(b2[v]) for v in np.flatnonzero(b2)} == {k: 2, 9: 8}
+    assert edits(2) == {i: 5.5}
+    # then i is an FNmax again (its neighbour 1 holds 9)
+    assert oracle.false_bits(f, g[3].reshape(f.shape))[i] & 4
+    full = oracle.fix(f, fhat, xi, max_rounds=5000, trace_cap=1000)
+    assert full.status == 0
+    assert [tuple(int(x) for x in t[:3]) for t in full.trace[:3]] == [(0, 2, 1), (1, 0, 1), (0, 1, 1)]
+    check_result(f, fhat, xi, full.g, full.edit_idx, full.edit_val, full.label_max, full.label_min)
+
+
 def test_troublemakers_are_first_discrepancies():
     # With equal extremum sets, the troublemaker set must equal the set of
     # first vertices, along each wrongly labelled vertex's integral line in f,
