@@ -103,7 +103,8 @@ typedef struct msz_plan_s* msz_plan;
 
 /* Allocates the device state for fields of one shape and type (Sec. 4 state:
  * g, directions, labels of f and g, per-vertex flags, case and edit lists).
- * opt may be NULL. Returns MSZ_ERR_OOM if device memory is insufficient. */
+ * opt may be NULL. Returns MSZ_ERR_OOM if device memory is insufficient and
+ * MSZ_ERR_CUDA if no CUDA device can be used. */
 int msz_plan_create(msz_plan* out, int ndim, const int64_t dims[3], int dtype,
                     const msz_options* opt);
 

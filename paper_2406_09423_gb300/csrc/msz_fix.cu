@@ -653,7 +653,11 @@ int create_engine(msz_engine_s** out, int nf, const int* ndim, const int64_t* di
   if (rc != MSZ_OK) return rc;
   msz_engine_s* E = new (std::nothrow) msz_engine_s();
   if (!E) return MSZ_ERR_OOM;
-  cudaGetDevice(&E->device);
+  if (cudaGetDevice(&E->device) != cudaSuccess) {  // no device or driver: not a memory shortage
+    cudaGetLastError();
+    delete E;
+    return MSZ_ERR_CUDA;
+  }
   if (opt) E->opt = *opt;
   HostArena measure{nullptr, 0, 0};
   host_engine(E, nf, ndim, dims, dtype, measure);

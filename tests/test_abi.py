@@ -55,3 +55,20 @@ def test_plan_bytes_and_argument_checks_without_gpu():
     assert L.msz_plan_bytes(4, d, 0) == -1
     d = (ctypes.c_int64 * 3)(1 << 16, 1 << 16, 1)
     assert L.msz_plan_bytes(2, d, 0) == -1  # 2^32 vertices: too many
+
+
+def test_no_device_is_an_error_not_a_fallback():
+    # without a CUDA device every entry point fails loudly; plan creation
+    # names the cause (a CUDA error, not a memory shortage)
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import paper_2406_09423_gb300 as msz
+
+    f = torch.zeros((8, 9))
+    with pytest.raises(RuntimeError, match="MSZ_ERR_CUDA"):
+        msz.Plan((8, 9), torch.float32)
+    with pytest.raises(RuntimeError):
+        msz.fix(f, f.clone(), 0.1)
+    with pytest.raises(RuntimeError):
+        msz.directions(f)
