@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
         unsigned char* sp = smem + (kTMA ? (qq & SM1) * SG::STAGE_BYTES : 0);
         const T* stage = reinterpret_cast<const T*>(sp);
         if (kTMA) {
-          // lane 0 waits for the stage; the warp follows its verdict
+          // lane 0 waits for the stage; the warp follows its decision
           bool got = true;
           if (lane == 0) got = mbar_wait_or_abort(&full[qq & SM1], (uint32_t)((qq / SG::STAGES) & 1), &s_abort);
           got = __shfl_sync(kFull, got, 0);
