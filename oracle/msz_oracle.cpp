@@ -28,7 +28,7 @@
 namespace {
 
 // ---------------------------------------------------------------------------
-// Grid and triangulation (Sec. 3: "a triangular/tetrahedral mesh").
+// Grid and triangulation (Sec. 3: a mesh of triangles or tetrahedra).
 // Reading: the Freudenthal/Kuhn triangulation of the regular grid. Vertex v
 // at (x, y, z) has linear index x + nx*(y + ny*z). Its neighbours are v + e
 // for every nonzero e in {0,1}^d and every -e, when inside the grid
@@ -346,8 +346,8 @@ struct Fixer {
       cnt.mismatch[1] += (uint64_t)wrong_min;
       if (wrong_max == 0 && wrong_min == 0) return ST_OK;
 
-      // Troublemaker (reading of "the first occurrence of discrepancy along
-      // the integral lines"): a wrongly labelled vertex t whose steepest
+      // Troublemaker (reading of the first place along an integral line
+      // where g and f disagree): a wrongly labelled vertex t whose steepest
       // neighbour in g differs from the one in f. Wrong maximum label: the
       // ascending neighbour in g, up_g[t], is decreased (Eq. 6). Wrong
       // minimum label: the descending neighbour of f, dn_f[t], is decreased

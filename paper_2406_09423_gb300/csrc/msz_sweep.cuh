@@ -1,6 +1,6 @@
 // C-loop sweep: extremum classification of every vertex of g and detection
 // of the four false critical point types (Sec. 4.1 Definitions 1-3; the
-// "find false critical points" and "update directions" steps of Sec. 5.1).
+// false-critical-point and direction-update steps of Sec. 5.1).
 //
 // GB300 design. A vertex v is the greatest of its closed Freudenthal ring iff
 //   g_v > max(U*(v))  and  g_v >= max(L*(v)),
