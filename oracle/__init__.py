@@ -42,6 +42,10 @@ COUNT_FIELDS = (
     "c_cases_fpmax", "c_cases_fpmin", "c_cases_fnmax", "c_cases_fnmin",
     "c_passes", "r_rounds", "r_cases_asc", "r_cases_desc", "label_evals",
     "mismatch_max", "mismatch_min", "dec_edits", "freezes", "edits",
+    "freeze_req_fpmax", "freeze_req_fpmin", "freeze_req_fnmax", "freeze_req_fnmin",
+    "freeze_req_rmax", "freeze_req_rmin",
+    "freeze_req_frozen_fpmax", "freeze_req_frozen_fpmin", "freeze_req_frozen_fnmax",
+    "freeze_req_frozen_fnmin", "freeze_req_frozen_rmax", "freeze_req_frozen_rmin",
 )
 
 STATUS = {0: "ok", -1: "arg", -2: "dtype", -3: "nonfinite", -4: "bound", -6: "noconverge"}

@@ -196,6 +196,13 @@ struct Counts {
   uint64_t dec_edits;      // decreasing edits applied
   uint64_t freezes;        // vertices frozen by the termination guard
   uint64_t edits;          // length of the final edit list
+  // Requests that froze their anchor's ring instead of decreasing their
+  // target, by the case that made them: C-loop FPmax, FPmin, FNmax, FNmin,
+  // R-loop wrong max label, wrong min label. freeze_req counts them all,
+  // freeze_req_frozen those whose target was already frozen (the others
+  // found the target at its lower bound).
+  uint64_t freeze_req[6];
+  uint64_t freeze_req_frozen[6];
 };
 
 enum { ST_OK = 0, ST_ARG = -1, ST_DTYPE = -2, ST_NONFINITE = -3, ST_BOUND = -4,
@@ -246,12 +253,15 @@ struct Fixer {
   // Termination guard (reading; the paper argues convergence in the reals,
   // Sec. 4.3): if t is frozen or already at its lower bound, every non-frozen
   // vertex of a's closed 1-ring is frozen instead, i.e. reset to f and never
-  // edited again.
-  void request(int64_t a, int64_t t) {
+  // edited again. kind: the case that asks (0-3 the C-loop types, 4 / 5 a
+  // troublemaker of a wrong max / min label), for the freeze counters.
+  void request(int64_t a, int64_t t, int kind) {
     if (!frozen[t] && g[t] > lb[t]) {
       mark[t] |= DEC;
       return;
     }
+    ++cnt.freeze_req[kind];
+    if (frozen[t]) ++cnt.freeze_req_frozen[kind];
     int64_t nb[14];
     const int k = neighbours(G, a, nb);
     if (!frozen[a]) mark[a] |= FREEZE;
@@ -292,7 +302,7 @@ struct Fixer {
         continue;
       ++k;
       const int64_t t = (type == FPMAX || type == FNMIN) ? i : up_g[i];
-      request(i, t);
+      request(i, t, type);
     }
     *ncase = k;
     return k;
@@ -356,8 +366,8 @@ struct Fixer {
       for (int64_t t = 0; t < n; ++t) {
         const unsigned tb = trouble_bits(t, Mg.data(), mg.data(), M.data(), m.data(),
                                          up_g.data(), dn_g.data(), up_f.data(), dn_f.data());
-        if (tb & 1u) { ++ta; request(t, up_g[t]); }
-        if (tb & 2u) { ++td; request(t, dn_f[t]); }
+        if (tb & 1u) { ++ta; request(t, up_g[t], 4); }
+        if (tb & 2u) { ++td; request(t, dn_f[t], 5); }
       }
       if (ta + td == 0) return ST_NOCONVERGE;  // cannot happen once extrema agree
       int64_t nd, nf;
