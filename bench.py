@@ -365,7 +365,7 @@ def run_served(torch, msz, dev, arrivals=32, rate=200.0, pool=2, budget_gb=60.0)
         key = (kind, seed)
         if key not in cache:
             if kind == "ocean":
-                f = torch.from_numpy(synth.ocean2d(3600, 2400, 1000 + seed)).to(dev)
+                f = synth.ocean2d(3600, 2400, 1000 + seed, device=dev)
             elif kind == "turb512":
                 f = synth.turbulence3d(512, 1000 + seed, device=dev)
             else:

@@ -31,7 +31,7 @@ def _fields():
     out.append(synth.bumps2d(77, 203, 5, dtype=np.float64))
     out.append(synth.lognormal3d(seed=1, shape=(20, 24, 33)))
     out.append(synth.turbulence3d(32, 8, kmax=4.0, dtype=np.float64, shape=(16, 32, 32)))
-    out.append(synth.ocean2d(3600, 2400, 2)[:160, :256].copy())
+    out.append(synth.ocean2d(3600, 2400, 2, window=(0, 160, 0, 256)))
     out.append(np.array([[1.5]], dtype=np.float32))
     out.append(synth.turbulence3d(48, 3, kmax=6.0))
     return out

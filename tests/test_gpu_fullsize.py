@@ -81,8 +81,8 @@ def _walk(a, dims, starts, up):
 CASES = [
     ("turbulence512-1e-3", lambda: synth.turbulence3d(512, 3, device="cuda"), 1e-3),
     ("turbulence512-1e-5", lambda: synth.turbulence3d(512, 3, device="cuda"), 1e-5),
-    ("ocean3600x2400-1e-3", lambda: torch.from_numpy(synth.ocean2d(3600, 2400, 2)).cuda(), 1e-3),
-    ("lognormal256-1e-4", lambda: torch.from_numpy(synth.lognormal3d(256, 1)).cuda(), 1e-4),
+    ("ocean3600x2400-1e-3", lambda: synth.ocean2d(3600, 2400, 2, device="cuda"), 1e-3),
+    ("lognormal256-1e-4", lambda: synth.lognormal3d(256, 1, device="cuda"), 1e-4),
 ]
 
 
