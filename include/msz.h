@@ -48,11 +48,13 @@ typedef enum {
   MSZ_ERR_NONFINITE = -3,  /* f or fhat holds a NaN or an infinity */
   MSZ_ERR_BOUND = -4,      /* fhat violates |fhat - f| <= xi at some vertex */
   MSZ_ERR_OOM = -5,        /* device or host allocation failed */
-  MSZ_ERR_NOCONVERGE = -6, /* round cap reached (msz_options.max_rounds) */
+  MSZ_ERR_NOCONVERGE = -6, /* round cap reached (msz_options.max_rounds); the result still
+                              holds the edit list of the field after its last round (no labels) */
   MSZ_ERR_TIMEOUT = -7,    /* a bounded device-side wait gave up */
   MSZ_ERR_CUDA = -8,       /* a CUDA runtime call failed */
   MSZ_ERR_BUSY = -9,       /* server: no free slot / request id unknown or not finished */
-  MSZ_ERR_TOO_LARGE = -10  /* msz_fix_noalloc: the field does not fit its static scratch */
+  MSZ_ERR_TOO_LARGE = -10, /* msz_fix_noalloc: the field does not fit its static scratch */
+  MSZ_ERR_CANCELLED = -11  /* server: the request was cancelled (msz_server_cancel) */
 } msz_status;
 
 /* Counters of one fix. The same quantities are computed by the reference
@@ -69,14 +71,25 @@ typedef struct {
   uint64_t dec_edits;    /* decreasing edits applied (Eqs. 2-6) */
   uint64_t freezes;      /* vertices reset to f by the termination guard */
   uint64_t edits;        /* length of the final edit list */
+  /* Requests that froze their anchor's closed ring instead of decreasing
+   * their target (the termination guard), by the case that made them:
+   * C-loop FPmax, FPmin, FNmax, FNmin, R-loop wrong max label, wrong min
+   * label. freeze_req counts them all, freeze_req_frozen those whose target
+   * was already frozen; the others found the target at its lower bound. */
+  uint64_t freeze_req[6];
+  uint64_t freeze_req_frozen[6];
 } msz_counts;
 
 /* msz_options.flags */
 #define MSZ_OPT_NO_TMA 1u        /* stage sweep planes with plain loads instead of TMA */
 #define MSZ_OPT_TIME_KERNELS 2u  /* fill msz_result.kernel_ms (CUDA events around each kernel kind) */
+#define MSZ_OPT_TEST_STALL 4u    /* test hook: fields start in a stage that no kernel serves, so no
+                                    state machine moves and the host's stall detection ends the
+                                    fix with MSZ_ERR_TIMEOUT (nothing waits or spins on the device) */
 
 typedef struct {
-  uint64_t max_rounds;   /* cap on C + R edit rounds; 0 = default (10^7) */
+  uint64_t max_rounds;   /* cap on C + R edit rounds; 0 = default (10^7). A fix that applies
+                            round max_rounds + 1 stops there with MSZ_ERR_NOCONVERGE */
   int32_t  label_tile;   /* reserved, 0 = automatic */
   uint32_t flags;        /* MSZ_OPT_* bits */
   int32_t  reserved[6];
@@ -200,6 +213,14 @@ int msz_server_submit(msz_server s, int ndim, const int64_t dims[3], int dtype, 
                       const void* decomp_dev, double xi, uint64_t* request_id);
 int msz_server_poll(msz_server s, uint64_t request_id, int wait_ms, msz_result* out);
 int msz_server_release(msz_server s, uint64_t request_id);
+/* Cancels a request (host side; no device wait is involved). A queued
+ * request is dropped at once; a running one leaves the running set at the
+ * next chunk boundary, when none of the server's kernels is in flight, and
+ * the other resident fields go on unchanged. Either way the request then
+ * finishes with status MSZ_ERR_CANCELLED (msz_server_poll) and is released
+ * as usual. MSZ_ERR_BUSY if it already finished, MSZ_ERR_ARG for an unknown
+ * id. */
+int msz_server_cancel(msz_server s, uint64_t request_id);
 int msz_server_destroy(msz_server s);
 
 /* Decompression side (Fig. 3 bottom; g_i = fhat_i + delta_i, Sec. 3):

@@ -63,7 +63,8 @@ def _result(torch, r, shape, dtype, copy):
     for s_ in shape:
         n *= int(s_)
     ok = r.status == 0
-    ne = int(r.n_edits) if ok else 0
+    # a fix stopped by the round cap still returns its edits so far
+    ne = int(r.n_edits) if (ok or r.status == -6) and r.edit_idx else 0
     idx = _view(torch, r.edit_idx, ne, torch.int32)
     val = _view(torch, r.edit_val, ne, dtype)
     lmax = _view(torch, r.label_max, n if ok else 0, torch.int32)
@@ -83,10 +84,10 @@ class Batch:
     together (msz_batch_create / msz_batch_fix); each result equals msz_fix
     on that field alone."""
 
-    def __init__(self, shapes, dtypes, max_rounds: int = 0, use_tma: bool = True):
+    def __init__(self, shapes, dtypes, max_rounds: int = 0, use_tma: bool = True, flags: int = 0):
         self.shapes = [tuple(int(v) for v in s_) for s_ in shapes]
         self.dtypes = list(dtypes)
-        flags = 0 if use_tma else native.MSZ_OPT_NO_TMA
+        flags |= 0 if use_tma else native.MSZ_OPT_NO_TMA
         self._b = native.msz_batch_create(self.shapes, self.dtypes, max_rounds, flags)
 
     def fix(self, fs, fhats, xis, copy: bool = True):
@@ -120,8 +121,9 @@ class Server:
     admitted as slots and memory allow and corrected together with the
     fields already resident; each result equals msz_fix on that field."""
 
-    def __init__(self, budget_bytes: int, max_slots: int = 64, max_rounds: int = 0, use_tma: bool = True):
-        flags = 0 if use_tma else native.MSZ_OPT_NO_TMA
+    def __init__(self, budget_bytes: int, max_slots: int = 64, max_rounds: int = 0, use_tma: bool = True,
+                 flags: int = 0):
+        flags |= 0 if use_tma else native.MSZ_OPT_NO_TMA
         self._s = native.msz_server_create(budget_bytes, max_slots, max_rounds, flags)
         self._inputs = {}
 
@@ -156,6 +158,11 @@ class Server:
         native.msz_server_release(self._s, rid)
         self._inputs.pop(rid, None)
 
+    def cancel(self, rid: int) -> int:
+        """msz_server_cancel: the request finishes with MSZ_ERR_CANCELLED (its
+        inputs stay referenced until it is polled or released)."""
+        return native.msz_server_cancel(self._s, rid)
+
     def close(self):
         if self._s:
             native.msz_server_destroy(self._s)
@@ -172,10 +179,11 @@ class Server:
 class Plan:
     """Device state for fields of one shape and dtype (msz_plan_create)."""
 
-    def __init__(self, shape, dtype, max_rounds: int = 0, use_tma: bool = True, time_kernels: bool = False):
+    def __init__(self, shape, dtype, max_rounds: int = 0, use_tma: bool = True, time_kernels: bool = False,
+                 flags: int = 0):
         self.shape = tuple(int(s) for s in shape)
         self.dtype = dtype
-        flags = (0 if use_tma else native.MSZ_OPT_NO_TMA) | (native.MSZ_OPT_TIME_KERNELS if time_kernels else 0)
+        flags |= (0 if use_tma else native.MSZ_OPT_NO_TMA) | (native.MSZ_OPT_TIME_KERNELS if time_kernels else 0)
         self._p = native.msz_plan_create(self.shape, dtype, max_rounds, flags)
 
     def fix(self, f, fhat, xi: float, copy: bool = True, check: bool = True) -> FixResult:

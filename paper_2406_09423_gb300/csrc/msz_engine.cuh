@@ -28,7 +28,9 @@
 
 namespace msz {
 
-enum : uint32_t { PH_INIT = 0, PH_FLABELS = 1, PH_C = 2, PH_R = 3, PH_DONE = 4, PH_ERR = 5 };
+enum : uint32_t { PH_INIT = 0, PH_FLABELS = 1, PH_C = 2, PH_R = 3, PH_DONE = 4, PH_ERR = 5, PH_PARKED = 6 };
+// PH_PARKED: no kernel serves this phase (MSZ_OPT_TEST_STALL, a test of the
+// host's stall detection): the field's state never moves.
 // Actions within a phase. In PH_C, ACT_NONE means the field's first (full)
 // classification sweep is pending; afterwards a C round runs ACT_GATHER
 // (list the cases of the current type), ACT_REQUEST (their requests),
@@ -464,10 +466,25 @@ __device__ __forceinline__ void mark(const Field<T>& F, int u, uint8_t bit, cons
   F.touched[list_slot(&F.st->ntouch)] = (uint32_t)u;
 }
 
-// Whether a request for target t decreases t (else its anchor's ring freezes).
+// What a request for target t does: RQ_DEC decreases t; otherwise its
+// anchor's ring freezes because t is frozen (RQ_FROZEN) or at its lower
+// bound (RQ_BOUND).
+enum : int { RQ_DEC = 0, RQ_FROZEN = 1, RQ_BOUND = 2 };
+template <class T>
+__device__ __forceinline__ int request_cause(const Field<T>& F, int t) {
+  if (F.flags[t] & FL_FROZEN) return RQ_FROZEN;
+  return F.g[t] > lower_bound_of(F.f[t], F.xi) ? RQ_DEC : RQ_BOUND;
+}
 template <class T>
 __device__ __forceinline__ bool request_decreases(const Field<T>& F, int t) {
-  return !(F.flags[t] & FL_FROZEN) && F.g[t] > lower_bound_of(F.f[t], F.xi);
+  return request_cause(F, t) == RQ_DEC;
+}
+
+// Counts a freezing request of case kind k (0-3 the C-loop types, 4 / 5 a
+// troublemaker of a wrong max / min label) with its cause.
+__device__ __forceinline__ void count_freeze_req(DevState* st, int k, int cause) {
+  atomicAdd((unsigned long long*)&st->cnt.freeze_req[k], 1ull);
+  if (cause == RQ_FROZEN) atomicAdd((unsigned long long*)&st->cnt.freeze_req_frozen[k], 1ull);
 }
 
 // A false case anchored at a asks for a decreasing edit of t. If t is frozen
@@ -522,17 +539,19 @@ __device__ __forceinline__ void freeze_ring_warp(const Field<T>& F, int a, int l
   if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE, ts);
 }
 
-// request() by a whole warp (lane = the thread's lane): lane 0 decides;
-// a freeze marks the closed 1-ring with one lane per vertex.
+// request() by a whole warp (lane = the thread's lane) for a case of kind
+// k: lane 0 decides; a freeze marks the closed 1-ring with one lane per
+// vertex.
 template <class T, int ND>
-__device__ __forceinline__ void request_warp(const Field<T>& F, int a, int t, int lane) {
-  int dec = 0;
-  if (lane == 0) dec = request_decreases(F, t);
-  dec = __shfl_sync(kFull, dec, 0);
-  if (dec) {
+__device__ __forceinline__ void request_warp(const Field<T>& F, int a, int t, int lane, int k) {
+  int cause = 0;
+  if (lane == 0) cause = request_cause(F, t);
+  cause = __shfl_sync(kFull, cause, 0);
+  if (cause == RQ_DEC) {
     if (lane == 0) mark(F, t, FL_DEC);
     return;
   }
+  if (lane == 0) count_freeze_req(F.st, k, cause);
   freeze_ring_warp<T, ND>(F, a, lane);
 }
 

@@ -204,8 +204,14 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
       int q = 0;
       Tile t;
       bool more = next_tile(t, blockIdx.x);
+      int fenced = -1;  // field whose maps this thread has acquired
       while (more && !*(volatile int*)&s_abort) {
         const CUtensorMap* gm = A.maps + 2 * t.i;
+        if (t.i != fenced) {
+          tensormap_acquire(gm);
+          tensormap_acquire(gm + 1);
+          fenced = t.i;
+        }
         for (int p = 0; p < t.ppt; ++p, ++q) {
           const int s = q & SM1;
           if (q >= SG::STAGES &&
@@ -480,7 +486,7 @@ __global__ void __launch_bounds__(kThreads) k_mark(GroupArgs<T> A) {
       const int v = (int)F.cases[j];
       const uint8_t d = F.gdir[v];  // exact: reclassified after every apply
       const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny);
-      request_warp<T, ND>(F, v, t, lane);
+      request_warp<T, ND>(F, v, t, lane, (int)type);
     }
   }
   tl.flush(A, K_SPARSE, none, done);
@@ -1177,6 +1183,9 @@ __global__ void __launch_bounds__(kThreads, 6) k_rcheck(GroupArgs<T> A) {
   constexpr uint32_t kRFreeze = 1024;
   __shared__ uint32_t s_fz[kRFreeze];
   __shared__ uint32_t s_nfz;
+  // freezing requests of the unit by kind (wrong max, wrong min) and cause
+  // (target frozen, target at its bound), added to the counters per unit
+  __shared__ uint32_t s_fzc[2][2];
   // The unit's touched vertices, staged here and added to the field's list
   // with one atomic per unit (a single counter for the whole grid otherwise).
   constexpr uint32_t kRStage = 2048;
@@ -1187,6 +1196,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_rcheck(GroupArgs<T> A) {
   ts.buf = s_tv;
   ts.cap = kRStage;
   if (threadIdx.x == 0) s_nfz = s_ntv = 0;
+  if (threadIdx.x < 4) s_fzc[threadIdx.x >> 1][threadIdx.x & 1] = 0;
   __syncthreads();
   UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
@@ -1195,12 +1205,15 @@ __global__ void __launch_bounds__(kThreads, 6) k_rcheck(GroupArgs<T> A) {
     DevState* st = F.st;
     const int v0 = (u_ - pre[i]) * kDenseChunk;
     const int v1 = min(F.G.n, v0 + kDenseChunk);
-    // the request of troublemaker a for target t (Eq. 6)
-    auto trouble = [&](int a, int t) {
-      if (request_decreases(F, t)) {
+    // the request of troublemaker a for target t (Eq. 6); k: 4 for a wrong
+    // max label, 5 for a wrong min label
+    auto trouble = [&](int a, int t, int k) {
+      const int cause = request_cause(F, t);
+      if (cause == RQ_DEC) {
         mark(F, t, FL_DEC, ts);
         return;
       }
+      atomicAdd(&s_fzc[k - 4][cause - 1], 1u);
       const uint32_t q = atomicAdd(&s_nfz, 1u);
       if (q < kRFreeze) s_fz[q] = (uint32_t)a;
       else request<T, ND>(F, a, t, ts);  // list full: the same freeze, vertex by vertex
@@ -1266,18 +1279,28 @@ __global__ void __launch_bounds__(kThreads, 6) k_rcheck(GroupArgs<T> A) {
           ++acc[0];
           if ((d & 15) != (fd & 15)) {
             ++acc[2];
-            trouble(v, v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny));
+            trouble(v, v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny), 4);
           }
         } else {
           ++acc[1];
           if ((d >> 4) != (fd >> 4)) {
             ++acc[3];
-            trouble(v, v + slot_offset(fd >> 4, ND, F.G.nx, F.G.nxny));
+            trouble(v, v + slot_offset(fd >> 4, ND, F.G.nx, F.G.nxny), 5);
           }
         }
       }
     }
     __syncthreads();
+    if (threadIdx.x < 4) {
+      // k: wrong max / min label; c: 0 target frozen, 1 target at its bound
+      const int k = threadIdx.x >> 1, c = threadIdx.x & 1;
+      const uint32_t n = s_fzc[k][c];
+      if (n) {
+        s_fzc[k][c] = 0;  // read by this thread alone
+        atomicAdd((unsigned long long*)&st->cnt.freeze_req[4 + k], (unsigned long long)n);
+        if (c == 0) atomicAdd((unsigned long long*)&st->cnt.freeze_req_frozen[4 + k], (unsigned long long)n);
+      }
+    }
     const uint32_t nfz = min(s_nfz, kRFreeze);
     if (nfz) {
       __syncthreads();  // every thread has read the count
@@ -1441,8 +1464,13 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
       if (cv[k] < 0) continue;
       const int v = cv[k];
       const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(F.gdir[v] & 15, ND, F.G.nx, F.G.nxny);
-      if (request_decreases(F, t)) mark(F, t, FL_DEC, ts);
-      else F.lc[0][atomicAdd(&C[1], 1u)] = (uint32_t)v;
+      const int cause = request_cause(F, t);
+      if (cause == RQ_DEC) {
+        mark(F, t, FL_DEC, ts);
+      } else {
+        count_freeze_req(st, (int)type, cause);
+        F.lc[0][atomicAdd(&C[1], 1u)] = (uint32_t)v;
+      }
     }
     cluster_barrier();
     if (const uint32_t nfz = C[1]) {
@@ -1525,6 +1553,12 @@ __device__ __forceinline__ bool bits_differ<double>(double a, double b) {
   return __double_as_longlong(a) != __double_as_longlong(b);
 }
 
+// Fields whose edit list is written: converged ones, and ones stopped by
+// the round cap (their edits so far).
+__device__ __forceinline__ bool emit_wanted(const DevState* st) {
+  return !st->emitted && (st->phase == PH_DONE || (st->phase == PH_ERR && st->status == MSZ_ERR_NOCONVERGE));
+}
+
 template <class T>
 __device__ __forceinline__ uint32_t emit_mask(const Field<T>& F, int base) {
   const uint4 wv = *reinterpret_cast<const uint4*>(F.flags + base);
@@ -1545,17 +1579,20 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_emit_count(GroupArgs<T> A) {
   const int* pre = A.prefix + K_EMIT * (A.nf + 1);
   __shared__ uint32_t s;
-  auto active = [](const Field<T>& F) { return F.st->phase == PH_DONE && !F.st->emitted; };
+  auto active = [](const Field<T>& F) { return emit_wanted(F.st); };
   MSZ_ACTIVE_UNITS(A, K_EMIT, pre, i, active) {
     const Field<T>& F = A.fields[i];
     const int tile = u_ - pre[i];
     const int base = tile * kEmitTile + threadIdx.x * kEmitItems;
     // final labels of g: the loop ends only after an R-check found every
     // vertex's g labels equal to f's, whose labels are resolved in Mf / mf
+    // (a field stopped by the round cap has no final labels)
     const int v1 = min(F.G.n, (tile + 1) * kEmitTile);
-    for (int v = tile * kEmitTile + threadIdx.x; v < v1; v += kThreads) {
-      F.Pup[v] = F.Mf[v];
-      F.Pdn[v] = F.mf[v];
+    if (F.st->phase == PH_DONE) {
+      for (int v = tile * kEmitTile + threadIdx.x; v < v1; v += kThreads) {
+        F.Pup[v] = F.Mf[v];
+        F.Pdn[v] = F.mf[v];
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) s = 0;
@@ -1573,7 +1610,7 @@ template <class T>
 __global__ void __launch_bounds__(1024) k_emit_scan(GroupArgs<T> A) {
   const Field<T>& F = A.fields[blockIdx.x];
   DevState* st = F.st;
-  if (st->phase != PH_DONE || st->emitted) return;
+  if (!emit_wanted(st)) return;
   const int ntiles = F.units[K_EMIT];
   __shared__ uint32_t warp_sums[32];
   __shared__ uint32_t carry_s;
@@ -1616,7 +1653,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_emit_write(GroupArgs<T> A) {
   const int* pre = A.prefix + K_EMIT * (A.nf + 1);
   __shared__ uint32_t ws[kThreads / 32];
-  auto active = [](const Field<T>& F) { return F.st->phase == PH_DONE && !F.st->emitted; };
+  auto active = [](const Field<T>& F) { return emit_wanted(F.st); };
   MSZ_ACTIVE_UNITS(A, K_EMIT, pre, fi, active) {
     const Field<T>& F = A.fields[fi];
     DevState* st = F.st;

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libmsz.so")
 MSZ_F32, MSZ_F64 = 0, 1
 MSZ_OPT_NO_TMA = 1
 MSZ_OPT_TIME_KERNELS = 2
+MSZ_OPT_TEST_STALL = 4
 # msz_result.kernel_ms: classification (full sweep + incremental), labels
 # (tile terminals + exit jumping), R-loop check, requests + apply
 KERNEL_KINDS = ("classify", "labels", "rcheck", "mark_apply")
@@ -24,7 +25,7 @@ MSZ_NUM_KERNELS = 12
 STATUS = {
     0: "MSZ_OK", -1: "MSZ_ERR_ARG", -2: "MSZ_ERR_DTYPE", -3: "MSZ_ERR_NONFINITE",
     -4: "MSZ_ERR_BOUND", -5: "MSZ_ERR_OOM", -6: "MSZ_ERR_NOCONVERGE", -7: "MSZ_ERR_TIMEOUT",
-    -8: "MSZ_ERR_CUDA", -9: "MSZ_ERR_BUSY", -10: "MSZ_ERR_TOO_LARGE",
+    -8: "MSZ_ERR_CUDA", -9: "MSZ_ERR_BUSY", -10: "MSZ_ERR_TOO_LARGE", -11: "MSZ_ERR_CANCELLED",
 }
 
 COUNT_FIELDS = (
@@ -33,6 +34,10 @@ COUNT_FIELDS = (
     "c_cases_fpmax", "c_cases_fpmin", "c_cases_fnmax", "c_cases_fnmin",
     "c_passes", "r_rounds", "r_cases_asc", "r_cases_desc", "label_evals",
     "mismatch_max", "mismatch_min", "dec_edits", "freezes", "edits",
+    "freeze_req_fpmax", "freeze_req_fpmin", "freeze_req_fnmax", "freeze_req_fnmin",
+    "freeze_req_rmax", "freeze_req_rmin",
+    "freeze_req_frozen_fpmax", "freeze_req_frozen_fpmin", "freeze_req_frozen_fnmax",
+    "freeze_req_frozen_fnmin", "freeze_req_frozen_rmax", "freeze_req_frozen_rmin",
 )
 
 
@@ -49,12 +54,14 @@ class MszCounts(ctypes.Structure):
         ("dec_edits", ctypes.c_uint64),
         ("freezes", ctypes.c_uint64),
         ("edits", ctypes.c_uint64),
+        ("freeze_req", ctypes.c_uint64 * 6),
+        ("freeze_req_frozen", ctypes.c_uint64 * 6),
     ]
 
     def as_dict(self) -> dict:
         flat = [self.sweeps, *self.c_rounds, *self.c_cases, self.c_passes, self.r_rounds,
                 *self.r_cases, self.label_evals, *self.mismatch, self.dec_edits, self.freezes,
-                self.edits]
+                self.edits, *self.freeze_req, *self.freeze_req_frozen]
         return {k: int(v) for k, v in zip(COUNT_FIELDS, flat)}
 
 
@@ -150,6 +157,8 @@ def lib() -> ctypes.CDLL:
         L.msz_server_poll.restype = I
         L.msz_server_release.argtypes = [P, U64]
         L.msz_server_release.restype = I
+        L.msz_server_cancel.argtypes = [P, U64]
+        L.msz_server_cancel.restype = I
         L.msz_server_destroy.argtypes = [P]
         L.msz_server_destroy.restype = I
         L.msz_fix_noalloc.argtypes = [I, P, I, P, P, D, P, P, P, P, P, ctypes.POINTER(MszResult)]
@@ -303,6 +312,10 @@ def msz_server_poll(srv, request_id: int, wait_ms: int = 0):
 
 def msz_server_release(srv, request_id: int) -> int:
     return lib().msz_server_release(srv, int(request_id))
+
+
+def msz_server_cancel(srv, request_id: int) -> int:
+    return lib().msz_server_cancel(srv, int(request_id))
 
 
 def msz_server_destroy(srv):
