@@ -782,9 +782,10 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
   });
   if (rc != MSZ_OK) return rc;
   DevState* H = E->h_states;
+  const bool parked = (E->opt.flags & MSZ_OPT_TEST_STALL) != 0;
   for (int i = 0; i < nf; ++i) {
     std::memset(&H[i], 0, sizeof(DevState));
-    H[i].phase = PH_INIT;
+    H[i].phase = parked ? PH_PARKED : PH_INIT;
     H[i].max_rounds = E->opt.max_rounds ? E->opt.max_rounds : 10000000ull;
   }
   if (cudaMemcpyAsync(E->d_states, H, sizeof(DevState) * nf, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -869,10 +870,12 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
     std::memset(&R, 0, sizeof(R));
     R.status = st;
     R.counts = H[i].cnt;
-    if (st == MSZ_OK) {
+    if (st == MSZ_OK || (st == MSZ_ERR_NOCONVERGE && H[i].emitted)) {
       R.edit_idx = E->bufs[i].edit_idx;
       R.edit_val = E->bufs[i].edit_val;
       R.n_edits = H[i].n_edits;
+    }
+    if (st == MSZ_OK) {
       R.label_max = E->bufs[i].Pup;
       R.label_min = E->bufs[i].Pdn;
     }
@@ -1101,6 +1104,7 @@ const char* msz_strerror(int status) {
     case MSZ_ERR_CUDA: return "CUDA runtime error";
     case MSZ_ERR_BUSY: return "no free slot or request not ready";
     case MSZ_ERR_TOO_LARGE: return "field too large for the static scratch of msz_fix_noalloc";
+    case MSZ_ERR_CANCELLED: return "request cancelled";
     default: return "unknown status";
   }
 }
@@ -1139,19 +1143,57 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kMaxDevices] = {};  // context the address belongs to
 
-// Device address of the scratch array on the current device (set up once).
+// Unique id of the current CUDA context (driver entry points, looked up
+// once), so that an address set up in a context that was since destroyed
+// (cudaDeviceReset) is not used in its successor. 0 if unavailable.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+unsigned long long current_ctx_id() {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult ra, rb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &ra) == cudaSuccess &&
+        ra == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &rb) == cudaSuccess &&
+        rb == cudaDriverEntryPointSuccess) {
+      get_cur = reinterpret_cast<CtxGetCurrentFn>(a);
+      get_id = reinterpret_cast<CtxGetIdFn>(b);
+    }
+    cudaGetLastError();
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur && get_id && get_cur(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS) return id;
+  return 0;
+}
+
+// Device address of the scratch array on the current device, set up once per
+// device and context.
 int noalloc_scratch(void** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MSZ_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return MSZ_ERR_CUDA;
+  }
+  // 0 while the runtime has not made a context current yet: then the set-up
+  // below runs (the symbol lookup initialises the context) and records it
+  const unsigned long long ctx = current_ctx_id();
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  if (!g_noalloc_ptr[dev] || ctx == 0 || g_noalloc_ctx[dev] != ctx) {
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
       cudaGetLastError();
+      g_noalloc_ptr[dev] = nullptr;
       return MSZ_ERR_CUDA;
     }
     g_noalloc_ptr[dev] = ptr;
+    g_noalloc_ctx[dev] = current_ctx_id();
   }
   *out = g_noalloc_ptr[dev];
   return MSZ_OK;
@@ -1179,11 +1221,16 @@ extern "C" int msz_fix_noalloc(int ndim, const int64_t dims[3], int dtype, const
   // An engine of one field whose arrays point into the static scratch and the
   // caller's outputs; its host-side arrays and state live on this stack frame.
   msz_engine_s E;
-  cudaGetDevice(&E.device);
+  if (cudaGetDevice(&E.device) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MSZ_ERR_CUDA);
+  }
   alignas(128) unsigned char host_buf[8192];
   HostArena measure{nullptr, 0, 0};
   host_engine(&E, 1, &ndim, dims, &dtype, measure);
-  if (measure.off > sizeof(host_buf)) return fail(MSZ_ERR_CUDA);
+  // the host arrays of one field have a fixed size (no dependence on N):
+  // this holds for every shape, and the scratch error is reported if not
+  if (measure.off > sizeof(host_buf)) return fail(MSZ_ERR_TOO_LARGE);
   HostArena h{host_buf, sizeof(host_buf), 0};
   rc = host_engine(&E, 1, &ndim, dims, &dtype, h);
   if (rc != MSZ_OK) return fail(rc);
@@ -1250,7 +1297,7 @@ struct SrvRequest {
 };
 
 struct SrvSlot {
-  int state = 0;  // 0 free, 1 running, 2 finished (result held), 3 release requested
+  int state = 0;  // 0 free, 1 running, 2 finished (result held), 3 release requested, 4 cancel requested
   uint64_t id = 0;
   void* block = nullptr;
   size_t bytes = 0;
@@ -1354,7 +1401,7 @@ bool srv_admit(msz_server_s* S) {
     cudaMemsetAsync(E->bufs[slot].flags, 0, (size_t)emit_tiles(G) * kEmitTile, S->stream);
     DevState& H = E->h_states[slot];
     std::memset(&H, 0, sizeof(DevState));
-    H.phase = PH_INIT;
+    H.phase = (E->opt.flags & MSZ_OPT_TEST_STALL) ? PH_PARKED : PH_INIT;
     H.max_rounds = E->opt.max_rounds ? E->opt.max_rounds : 10000000ull;
     cudaMemcpyAsync(E->d_states + slot, &H, sizeof(DevState), cudaMemcpyHostToDevice, S->stream);
     S->f[slot] = R.f;
@@ -1382,6 +1429,20 @@ void srv_worker(msz_server_s* S) {
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(S->mu);
+      // cancelled running fields leave the running set (no kernel is in
+      // flight here: every chunk ends with a stream synchronisation)
+      for (int i = 0; i < S->slots_n; ++i) {
+        SrvSlot& sl = S->slots[i];
+        if (sl.state == 4) {
+          std::memset(&sl.result, 0, sizeof(sl.result));
+          sl.result.status = MSZ_ERR_CANCELLED;
+          sl.done_ns = now_ns();
+          sl.result.device_ms = (float)((sl.done_ns - sl.submit_ns) * 1e-6);
+          sl.state = 2;
+          changed = true;
+          S->cv.notify_all();
+        }
+      }
       // free released slots
       for (int i = 0; i < S->slots_n; ++i) {
         SrvSlot& sl = S->slots[i];
@@ -1444,10 +1505,12 @@ void srv_worker(msz_server_s* S) {
       std::memset(&R, 0, sizeof(R));
       R.status = st;
       R.counts = H.cnt;
-      if (st == MSZ_OK) {
+      if (st == MSZ_OK || (st == MSZ_ERR_NOCONVERGE && H.emitted)) {
         R.edit_idx = E->bufs[i].edit_idx;
         R.edit_val = E->bufs[i].edit_val;
         R.n_edits = H.n_edits;
+      }
+      if (st == MSZ_OK) {
         R.label_max = E->bufs[i].Pup;
         R.label_min = E->bufs[i].Pdn;
       }
@@ -1592,6 +1655,25 @@ int msz_server_release(msz_server S, uint64_t request_id) {
   auto it = S->where.find(request_id);
   if (it == S->where.end() || S->slots[it->second].state != 2) return MSZ_ERR_BUSY;
   S->slots[it->second].state = 3;
+  S->cv.notify_all();
+  return MSZ_OK;
+}
+
+int msz_server_cancel(msz_server S, uint64_t request_id) {
+  if (!S) return MSZ_ERR_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  for (auto q = S->queue.begin(); q != S->queue.end(); ++q)
+    if (q->id == request_id) {
+      S->queue.erase(q);
+      S->rejected[request_id] = SrvDone{MSZ_ERR_CANCELLED, now_ns()};
+      S->cv.notify_all();
+      return MSZ_OK;
+    }
+  auto it = S->where.find(request_id);
+  if (it == S->where.end()) return S->rejected.count(request_id) ? MSZ_ERR_BUSY : MSZ_ERR_ARG;
+  SrvSlot& sl = S->slots[it->second];
+  if (sl.state != 1) return MSZ_ERR_BUSY;
+  sl.state = 4;
   S->cv.notify_all();
   return MSZ_OK;
 }

@@ -4,7 +4,10 @@ or they run where an allocation may block or fail). It keeps its scratch in a
 static device array inside the library; these tests check, through the C ABI,
 that its results equal msz_fix's (bit for bit: the method's tolerance is
 0 ulp) on two calls in a row, and that a field too large for that array is
-rejected. This file is collected last on purpose."""
+rejected. It also runs two fields of the same vertex count but transposed
+shapes back to back: the array is laid out identically for both, so the
+second call rewrites the sweep's tensor maps at the addresses the first
+used. This file is collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -60,6 +63,36 @@ def test_noalloc_matches_fix_twice(name, make, rel):
         assert torch.equal(lmax.view(f.shape), ref.label_max)
         assert torch.equal(lmin.view(f.shape), ref.label_min)
         assert r.counts.as_dict() == ref.counts
+
+
+def _noalloc(native, f, fh, xi, tdt):
+    n = f.numel()
+    idx = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    val = torch.zeros(n, dtype=tdt, device="cuda")
+    lmax = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    lmin = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    r = native.msz_fix_noalloc(tuple(f.shape), tdt, f.data_ptr(), fh.data_ptr(), xi, idx.data_ptr(),
+                               val.data_ptr(), lmax.data_ptr(), lmin.data_ptr(),
+                               torch.cuda.current_stream().cuda_stream)
+    return r, idx, val, lmax, lmin
+
+
+def test_noalloc_transposed_shapes_back_to_back():
+    msz, native = _setup()
+    fields = []
+    for shape, seed in (((64, 128), 3), ((128, 64), 4), ((64, 128), 5)):
+        f = synth.bumps2d(shape[1], shape[0], seed)
+        xi = synth.xi_for(f, 1e-3)
+        fields.append((torch.from_numpy(f).cuda(), torch.from_numpy(synth.quantise(f, xi)).cuda(), xi))
+    refs = [msz.fix(f, h, x) for f, h, x in fields]
+    for (f, h, x), ref in zip(fields, refs):
+        r, idx, val, lmax, lmin = _noalloc(native, f, h, x, torch.float32)
+        assert r.status == 0
+        ne = int(r.n_edits)
+        assert ne == ref.n_edits and r.counts.as_dict() == ref.counts
+        assert torch.equal(idx[:ne].long(), ref.edit_idx)
+        assert torch.equal(val[:ne].view(torch.int32), ref.edit_val.view(torch.int32))
+        assert torch.equal(lmax.view(f.shape), ref.label_max) and torch.equal(lmin.view(f.shape), ref.label_min)
 
 
 def test_noalloc_rejects_fields_beyond_its_scratch():
