@@ -123,17 +123,18 @@ HBM_BOUND = ("k_csweep", "k_ecount", "k_efill", "k_jump", "k_rcheck")
 
 # DRAM bytes per work unit from one ncu capture of a working launch on the
 # 320^3 field of the same workload (dram__bytes_read.sum +
-# dram__bytes_write.sum of the launch / its units; profiles/k_*_turb320_f32.md),
-# scaled to the bench's launches by their units. Only kernels unchanged since
-# their capture are listed.
-PROFILED_TRAFFIC = {"k_rcheck": 584.882432e6 / 320 ** 3}
+# dram__bytes_write.sum of the launch / its units), scaled to the bench's
+# launches by their units. Only kernels unchanged since their capture are
+# listed.
+PROFILED_TRAFFIC = {}
 
 
 def kernel_bytes(name, st, n, es):
     """Algorithmic DRAM bytes of a kernel's working launches (element size es,
     3D field of n vertices) from its work units, or None for the sparse
     kernels whose traffic is dominated by scattered L2 accesses:
-    k_csweep      g (es) + f's direction byte per vertex swept;
+    k_csweep      the stencil sweep's minimum: g (es) and f's direction byte
+                  read, one byte of g's classification written per vertex;
     k_label_tile  g's direction byte read + two tile terminals (8) written per
                   vertex of the tiles recomputed (f's evaluation, once per fix,
                   also reads f and g and writes both direction bytes: not
@@ -145,10 +146,12 @@ def kernel_bytes(name, st, n, es):
                   written (8) per exit;
     k_jump        4 bytes per exit-table access (entry read; gather and write
                   of the entries still holding a rank);
-    k_rcheck      four label words per vertex (16)."""
+    k_rcheck      the R-check's minimum: four label words (16), both
+                  direction bytes (2) read and one request byte written (1)
+                  per vertex."""
     u, w = st["units"], st["work_launches"]
     if name == "k_csweep":
-        return u * (es + 1)
+        return u * (es + 2)
     if name == "k_label_tile":
         return u * 9
     if name == "k_ecount":
@@ -158,7 +161,7 @@ def kernel_bytes(name, st, n, es):
     if name == "k_jump":
         return u * 4
     if name == "k_rcheck":
-        return u * 16
+        return u * 19
     return None
 
 
@@ -198,6 +201,40 @@ def oracle_sample(f, cases, crop, max_seconds=30.0):
     desc = (f"oracle fix of the leading {crop}^3 block of the 512^3 field "
             f"({fc.size} vertices) at xi/range in {done}, single thread")
     return tot_v / tot_s / 1e6, tot_s, desc
+
+
+def oracle_c1():
+    """The oracle on the 128 x 128 float32 bumps field (seed 0, xi = 1e-3
+    range), timed here on one host core."""
+    from paper_2406_09423_gb300 import synth
+
+    import oracle
+
+    f = synth.bumps2d(128, 128, 0)
+    xi = synth.xi_for(f, 1e-3)
+    fh = synth.quantise(f, xi)
+    t = time.perf_counter()
+    r = oracle.fix(f, fh, xi)
+    dt = time.perf_counter() - t
+    return {"workload": "bumps 128^2 f32, xi = 1e-3 range", "status": r.status, "seconds": dt,
+            "mvps": f.size / dt / 1e6}
+
+
+def oracle_records():
+    """Wall time of the oracle's full-size runs, as recorded with their
+    results in tests/golden/fullsize_*.json (one core of the host named
+    there); far too long to repeat inside a benchmark run."""
+    import glob
+
+    out = {}
+    for p in sorted(glob.glob(os.path.join(ROOT, "tests", "golden", "fullsize_*.json"))):
+        rec = json.load(open(p))
+        n = 1
+        for d in rec["shape"]:
+            n *= d
+        out[rec["name"]] = {"seconds": rec["oracle_seconds"], "mvps": n / rec["oracle_seconds"] / 1e6,
+                            "host": rec.get("host")}
+    return out
 
 
 def run_reference(args):
@@ -340,7 +377,7 @@ def run_batched(torch, msz, dev, count=64):
             "identical_to_plain": bool(same), "max_sweeps": max(r.counts["sweeps"] for r in res)}
 
 
-def run_served(torch, msz, dev, arrivals=32, rate=200.0, pool=2, budget_gb=60.0):
+def run_served(torch, msz, dev, arrivals=300, rate=200.0, pool=8, budget_gb=60.0):
     """Served form: Poisson arrivals (mean `rate`/s, seed 4) of fields drawn
     from the single-field workloads (3600x2400 ocean or 512^3 turbulence with
     probability 1/2 each, 5% 384^3 turbulence; xi uniform over 1e-3, 1e-4,
@@ -431,16 +468,31 @@ def run_served(torch, msz, dev, arrivals=32, rate=200.0, pool=2, budget_gb=60.0)
     t_plain = time.perf_counter() - t0
     for p in plans.values():
         p.close()
+    lat_plain_in_order = list(lat_plain)
     lat_plain.sort()
 
     def pct(a, q):
-        return a[min(len(a) - 1, max(0, int(round(q * len(a))) - 1))]
+        a = sorted(a)
+        return a[min(len(a) - 1, max(0, int(round(q * len(a))) - 1))] if a else None
 
-    return {"arrivals": arrivals, "rate_per_s": rate, "budget_gb": budget_gb, "vertices": n_total,
+    kind_of = [r[0] for r in reqs]
+    served_by_kind = {}
+    for j, lt, _ in done.values():
+        served_by_kind.setdefault(kind_of[j], []).append(lt)
+    plain_by_kind = {}
+    for j, lt in enumerate(lat_plain_in_order):
+        plain_by_kind.setdefault(kind_of[j], []).append(lt)
+    per_kind = {kname: {"n": len(v), "served_p50_s": pct(v, 0.5), "served_p99_s": pct(v, 0.99),
+                        "plain_p50_s": pct(plain_by_kind.get(kname, []), 0.5),
+                        "plain_p99_s": pct(plain_by_kind.get(kname, []), 0.99)}
+                for kname, v in sorted(served_by_kind.items())}
+    return {"arrivals": arrivals, "rate_per_s": rate, "budget_gb": budget_gb, "pool_seeds": pool,
+            "vertices": n_total,
             "served": {"p50_s": pct(lat, 0.5), "p99_s": pct(lat, 0.99), "fields_per_s": arrivals / t_served,
                        "mvps": n_total / t_served / 1e6, "wall_s": t_served},
             "plain": {"p50_s": pct(lat_plain, 0.5), "p99_s": pct(lat_plain, 0.99),
                       "fields_per_s": arrivals / t_plain, "mvps": n_total / t_plain / 1e6, "wall_s": t_plain},
+            "per_kind": per_kind,
             "mix": {kname: sum(1 for kk, _, _ in kinds if kk == kname) for kname in ("ocean", "turb512", "turb384")}}
 
 
@@ -457,7 +509,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-metrics", action="store_true", help="skip the Appendix B metrics per bound")
-    ap.add_argument("--arrivals", type=int, default=32, help="served form: number of Poisson arrivals")
+    ap.add_argument("--arrivals", type=int, default=300, help="served form: number of Poisson arrivals")
     ap.add_argument("--profile-fix", type=float, default=None, metavar="REL",
                     help="run one fix of the --size workload at xi = REL * range and exit (for ncu captures)")
     args = ap.parse_args()
@@ -583,21 +635,29 @@ def main():
             row["achieved_gbs"] = b / (st["work_ms"] / 1e3) / 1e9
             row["frac"] = row["achieved_gbs"] / peak_gbs
         kernels.append(row)
-    roofline = None
-    hbm_rows = [k for k in kernels if "achieved_gbs" in k and k["name"] in HBM_BOUND]
-    if hbm_rows:
-        top = max(hbm_rows, key=lambda k: k["work_ms"])
-        avg_ms = top["work_ms"] / top["work_launches"]
-        per_unit = PROFILED_TRAFFIC.get(top["name"])
-        traffic = per_unit * top["units"] / top["work_launches"] if per_unit else None
-        longest = max(kernels, key=lambda k: k["work_ms"])
-        roofline = {"bound": "hbm", "achieved": top["achieved_gbs"], "peak": peak_gbs, "unit": "GB/s",
-                    "frac": top["frac"], "traffic": traffic, "kernel": top["name"],
-                    "note": ("the HBM-bound kernel with the most working time; the longest kernel, "
-                             f"{longest['name']}, is not bound by HBM bandwidth") if longest is not top else None,
-                    "avg_launch_ms": avg_ms, "bytes_per_launch": top["algorithmic_bytes"] / top["work_launches"],
-                    "work_launches": top["work_launches"], "peak_source": peak_src,
-                    "share_of_kernel_time": top["ms"] / sum(k["ms"] for k in kernels)}
+    total_kms = sum(k["ms"] for k in kernels)
+
+    def roof(row, note):
+        avg_ms = row["work_ms"] / row["work_launches"]
+        per_unit = PROFILED_TRAFFIC.get(row["name"])
+        traffic = per_unit * row["units"] / row["work_launches"] if per_unit else None
+        return {"bound": "hbm", "achieved": row["achieved_gbs"], "peak": peak_gbs, "unit": "GB/s",
+                "frac": row["frac"], "traffic": traffic, "kernel": row["name"], "note": note,
+                "avg_launch_ms": avg_ms, "bytes_per_launch": row["algorithmic_bytes"] / row["work_launches"],
+                "work_launches": row["work_launches"], "peak_source": peak_src,
+                "share_of_kernel_time": row["ms"] / total_kms}
+
+    # the roofline object is the kernel with the most working time; the
+    # HBM-streaming kernel with the most working time is reported beside it
+    roofline = roofline_stream = None
+    with_bytes = [k for k in kernels if "achieved_gbs" in k]
+    if with_bytes:
+        top = max(with_bytes, key=lambda k: k["work_ms"])
+        roofline = roof(top, "the kernel with the most working time")
+        hbm_rows = [k for k in with_bytes if k["name"] in HBM_BOUND]
+        if hbm_rows:
+            hs = max(hbm_rows, key=lambda k: k["work_ms"])
+            roofline_stream = roof(hs, "the HBM-streaming kernel with the most working time")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -605,7 +665,8 @@ def main():
 
         v, s, desc = oracle_sample(f, cases, args.crop)
         cpu = {"value": v, "unit": "Mvertices/s", "cores": 1, "kind": "oracle", "sample": desc,
-               "seconds": s, "host_cores": multiprocessing.cpu_count()}
+               "seconds": s, "host_cores": multiprocessing.cpu_count(), "c1": oracle_c1(),
+               "fullsize_records": oracle_records()}
 
     # Appendix B metrics of each bound (outside the timed region): right
     # labelled ratio and PSNR of f-hat before and of the edited field after
@@ -637,12 +698,22 @@ def main():
         served = run_served(torch, msz, dev, arrivals=args.arrivals)
 
     per_xi = {}
+    kinds6 = ("fpmax", "fpmin", "fnmax", "fnmin", "rmax", "rmin")
     for (rel, c, ne), ms in zip(counts, step_ms):
-        d = per_xi.setdefault(str(rel), {"ms": [], "sweeps": c["sweeps"], "label_evals": c["label_evals"],
-                                         "edits": ne, "freezes": c["freezes"]})
+        d = per_xi.setdefault(str(rel), {
+            "ms": [], "sweeps": c["sweeps"], "label_evals": c["label_evals"], "edits": ne,
+            "dec_edits": c["dec_edits"], "freezes": c["freezes"],
+            # freezing requests by the case that made them, and how many of
+            # them found their target already frozen (the others at its bound)
+            "freeze_req": {k: c["freeze_req_" + k] for k in kinds6},
+            "freeze_req_target_frozen": {k: c["freeze_req_frozen_" + k] for k in kinds6},
+            "c_rounds": sum(c["c_rounds_" + k] for k in kinds6[:4]), "r_rounds": c["r_rounds"]})
         d["ms"].append(ms)
     for rel_s, d in per_xi.items():
-        d["mvps"] = n / (statistics.median(d["ms"]) / 1e3) / 1e6
+        srt = sorted(d["ms"])
+        d["p50_ms"] = statistics.median(srt)
+        d["p99_ms"] = srt[max(0, int(round(0.99 * len(srt))) - 1)]
+        d["mvps"] = n / (d["p50_ms"] / 1e3) / 1e6
         if rel_s in quality:
             d["quality"] = quality[rel_s]
     step_rates = sorted(n / (ms / 1e3) / 1e6 for ms in step_ms)
@@ -659,6 +730,7 @@ def main():
                        "form": "plain (one field per msz_fix)", "parallelism": f"replicas x{world}",
                        "l2": "inputs 2 x 537 MB > 129 MB L2, no flush"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "roofline_stream": roofline_stream,
             "cpu_baseline": cpu,
             "latency_ms": {"p50": p50, "p99": p99}, "per_xi": per_xi,
             "step_mvps": {"min": step_rates[0], "max": step_rates[-1]},
