@@ -97,17 +97,25 @@ struct Field {
   uint8_t* fdir;
   uint8_t* gdir;
   uint8_t* flags;
-  int32_t* Mf;    // f: tile terminals (kExt-flagged), labels once f's evaluation is done
+  int32_t* Mf;    // f's labels once f's evaluation is done
   int32_t* mf;
-  int32_t* Pup;   // g: tile terminals (kExt-flagged), labels once the field has converged
+  int32_t* Pup;   // outputs: max / min labels once the field has converged
   int32_t* Pdn;
+  uint32_t* term; // tile terminals (kTermFlag form) of the current evaluation; Pup's memory
+                  // (the outputs are written only at emission)
+  uint32_t* tface[2];  // per direction, at tile-face vertices (the only possible tile exits): the
+                       // global index of the tile terminal, kExt-flagged for an extremum; [0] is
+                       // Pdn's memory
   // per direction (0: ascending lines / max labels, 1: descending / min)
   uint32_t* ex[2];  // bitmap of tile-exit vertices
   uint32_t* ep[2];  // per bitmap word: exits before it within its dense unit
   uint32_t* ub[2];  // per dense unit: exits before it (after the scan; counts before)
   uint2* xr[2];     // per bitmap word: (bitmap word, exits before it): one load gives a rank
   uint32_t* lc[2];  // compact exit table, indexed by exit rank
-  uint8_t* tdirty;  // label tiles whose terminals must be recomputed
+  uint8_t* tdirty;  // per label tile: bit 0 terminals to recompute, bit 1 recomputed and not yet checked
+  uint32_t* texit;  // per label tile and direction: bitmap over the shell cells its lines leave through
+  uint32_t* tsnap;  // per label tile, direction and shell cell: the exit's label at the tile's last check
+  uint8_t* twrong;  // per label tile: its last check found a wrong label
   uint8_t* cls;     // false-type bits of g per vertex (FPmax, FPmin, FNmax, FNmin), padded to kEmitTile
   uint32_t* cases;  // the round's cases of the current type
   uint32_t* epoch;  // round in which a vertex was last reclassified (claims a vertex once per round)

@@ -143,6 +143,10 @@ struct FieldBufs {
   uint2* xr[2] = {nullptr, nullptr};
   uint32_t* lc[2] = {nullptr, nullptr};
   uint8_t* tdirty = nullptr;
+  uint32_t* texit = nullptr;
+  uint32_t* tsnap = nullptr;
+  uint8_t* twrong = nullptr;
+  uint32_t* tface1 = nullptr;
   uint8_t* cls = nullptr;
   uint32_t* cases = nullptr;
   uint32_t* epoch = nullptr;
@@ -183,6 +187,10 @@ void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs
     B.lc[d] = (uint32_t*)b.take(n * 4);
   }
   B.tdirty = (uint8_t*)b.take((size_t)label_tiles(G));
+  B.texit = (uint32_t*)b.take((size_t)label_tiles(G) * 2 * (G.nd == 3 ? LabelGeom<3>::SHW : LabelGeom<2>::SHW) * 4);
+  B.tsnap = (uint32_t*)b.take((size_t)label_tiles(G) * 2 * (G.nd == 3 ? LabelGeom<3>::SHELL : LabelGeom<2>::SHELL) * 4);
+  B.twrong = (uint8_t*)b.take((size_t)label_tiles(G));
+  B.tface1 = (uint32_t*)b.take(n * 4);
   B.cls = (uint8_t*)b.take(nt * kEmitTile);
   B.cases = (uint32_t*)b.take(n * 4);
   B.epoch = (uint32_t*)b.take(n * 4);
@@ -235,6 +243,7 @@ struct Group {
   bool small_ok = false;  // a k_csmall cluster fits on the device
   size_t label_smem[2] = {0, 0};  // f's pass, g's passes
   int grid_label[2] = {0, 0};
+  int grid_rcheck = 0;
 
   // Host arrays for nf fields (null pointers while measuring).
   void host_carve(HostArena& h) {
@@ -307,6 +316,9 @@ struct Group {
       F.mf = B.mf;
       F.Pup = B.Pup;
       F.Pdn = B.Pdn;
+      F.term = reinterpret_cast<uint32_t*>(B.Pup);
+      F.tface[0] = reinterpret_cast<uint32_t*>(B.Pdn);
+      F.tface[1] = B.tface1;
       for (int d = 0; d < 2; ++d) {
         F.ex[d] = B.ex[d];
         F.ep[d] = B.ep[d];
@@ -315,6 +327,9 @@ struct Group {
         F.lc[d] = B.lc[d];
       }
       F.tdirty = B.tdirty;
+      F.texit = B.texit;
+      F.tsnap = B.tsnap;
+      F.twrong = B.twrong;
       F.cls = B.cls;
       F.cases = B.cases;
       F.epoch = B.epoch;
@@ -364,6 +379,7 @@ struct Group {
       return MSZ_ERR_CUDA;
     grid_label[0] = occ_grid((const void*)k_label_tile<T, ND, false>, kThreads, label_smem[0], args.total[K_LABEL]);
     grid_label[1] = occ_grid((const void*)k_label_tile<T, ND, true>, kThreads, label_smem[1], args.total[K_LABEL]);
+    grid_rcheck = occ_grid((const void*)k_rcheck<T, ND>, kThreads, 0, args.total[K_LABEL]);
     if (cudaGetLastError() != cudaSuccess) return MSZ_ERR_CUDA;
     {
       cudaLaunchConfig_t cfg = {};
@@ -459,9 +475,9 @@ struct Group {
     k_label_tile<T, ND, true><<<grid_label[1], kThreads, label_smem[1], s>>>(a());
     k_ecount<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
     k_escan<T><<<nf, 1024, 0, s>>>(a());
-    k_efill<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
+    k_efill<T, ND><<<grid[K_DENSE], kThreads, 0, s>>>(a());
     for (int j = 0; j < kJumpsPerStep; ++j) k_jump<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
-    k_rcheck<T, ND><<<grid[K_DENSE], kThreads, 0, s>>>(a());
+    k_rcheck<T, ND><<<grid_rcheck, kThreads, 0, s>>>(a());
   }
   template <class A>
   void tail(cudaStream_t s, A&& a) {

@@ -24,10 +24,128 @@ struct LabelGeom {
   static constexpr int TZ = (ND == 3) ? 16 : 1;
   static constexpr int TV = TX * TY * TZ;  // 4096 (3D) / 2048 (2D) vertices
   static constexpr int SX = TX + 2, SY = TY + 2, SZ = (ND == 3) ? TZ + 2 : 1;
-  static constexpr int HALO = SX * SY * SZ;  // < 65536: pointers fit in 16 bits
+  static constexpr int HALO = SX * SY * SZ;  // < 32768: a pointer and a flag fit in 16 bits
   static constexpr int PER_THREAD = TV / kThreads;
   static constexpr int ROWS = SY * SZ;
+  // The halo shell: the halo cells outside the tile (the only cells a path
+  // can leave the tile through). In 3D the two end planes (SX * SY cells
+  // each), then per inner plane a ring of 2 SX + 2 (SY - 2) cells; in 2D one
+  // ring.
+  static constexpr int RING = 2 * SX + 2 * (SY - 2);
+  static constexpr int SHELL = (ND == 3) ? 2 * SX * SY + TZ * RING : RING;
+  static constexpr int SHW = (SHELL + 31) / 32;  // 32-bit words of a shell bitmap
+  static_assert(HALO <= 0x4000 && TV <= 0x4000, "pointers, indices and the terminal flags share 16 bits");
 };
+
+// Tile terminals (k_label_tile's output, one 32-bit word per vertex): the
+// ascending terminal in the low 16 bits, the descending one in the high 16.
+// Every terminal half has kTermFlag set. With kTermExtr also set, the low 14
+// bits are the tile cell index (lx + TX (ly + TY lz)) of the extremum inside
+// the tile where the vertex's integral line ends; otherwise they are the
+// shell index of the halo cell where the line leaves its tile (a tile exit).
+// During the pointer doubling an unflagged half is a pointer (halo index).
+constexpr uint32_t kTermFlag = 0x8000u;
+constexpr uint32_t kTermExtr = 0x4000u;
+constexpr uint32_t kTermIdx = 0x3fffu;
+
+// Halo coordinates of shell cell s.
+template <int ND>
+__host__ __device__ __forceinline__ void shell_cell(int s, int& hx, int& hy, int& hz) {
+  using LG = LabelGeom<ND>;
+  int q = s;
+  hz = 0;
+  if (ND == 3) {
+    constexpr int P = LG::SX * LG::SY;
+    if (s < 2 * P) {
+      hz = (s < P) ? 0 : LG::SZ - 1;
+      const int r = s - (s < P ? 0 : P);
+      hy = r / LG::SX;
+      hx = r - hy * LG::SX;
+      return;
+    }
+    const int r = s - 2 * P;
+    hz = 1 + r / LG::RING;
+    q = r - (hz - 1) * LG::RING;
+  }
+  if (q < LG::SX) {
+    hy = 0;
+    hx = q;
+  } else if (q < 2 * LG::SX) {
+    hy = LG::SY - 1;
+    hx = q - LG::SX;
+  } else {
+    const int w = q - 2 * LG::SX;
+    hy = 1 + (w >> 1);
+    hx = (w & 1) * (LG::SX - 1);
+  }
+}
+
+// Shell index of the shell cell at halo coordinates (hx, hy, hz) (the
+// inverse of shell_cell).
+template <int ND>
+__host__ __device__ __forceinline__ int shell_index(int hx, int hy, int hz) {
+  using LG = LabelGeom<ND>;
+  int base = 0;
+  if (ND == 3) {
+    constexpr int P = LG::SX * LG::SY;
+    if (hz == 0) return hy * LG::SX + hx;
+    if (hz == LG::SZ - 1) return P + hy * LG::SX + hx;
+    base = 2 * P + (hz - 1) * LG::RING;
+  }
+  if (hy == 0) return base + hx;
+  if (hy == LG::SY - 1) return base + LG::SX + hx;
+  return base + 2 * LG::SX + 2 * (hy - 1) + (hx != 0);
+}
+
+// Halo coordinates of halo index h.
+template <int ND>
+__device__ __forceinline__ void halo_cell(int h, int& hx, int& hy, int& hz) {
+  using LG = LabelGeom<ND>;
+  hx = h % LG::SX;
+  const int t = h / LG::SX;
+  hy = t % LG::SY;
+  hz = t / LG::SY;
+}
+
+// Origin (first vertex) of the label tile holding vertex (x, y, z).
+template <int ND>
+__device__ __forceinline__ void tile_origin_of(int x, int y, int z, int& x0, int& y0, int& z0) {
+  using LG = LabelGeom<ND>;
+  x0 = x - x % LG::TX;
+  y0 = y - y % LG::TY;
+  z0 = z - z % LG::TZ;
+}
+
+// Global index of the extremum of terminal half t (kTermExtr set) of a
+// vertex whose tile starts at (x0, y0, z0): the tile cell index decoded with
+// shifts (the tile sides are powers of two).
+template <int ND>
+__device__ __forceinline__ int extremum_vertex(const Geom& G, uint32_t t, int x0, int y0, int z0) {
+  using LG = LabelGeom<ND>;
+  static_assert((LG::TX & (LG::TX - 1)) == 0 && (LG::TY & (LG::TY - 1)) == 0, "power-of-two tile sides");
+  const int ci = (int)(t & kTermIdx);
+  return (x0 + ci % LG::TX) + G.nx * ((y0 + (ci / LG::TX) % LG::TY) + G.ny * (z0 + ci / (LG::TX * LG::TY)));
+}
+
+// Shell cells' halo coordinates packed hx | hy << 8 | hz << 16, for a
+// block's shared decode table (filled by every thread, then synchronised).
+template <int ND>
+__device__ __forceinline__ void fill_shell_table(uint32_t* tab) {
+  for (int s = threadIdx.x; s < LabelGeom<ND>::SHELL; s += blockDim.x) {
+    int hx, hy, hz;
+    shell_cell<ND>(s, hx, hy, hz);
+    tab[s] = (uint32_t)hx | ((uint32_t)hy << 8) | ((uint32_t)hz << 16);
+  }
+}
+
+// Global index of shell cell s of the tile starting at (x0, y0, z0), from
+// the shared decode table.
+template <int ND>
+__device__ __forceinline__ int shell_vertex(const Geom& G, const uint32_t* tab, int s, int x0, int y0, int z0) {
+  const uint32_t c = tab[s];
+  return (x0 - 1 + (int)(c & 0xffu)) +
+         G.nx * ((y0 - 1 + (int)((c >> 8) & 0xffu)) + G.ny * (ND == 3 ? z0 - 1 + (int)(c >> 16) : 0));
+}
 
 // Marks every label tile whose tile or one-vertex halo contains vertex u:
 // the tiles of u + d for d in {-1,0,1}^d (their terminals must be redone).
@@ -123,7 +241,10 @@ __global__ void __launch_bounds__(kThreads) k_init(GroupArgs<T> A) {
     {
       const int ntl = F.units[K_LABEL], nu = F.units[K_DENSE], lu = u_ - pre[i];
       const int per = (ntl + nu - 1) / nu;
-      for (int t = lu * per + threadIdx.x; t < min(ntl, (lu + 1) * per); t += blockDim.x) F.tdirty[t] = 1;
+      for (int t = lu * per + threadIdx.x; t < min(ntl, (lu + 1) * per); t += blockDim.x) {
+        F.tdirty[t] = 1;
+        F.twrong[t] = 0;
+      }
       const int ncc = 4 * F.units[K_EMIT], pc = (ncc + nu - 1) / nu;
       for (int t = lu * pc + threadIdx.x; t < min(ncc, (lu + 1) * pc); t += blockDim.x) F.ccnt[t] = 0;
     }
@@ -614,9 +735,10 @@ __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
 // steepest ascending / descending neighbour (candidates in ascending index
 // order: ties go to the larger index for the maximum and to the smaller for
 // the minimum; NaN halo cells never win), and follows the pointers inside the
-// tile by pointer doubling. Each vertex leaves with a pointer to the first
-// vertex outside the tile on its integral line, or to the extremum it reaches
-// inside. Job 0: f (fdir, Mf, mf). Job 1: g (gdir, Pup, Pdn).
+// tile by pointer doubling. Each vertex leaves with its tile terminal in each
+// direction (one 32-bit word, see kTermFlag): the shell cell where its
+// integral line leaves the tile, or the extremum inside the tile where it
+// ends. Job 0: f (fdir, terminals), job 1: g (terminals from gdir).
 // ---------------------------------------------------------------------------
 // Dynamic shared memory of k_label_tile: f's pass holds the halo values and
 // the pointers, g's passes the pointers only.
@@ -628,10 +750,9 @@ size_t label_smem_bytes() {
 
 // A tile's values with a one-cell halo: every in-grid cell by an
 // asynchronous global -> shared copy (all of the block's copies in flight at
-// once), the others NaN. init_pp: halo pointers start as self pointers.
+// once), the others NaN.
 template <class T, int ND>
-__device__ __forceinline__ void load_halo(T* val, uint32_t* PP, const T* src, const Geom& G, int x0, int y0, int z0,
-                                          bool init_pp) {
+__device__ __forceinline__ void load_halo(T* val, const T* src, const Geom& G, int x0, int y0, int z0) {
   using LG = LabelGeom<ND>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int row = warp; row < LG::ROWS; row += kThreads / 32) {
@@ -644,7 +765,6 @@ __device__ __forceinline__ void load_halo(T* val, uint32_t* PP, const T* src, co
       const int h = hx + LG::SX * row;
       if (rin && gx >= 0 && gx < G.nx) cp_async_elem(&val[h], src + rbase + gx);
       else val[h] = qnan<T>();
-      if (init_pp) PP[h] = (uint32_t)h | ((uint32_t)h << 16);
     }
   }
 }
@@ -693,6 +813,17 @@ __device__ __forceinline__ bool leaves_tile(int s, uint32_t bhi, uint32_t blo) {
   return (m & (neg ? blo : bhi)) != 0u;
 }
 
+// One pointer-doubling step of a 16-bit half a (lo: the low half of the
+// words in PP, else the high half): a flagged half is a final terminal value
+// and stays; a pointer moves to the pointed cell's half. The load is made in
+// either case (a flagged half's low bits index a valid cell) so that both
+// halves' loads issue together.
+__device__ __forceinline__ uint32_t double_half(const uint32_t* PP, uint32_t a, bool lo) {
+  const uint32_t w = PP[a & kTermIdx];
+  const uint32_t q = lo ? (w & 0xffffu) : (w >> 16);
+  return (a & kTermFlag) ? a : q;
+}
+
 // JOB: the fields in f's pass (false) or in g's (true); the two are launched
 // side by side, each doing nothing for the other's fields.
 template <class T, int ND, bool JOB>
@@ -700,9 +831,11 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
   using LG = LabelGeom<ND>;
   extern __shared__ __align__(16) unsigned char lsm[];
   T* val = reinterpret_cast<T*>(lsm);
-  // Pointers in halo coordinates: halo cells and extrema point to themselves
-  // (terminal); interior cells to their steepest neighbour.
-  // ascending pointer (low 16 bits) and descending pointer (high 16 bits)
+  // Per halo cell, the ascending (low 16 bits) and descending (high 16 bits)
+  // halves: a tile cell's halves point to its steepest neighbours (halo
+  // indices), or hold its own terminal value kTermFlag | kTermExtr | cell
+  // index if it is the extremum; a shell cell's halves hold its terminal
+  // value kTermFlag | shell index.
   uint32_t* PP = reinterpret_cast<uint32_t*>(lsm + (JOB ? 0 : ((LG::HALO * sizeof(T) + 15) / 16) * 16));
   const int* pre = A.prefix + K_LABEL * (A.nf + 1);
   constexpr int HS = LG::SX, HSS = LG::SX * LG::SY;
@@ -710,6 +843,11 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
   constexpr int kExWords = (LG::HALO + 31) / 32 + 2;
   constexpr int kSegs = (LG::SX + 31) / 32;
   __shared__ uint32_t exs[2][kExWords];
+  // the same exits by shell index (the tile's record for the label lookups)
+  constexpr int kShW = LabelGeom<ND>::SHW;
+  __shared__ uint32_t shx[2][kShW];
+  __shared__ uint32_t s_shell[LG::SHELL];  // shell cells' halo coordinates
+  fill_shell_table<ND>(s_shell);
   auto active = [](const Field<T>& F) {
     return F.st->action == ACT_LABELS && F.st->lstate == L_INIT && (F.st->ljob != 0) == JOB;
   };
@@ -725,39 +863,44 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
     const Field<T>& F = A.fields[fi];
     DevState* st = F.st;
     constexpr bool job = JOB;
-    int32_t* OA = job ? F.Pup : F.Mf;
-    int32_t* OB = job ? F.Pdn : F.mf;
     const Geom G = F.G;
     const int tiles_x = (G.nx + LG::TX - 1) / LG::TX;
     const int tiles_y = (G.ny + LG::TY - 1) / LG::TY;
     const int tile = u_ - pre[fi];
     // g's terminals only change in tiles whose tile or halo was edited
-    const bool redo = !job || F.tdirty[tile];
-    __syncthreads();
+    const bool redo = !job || (F.tdirty[tile] & 1);
+    __syncthreads();  // the block's previous tile is done with the shared arrays
     if (!redo) continue;
     const int x0 = (tile % tiles_x) * LG::TX;
     const int y0 = ((tile / tiles_x) % tiles_y) * LG::TY;
     const int z0 = (tile / (tiles_x * tiles_y)) * LG::TZ;
-    __syncthreads();
     for (int k = threadIdx.x; k < 2 * kExWords; k += kThreads) exs[k / kExWords][k % kExWords] = 0u;
-    // Halo cells are terminals. Job 0 reads f's values with the halo; job 1
-    // needs no values: g's direction bytes are kept exact by the
-    // classification that follows every apply.
-    if (!job) load_halo<T, ND>(val, PP, F.f, G, x0, y0, z0, true);
-    else
-      for (int h = threadIdx.x; h < LG::HALO; h += kThreads) PP[h] = (uint32_t)h | ((uint32_t)h << 16);
+    for (int k = threadIdx.x; k < 2 * kShW; k += kThreads) shx[k / kShW][k % kShW] = 0u;
+    // Job 0 reads f's values with the halo; job 1 needs no values: g's
+    // direction bytes are kept exact by the classification that follows
+    // every apply. The shell cells get their terminal values.
+    if (!job) load_halo<T, ND>(val, F.f, G, x0, y0, z0);
+    for (int s = threadIdx.x; s < LG::SHELL; s += kThreads) {
+      int hx, hy, hz;
+      shell_cell<ND>(s, hx, hy, hz);
+      const uint32_t t = kTermFlag | (uint32_t)s;
+      PP[hx + HS * (hy + LG::SY * hz)] = t | (t << 16);
+    }
     cp_async_wait_all();
     __syncthreads();
-    // Pointers of the tile cells. A pointer that leaves the tile marks its
-    // halo cell as a tile exit: the first halo cell on an integral line is
-    // the steepest neighbour of the line's last tile cell, so the marked
-    // cells are exactly the terminals in the halo.
+    // Pointers of the tile cells inside the grid (the others are never
+    // reached and stay out of the doubling). A pointer that leaves the tile
+    // marks its shell cell as a tile exit: the first halo cell on an
+    // integral line is the steepest neighbour of the line's last tile cell,
+    // so the marked cells are exactly the exits of the tile's lines.
+    uint32_t live = 0;
 #pragma unroll
     for (int k = 0; k < LG::PER_THREAD; ++k) {
       const int i = threadIdx.x + k * kThreads;
       const int lx = i % LG::TX, ly = (i / LG::TX) % LG::TY, lz = i / (LG::TX * LG::TY);
       const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-      if (x >= G.nx || y >= G.ny || z >= G.nz) continue;  // outside the grid: keeps its self pointer
+      if (x >= G.nx || y >= G.ny || z >= G.nz) continue;
+      live |= 1u << k;
       const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
       const int v = x + G.nx * (y + G.ny * z);
       uint32_t db;
@@ -769,26 +912,35 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
       }
       const int sa = (int)(db & 15u), sd = (int)(db >> 4);
       const int ca = c + slot_offset(sa, ND, HS, HSS), cd = c + slot_offset(sd, ND, HS, HSS);
-      PP[c] = (uint32_t)ca | ((uint32_t)cd << 16);
+      const uint32_t self = kTermFlag | kTermExtr | (uint32_t)i;  // i: the tile cell index
+      PP[c] = (sa == kSelf ? self : (uint32_t)ca) | ((sd == kSelf ? self : (uint32_t)cd) << 16);
       const uint32_t bhi = (uint32_t)(lx == LG::TX - 1) | ((uint32_t)(ly == LG::TY - 1) << 1) |
                            ((uint32_t)(ND == 3 && lz == LG::TZ - 1) << 2);
       const uint32_t blo = (uint32_t)(lx == 0) | ((uint32_t)(ly == 0) << 1) | ((uint32_t)(ND == 3 && lz == 0) << 2);
       if (bhi | blo) {
-        if (leaves_tile<ND>(sa, bhi, blo)) atomicOr(&exs[0][ca >> 5], 1u << (ca & 31));
-        if (leaves_tile<ND>(sd, bhi, blo)) atomicOr(&exs[1][cd >> 5], 1u << (cd & 31));
+        // the exit's halo coordinates from the cell's and the slot's
+        auto mark_exit = [&](int d, int sl, int ch) {
+          atomicOr(&exs[d][ch >> 5], 1u << (ch & 31));
+          constexpr int npos = Slots<ND>::NPOS;
+          const bool neg = sl >= npos;
+          const int m = slot_mask(ND, neg ? sl - npos : sl), sg = neg ? -1 : 1;
+          const int sh = shell_index<ND>(lx + 1 + sg * (m & 1), ly + 1 + sg * ((m >> 1) & 1),
+                                         (ND == 3) ? lz + 1 + sg * ((m >> 2) & 1) : 0);
+          atomicOr(&shx[d][sh >> 5], 1u << (sh & 31));
+        };
+        if (leaves_tile<ND>(sa, bhi, blo)) mark_exit(0, sa, ca);
+        if (leaves_tile<ND>(sd, bhi, blo)) mark_exit(1, sd, cd);
       }
     }
     if (!job) {
       // g's values (f-hat at this point) for g's first direction bytes,
       // copied in while the pointers double
       __syncthreads();
-      load_halo<T, ND>(val, PP, F.g, G, x0, y0, z0, false);
+      load_halo<T, ND>(val, F.g, G, x0, y0, z0);
     }
     __syncthreads();
-    // pointer doubling; a cell whose two pointers reach terminals is done
-    uint32_t live = (1u << LG::PER_THREAD) - 1u;
-    for (int round = 0; round < 2 * LG::TV; ++round) {
-      int changed = 0;
+    // pointer doubling until every cell of the tile holds its two terminals
+    for (int round = 0; round < 2 * LG::TV && __syncthreads_or(live != 0u); ++round) {
 #pragma unroll
       for (int k = 0; k < LG::PER_THREAD; ++k) {
         if (!((live >> k) & 1u)) continue;
@@ -797,16 +949,13 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
         const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
         const uint32_t p = PP[c];
         const uint32_t a = p & 0xffffu, b = p >> 16;
-        const uint32_t a2 = PP[a] & 0xffffu, b2 = PP[b] >> 16;
-        if (a2 == a && b2 == b) {
-          live &= ~(1u << k);
-        } else {
-          PP[c] = a2 | (b2 << 16);
-          changed = 1;
-        }
+        const uint32_t a2 = double_half(PP, a, true);
+        const uint32_t b2 = double_half(PP, b, false);
+        if (a2 != a || b2 != b) PP[c] = a2 | (b2 << 16);
+        if (a2 & b2 & kTermFlag) live &= ~(1u << k);
       }
-      if (!__syncthreads_or(changed)) break;
     }
+    __syncthreads();
 #pragma unroll
     for (int k = 0; k < LG::PER_THREAD; ++k) {
       const int i = threadIdx.x + k * kThreads;
@@ -814,23 +963,26 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
       const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
       if (x < G.nx && y < G.ny && z < G.nz) {
         const int v = x + G.nx * (y + G.ny * z);
-        const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
-        // terminal cell -> global index; a terminal in the halo is a tile
-        // exit (its bit is set in the block's halo bitmap, flushed below);
-        // one inside the tile is an extremum (flag kExt)
-        auto global_of = [&](int h) -> int {
-          const int hx = h % LG::SX, hy = (h / LG::SX) % LG::SY, hz = h / HSS;
-          const int e = (x0 - 1 + hx) + G.nx * ((y0 - 1 + hy) + G.ny * ((ND == 3) ? (z0 - 1 + hz) : 0));
-          const bool halo = hx == 0 || hx == LG::SX - 1 || hy == 0 || hy == LG::SY - 1 ||
-                            (ND == 3 && (hz == 0 || hz == LG::SZ - 1));
-          return (int)((uint32_t)e | (halo ? 0u : kExt));
-        };
-        const uint32_t p = PP[c];
-        OA[v] = global_of((int)(p & 0xffffu));
-        OB[v] = global_of((int)(p >> 16));
+        const uint32_t p = PP[(lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0)];
+        F.term[v] = p;
+        // a face cell can be another tile's exit: its terminals as global
+        // indices for the exit table
+        const bool face = lx == 0 || lx == LG::TX - 1 || ly == 0 || ly == LG::TY - 1 ||
+                          (ND == 3 && (lz == 0 || lz == LG::TZ - 1));
+        if (face) {
+#pragma unroll
+          for (int d = 0; d < 2; ++d) {
+            const uint32_t t = (p >> (16 * d)) & 0xffffu;
+            F.tface[d][v] = (t & kTermExtr)
+                                ? ((uint32_t)extremum_vertex<ND>(G, t, x0, y0, z0) | kExt)
+                                : (uint32_t)shell_vertex<ND>(G, s_shell, (int)(t & kTermIdx), x0, y0, z0);
+          }
+        }
       }
     }
-    __syncthreads();
+    // the tile's exit record
+    for (int k = threadIdx.x; k < 2 * kShW; k += kThreads)
+      F.texit[(size_t)tile * 2 * kShW + k] = shx[k / kShW][k % kShW];
     // Exit bits into the field's bitmaps: one atomic per global word that a
     // halo-row segment (at most 32 cells, contiguous in x) touches.
     for (int it = threadIdx.x; it < 2 * LG::ROWS * kSegs; it += kThreads) {
@@ -868,7 +1020,9 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
         F.gdir[x + G.nx * (y + G.ny * z)] = (uint8_t)halo_dir<T, ND>(val, c);
       }
     }
-    if (job && threadIdx.x == 0) F.tdirty[tile] = 0;  // f's pass leaves every tile dirty for g's first
+    // recomputed, for the R-check to examine (f's pass leaves every tile
+    // dirty for g's first)
+    if (job && threadIdx.x == 0) F.tdirty[tile] = 2;
     if (threadIdx.x == 0)
       log_units(A, st, KID_LABEL,
                 (uint64_t)min(LG::TX, G.nx - x0) * min(LG::TY, G.ny - y0) * min(LG::TZ, G.nz - z0));
@@ -893,15 +1047,6 @@ __device__ __forceinline__ uint32_t exit_rank(const uint32_t* ex, const uint32_t
 __device__ __forceinline__ uint32_t exit_rank2(const uint2* xr, int e) {
   const uint2 p = xr[e >> 5];
   return p.y + (uint32_t)__popc(p.x & ((1u << (e & 31)) - 1u));
-}
-
-// Label of v (direction d) from its tile terminal: the extremum itself, or
-// the label the exit table holds for the exit its line leaves the tile
-// through.
-template <class T>
-__device__ __forceinline__ int resolve_label(const Field<T>& F, int d, const int32_t* Tt, int v) {
-  const uint32_t t = (uint32_t)Tt[v];
-  return (t & kExt) ? (int)(t & ~kExt) : (int)(F.lc[d][exit_rank2(F.xr[d], (int)t)] & ~kRes);
 }
 
 template <class T>
@@ -1018,8 +1163,11 @@ __global__ void __launch_bounds__(1024) k_escan(GroupArgs<T> A) {
 
 // One bitmap word per thread; the word's exits (ranks r, r + 1, ...) are
 // handled in batches of kBatch so that their loads are in flight together.
+// An exit's entry comes from its tile terminal (a tile-face vertex: the
+// global index k_label_tile wrote for it): the rank of the exit where its
+// line leaves that tile, or (kRes) the extremum it ends at inside.
 constexpr int kBatch = 8;
-template <class T>
+template <class T, int ND>
 __global__ void __launch_bounds__(kThreads, 6) k_efill(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
   auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_FILL; };
@@ -1035,7 +1183,6 @@ __global__ void __launch_bounds__(kThreads, 6) k_efill(GroupArgs<T> A) {
     tl.enter(A, K_DENSE, i, none, done);
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
-    const bool job = st->ljob != 0;
     const int u = u_ - pre[i];
     const int nw = (F.G.n + 31) >> 5;
     const int w = u * kThreads + threadIdx.x;
@@ -1049,7 +1196,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_efill(GroupArgs<T> A) {
       }
 #pragma unroll
       for (int d = 0; d < 2; ++d) {
-        const int32_t* Tt = d ? (job ? F.Pdn : F.mf) : (job ? F.Pup : F.Mf);
+        const uint32_t* Tt = F.tface[d];
         const uint32_t *ex = F.ex[d], *ep = F.ep[d], *ub = F.ub[d];
         uint32_t* lc = F.lc[d];
         uint32_t r = r2[d];
@@ -1069,7 +1216,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_efill(GroupArgs<T> A) {
             }
           }
 #pragma unroll
-          for (int j = 0; j < kBatch; ++j) t[j] = (e[j] >= 0) ? (uint32_t)Tt[e[j]] : kExt;
+          for (int j = 0; j < kBatch; ++j) t[j] = (e[j] >= 0) ? Tt[e[j]] : kExt;
           // every entry of the batch before any store: a store to the table
           // may alias the bitmap and prefix words as far as the compiler
           // knows, so interleaving them would run the rank loads one by one
@@ -1156,16 +1303,20 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
   tl.flush(A, K_DENSE, pre_flush, done);
 }
 
-// Job 0: f's labels in place of its tile terminals (safe while other threads
-// resolve: a vertex's resolution reads only its own terminal and the exit
-// tables). Job 1, the R-loop check (Sec. 4.2): count wrong
+// Labels from the tile terminals once the exit tables hold labels. Job 0:
+// f's labels into Mf / mf. Job 1, the R-loop check (Sec. 4.2): count wrong
 // labels; a wrongly labelled vertex whose steepest neighbour in g differs
 // from f's is a troublemaker. Wrong max label: decrease its ascending
 // neighbour in g (Eq. 6). Wrong min label: decrease the descending neighbour
-// that f prescribes.
+// that f prescribes. Units are label tiles: a block first looks up the labels
+// of the tile's shell cells that are exits (one (bitmap word, exits before
+// it) load, and one table load per exit), then gives every vertex its labels
+// from its terminals by a shared-memory lookup (or, for a line ending inside
+// the tile, the extremum's index).
 template <class T, int ND>
-__global__ void __launch_bounds__(kThreads, 6) k_rcheck(GroupArgs<T> A) {
-  const int* pre = A.prefix + K_DENSE * (A.nf + 1);
+__global__ void __launch_bounds__(kThreads, 4) k_rcheck(GroupArgs<T> A) {
+  using LG = LabelGeom<ND>;
+  const int* pre = A.prefix + K_LABEL * (A.nf + 1);
   auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_DONE; };
   uint32_t acc[4] = {0, 0, 0, 0};
   auto pre_flush = [&](DevState* st) {
@@ -1177,6 +1328,17 @@ __global__ void __launch_bounds__(kThreads, 6) k_rcheck(GroupArgs<T> A) {
     else ctrl_after_rcheck(st);
     log_work(A);
   };
+  // labels of the tile's shell cells (ascending, descending lines), and the
+  // tile's exit record (which of them its lines leave through)
+  __shared__ uint32_t s_lab[2][LG::SHELL];
+  __shared__ uint32_t s_shx[2 * LabelGeom<ND>::SHW];
+  __shared__ uint32_t s_shell[LG::SHELL];  // shell cells' halo coordinates
+  fill_shell_table<ND>(s_shell);
+  // the tile's exits as bit positions of its record (direction * SHW * 32 +
+  // shell index), and the scan sums that list them
+  __shared__ uint16_t s_xl[2 * LG::SHELL];
+  __shared__ uint32_t s_wsum[kThreads / 32];
+  __shared__ uint32_t s_nxl;
   // Troublemakers whose request freezes a ring: their anchors, marked by
   // the block's warps at the end of the unit (a lane per ring vertex)
   // instead of vertex by vertex in one thread.
@@ -1197,14 +1359,111 @@ __global__ void __launch_bounds__(kThreads, 6) k_rcheck(GroupArgs<T> A) {
   ts.cap = kRStage;
   if (threadIdx.x == 0) s_nfz = s_ntv = 0;
   if (threadIdx.x < 4) s_fzc[threadIdx.x >> 1][threadIdx.x & 1] = 0;
-  __syncthreads();
   UnitTally tl;
-  MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
-    tl.enter(A, K_DENSE, i, pre_flush, done);
+  MSZ_ACTIVE_UNITS(A, K_LABEL, pre, i, active) {
+    tl.enter(A, K_LABEL, i, pre_flush, done);
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
-    const int v0 = (u_ - pre[i]) * kDenseChunk;
-    const int v1 = min(F.G.n, v0 + kDenseChunk);
+    const Geom G = F.G;
+    const int tiles_x = (G.nx + LG::TX - 1) / LG::TX;
+    const int tiles_y = (G.ny + LG::TY - 1) / LG::TY;
+    const int tile = u_ - pre[i];
+    const int x0 = (tile % tiles_x) * LG::TX;
+    const int y0 = ((tile / tiles_x) % tiles_y) * LG::TY;
+    const int z0 = (tile / (tiles_x * tiles_y)) * LG::TZ;
+    constexpr int kShW = LabelGeom<ND>::SHW;
+    __syncthreads();  // the previous tile's tables have been read
+    for (int k = threadIdx.x; k < 2 * kShW; k += kThreads) s_shx[k] = F.texit[(size_t)tile * 2 * kShW + k];
+    __syncthreads();
+    // The tile's exits (the shell cells its lines leave through) listed in
+    // shared memory, then their labels looked up a few per thread with the
+    // loads in flight together, and compared with the tile's snapshot of
+    // them from its last check (R-check only).
+    const bool job = st->ljob != 0;
+    int relabel = 0;
+    {
+      uint32_t bits = threadIdx.x < 2 * kShW ? s_shx[threadIdx.x] : 0u;
+      const uint32_t cnt = (uint32_t)__popc(bits);
+      uint32_t incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if ((threadIdx.x & 31) >= o) incl += y;
+      }
+      if ((threadIdx.x & 31) == 31) s_wsum[threadIdx.x >> 5] = incl;
+      __syncthreads();
+      uint32_t off = incl - cnt;
+      for (int k = 0; k < (int)(threadIdx.x >> 5); ++k) off += s_wsum[k];
+      for (; bits; bits &= bits - 1) s_xl[off++] = (uint16_t)(threadIdx.x * 32 + __ffs(bits) - 1);
+      if (threadIdx.x == kThreads - 1) s_nxl = off;
+      __syncthreads();
+    }
+    const uint32_t nxl = s_nxl;
+    for (uint32_t j0 = threadIdx.x; j0 < nxl; j0 += 4 * kThreads) {
+      int q[4];
+      uint2 p[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t j = j0 + k * kThreads;
+        q[k] = j < nxl ? (int)s_xl[j] : -1;
+        const int d = q[k] >= kShW * 32 ? 1 : 0, s = q[k] - d * kShW * 32;
+        const int e = q[k] >= 0 ? shell_vertex<ND>(G, s_shell, s, x0, y0, z0) : 0;
+        p[k] = F.xr[d][e >> 5];
+        p[k].x &= (1u << (e & 31)) - 1u;
+      }
+      uint32_t lab[4], old[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int d = q[k] >= kShW * 32 ? 1 : 0, s = q[k] - d * kShW * 32;
+        lab[k] = q[k] >= 0 ? F.lc[d][p[k].y + (uint32_t)__popc(p[k].x)] & ~kRes : 0u;
+        old[k] = (q[k] >= 0 && job) ? F.tsnap[((size_t)tile * 2 + d) * LG::SHELL + s] : 0u;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (q[k] < 0) continue;
+        const int d = q[k] >= kShW * 32 ? 1 : 0, s = q[k] - d * kShW * 32;
+        s_lab[d][s] = lab[k];
+        if (job && old[k] != lab[k]) {
+          F.tsnap[((size_t)tile * 2 + d) * LG::SHELL + s] = lab[k];
+          relabel = 1;
+        }
+      }
+    }
+    // A tile whose terminals were not recomputed, whose exits kept their
+    // labels and whose last check found no wrong label has none now: its
+    // vertices' labels and direction bytes are those of that check (any edit
+    // in the tile or its halo would have marked it for recomputation), so
+    // it holds no troublemaker and adds nothing to the counts.
+    const uint8_t tstate = job ? F.tdirty[tile] : 0;
+    const bool examine = __syncthreads_or(relabel) || !job || (tstate & 2) || F.twrong[tile];
+    if (!examine) continue;
+    // label of one terminal half t (direction d) of a vertex of this tile
+    auto label_of = [&](uint32_t t, int d) -> int32_t {
+      return (t & kTermExtr) ? extremum_vertex<ND>(G, t, x0, y0, z0) : (int32_t)s_lab[d][t & kTermIdx];
+    };
+    // kRB vertices per thread and iteration, their loads issued together
+    constexpr int kRB = 4;
+    static_assert(LG::PER_THREAD % kRB == 0, "whole batches");
+    if (!job) {
+      for (int kb = 0; kb < LG::PER_THREAD; kb += kRB) {
+        int vv[kRB];
+        uint32_t tt[kRB];
+#pragma unroll
+        for (int k = 0; k < kRB; ++k) {
+          const int c = threadIdx.x + (kb + k) * kThreads;
+          const int x = x0 + c % LG::TX, y = y0 + (c / LG::TX) % LG::TY, z = z0 + c / (LG::TX * LG::TY);
+          vv[k] = (x < G.nx && y < G.ny && z < G.nz) ? x + G.nx * (y + G.ny * z) : -1;
+          tt[k] = vv[k] >= 0 ? F.term[vv[k]] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kRB; ++k)
+          if (vv[k] >= 0) {
+            F.Mf[vv[k]] = label_of(tt[k] & 0xffffu, 0);
+            F.mf[vv[k]] = label_of(tt[k] >> 16, 1);
+          }
+      }
+      continue;
+    }
     // the request of troublemaker a for target t (Eq. 6); k: 4 for a wrong
     // max label, 5 for a wrong min label
     auto trouble = [&](int a, int t, int k) {
@@ -1218,79 +1477,55 @@ __global__ void __launch_bounds__(kThreads, 6) k_rcheck(GroupArgs<T> A) {
       if (q < kRFreeze) s_fz[q] = (uint32_t)a;
       else request<T, ND>(F, a, t, ts);  // list full: the same freeze, vertex by vertex
     };
-    // kRB vertices per thread and iteration, their loads issued together
-    constexpr int kRB = 4;
-    if (st->ljob == 0) {
-      // every label of the batch before any store, which the compiler could
-      // not move the next loads past
-      int32_t* Mf = F.Mf;
-      int32_t* mf = F.mf;
-      for (int vb = v0 + threadIdx.x; vb < v1; vb += kRB * kThreads) {
-        uint32_t tu[kRB], td[kRB];
-#pragma unroll
-        for (int k = 0; k < kRB; ++k) {
-          const int v = vb + k * kThreads;
-          const bool in = v < v1;
-          tu[k] = in ? (uint32_t)Mf[v] : kExt;
-          td[k] = in ? (uint32_t)mf[v] : kExt;
-        }
-#pragma unroll
-        for (int k = 0; k < kRB; ++k) {
-          tu[k] = (tu[k] & kExt) ? (tu[k] & ~kExt) : (F.lc[0][exit_rank2(F.xr[0], (int)tu[k])] & ~kRes);
-          td[k] = (td[k] & kExt) ? (td[k] & ~kExt) : (F.lc[1][exit_rank2(F.xr[1], (int)td[k])] & ~kRes);
-        }
-#pragma unroll
-        for (int k = 0; k < kRB; ++k) {
-          const int v = vb + k * kThreads;
-          if (v < v1) {
-            Mf[v] = (int32_t)tu[k];
-            mf[v] = (int32_t)td[k];
-          }
-        }
-      }
-      continue;
-    }
-    for (int vb = v0 + threadIdx.x; vb < v1; vb += kRB * kThreads) {
-      uint32_t tu[kRB], td[kRB];
+    uint32_t any_wrong = 0;
+    for (int kb = 0; kb < LG::PER_THREAD; kb += kRB) {
+      int vv[kRB];
+      uint32_t tt[kRB];
       int32_t M[kRB], m[kRB];
 #pragma unroll
       for (int k = 0; k < kRB; ++k) {
-        const int v = vb + k * kThreads;
-        const bool in = v < v1;
-        tu[k] = in ? (uint32_t)F.Pup[v] : kExt;
-        td[k] = in ? (uint32_t)F.Pdn[v] : kExt;
-        M[k] = in ? F.Mf[v] : 0;
-        m[k] = in ? F.mf[v] : 0;
-      }
-#pragma unroll
-      for (int k = 0; k < kRB; ++k) {
-        tu[k] = (tu[k] & kExt) ? (tu[k] & ~kExt) : (F.lc[0][exit_rank2(F.xr[0], (int)tu[k])] & ~kRes);
-        td[k] = (td[k] & kExt) ? (td[k] & ~kExt) : (F.lc[1][exit_rank2(F.xr[1], (int)td[k])] & ~kRes);
+        const int c = threadIdx.x + (kb + k) * kThreads;
+        const int x = x0 + c % LG::TX, y = y0 + (c / LG::TX) % LG::TY, z = z0 + c / (LG::TX * LG::TY);
+        vv[k] = (x < G.nx && y < G.ny && z < G.nz) ? x + G.nx * (y + G.ny * z) : -1;
+        const bool in = vv[k] >= 0;
+        tt[k] = in ? F.term[vv[k]] : 0u;
+        M[k] = in ? F.Mf[vv[k]] : 0;
+        m[k] = in ? F.mf[vv[k]] : 0;
       }
       uint32_t wrong = 0;  // bit 2k: max label wrong, bit 2k+1: min label wrong
 #pragma unroll
       for (int k = 0; k < kRB; ++k)
-        if (vb + k * kThreads < v1)
-          wrong |= ((uint32_t)((int32_t)tu[k] != M[k]) << (2 * k)) | ((uint32_t)((int32_t)td[k] != m[k]) << (2 * k + 1));
+        if (vv[k] >= 0)
+          wrong |= ((uint32_t)(label_of(tt[k] & 0xffffu, 0) != M[k]) << (2 * k)) |
+                   ((uint32_t)(label_of(tt[k] >> 16, 1) != m[k]) << (2 * k + 1));
+      any_wrong |= wrong;
       for (; wrong; wrong &= wrong - 1) {
-        const int bit = __ffs(wrong) - 1, v = vb + (bit >> 1) * kThreads;
+        const int bit = __ffs(wrong) - 1;
+        int v = vv[0];  // vv[bit >> 1], selected without indexing the array
+#pragma unroll
+        for (int k = 1; k < kRB; ++k)
+          if ((bit >> 1) == k) v = vv[k];
         const uint8_t d = F.gdir[v], fd = F.fdir[v];
         if ((bit & 1) == 0) {
           ++acc[0];
           if ((d & 15) != (fd & 15)) {
             ++acc[2];
-            trouble(v, v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny), 4);
+            trouble(v, v + slot_offset(d & 15, ND, G.nx, G.nxny), 4);
           }
         } else {
           ++acc[1];
           if ((d >> 4) != (fd >> 4)) {
             ++acc[3];
-            trouble(v, v + slot_offset(fd >> 4, ND, F.G.nx, F.G.nxny), 5);
+            trouble(v, v + slot_offset(fd >> 4, ND, G.nx, G.nxny), 5);
           }
         }
       }
     }
-    __syncthreads();
+    const int tile_wrong = __syncthreads_or(any_wrong != 0u);
+    if (threadIdx.x == 0) {
+      F.twrong[tile] = (uint8_t)tile_wrong;
+      if (tstate & 2) F.tdirty[tile] = 0;
+    }
     if (threadIdx.x < 4) {
       // k: wrong max / min label; c: 0 target frozen, 1 target at its bound
       const int k = threadIdx.x >> 1, c = threadIdx.x & 1;
@@ -1321,7 +1556,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_rcheck(GroupArgs<T> A) {
       __syncthreads();  // the buffer is free for the next unit
     }
   }
-  tl.flush(A, K_DENSE, pre_flush, done);
+  tl.flush(A, K_LABEL, pre_flush, done);
 }
 
 // Applies the flags of touched vertex u: a freeze sets g = f and freezes u
