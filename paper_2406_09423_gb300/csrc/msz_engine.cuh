@@ -103,9 +103,6 @@ struct Field {
   int32_t* Pdn;
   uint32_t* term; // tile terminals (kTermFlag form) of the current evaluation; Pup's memory
                   // (the outputs are written only at emission)
-  uint32_t* tface[2];  // per direction, at tile-face vertices (the only possible tile exits): the
-                       // global index of the tile terminal, kExt-flagged for an extremum; [0] is
-                       // Pdn's memory
   // per direction (0: ascending lines / max labels, 1: descending / min)
   uint32_t* ex[2];  // bitmap of tile-exit vertices
   uint32_t* ep[2];  // per bitmap word: exits before it within its dense unit

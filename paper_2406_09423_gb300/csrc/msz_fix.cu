@@ -146,7 +146,6 @@ struct FieldBufs {
   uint32_t* texit = nullptr;
   uint32_t* tsnap = nullptr;
   uint8_t* twrong = nullptr;
-  uint32_t* tface1 = nullptr;
   uint8_t* cls = nullptr;
   uint32_t* cases = nullptr;
   uint32_t* epoch = nullptr;
@@ -190,7 +189,6 @@ void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs
   B.texit = (uint32_t*)b.take((size_t)label_tiles(G) * 2 * (G.nd == 3 ? LabelGeom<3>::SHW : LabelGeom<2>::SHW) * 4);
   B.tsnap = (uint32_t*)b.take((size_t)label_tiles(G) * 2 * (G.nd == 3 ? LabelGeom<3>::SHELL : LabelGeom<2>::SHELL) * 4);
   B.twrong = (uint8_t*)b.take((size_t)label_tiles(G));
-  B.tface1 = (uint32_t*)b.take(n * 4);
   B.cls = (uint8_t*)b.take(nt * kEmitTile);
   B.cases = (uint32_t*)b.take(n * 4);
   B.epoch = (uint32_t*)b.take(n * 4);
@@ -317,8 +315,6 @@ struct Group {
       F.Pup = B.Pup;
       F.Pdn = B.Pdn;
       F.term = reinterpret_cast<uint32_t*>(B.Pup);
-      F.tface[0] = reinterpret_cast<uint32_t*>(B.Pdn);
-      F.tface[1] = B.tface1;
       for (int d = 0; d < 2; ++d) {
         F.ex[d] = B.ex[d];
         F.ep[d] = B.ep[d];

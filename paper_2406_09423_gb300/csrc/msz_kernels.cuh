@@ -37,6 +37,31 @@ struct LabelGeom {
   static_assert(HALO <= 0x4000 && TV <= 0x4000, "pointers, indices and the terminal flags share 16 bits");
 };
 
+// The cells of a label tile that one thread owns: cell i = threadIdx.x +
+// k kThreads for k < PER_THREAD. kThreads is a multiple of TX, so the thread
+// keeps its x and each step moves it by RS = kThreads / TX rows (in 3D a
+// whole plane, RS = TY): its halo index is c0 + k HSTEP, its vertex index
+// v0 + k VSTEP, with no per-cell index arithmetic.
+template <int ND>
+struct CellWalk {
+  using LG = LabelGeom<ND>;
+  static constexpr int RS = kThreads / LG::TX;
+  static_assert(kThreads % LG::TX == 0 && (ND == 3 ? RS == LG::TY : RS * LG::PER_THREAD == LG::TY),
+                "a thread's cells are whole rows or planes apart");
+  static constexpr int HSTEP = (ND == 3) ? LG::SX * LG::SY : RS * LG::SX;
+  int lx, r0;  // the thread's x in the tile, its first row
+  __device__ __forceinline__ CellWalk() : lx((int)threadIdx.x % LG::TX), r0((int)threadIdx.x / LG::TX) {}
+  __device__ __forceinline__ int ly(int k) const { return (ND == 3) ? r0 : r0 + k * RS; }
+  __device__ __forceinline__ int lz(int k) const { return (ND == 3) ? k : 0; }
+  __device__ __forceinline__ int c0() const { return (lx + 1) + LG::SX * (r0 + 1) + ((ND == 3) ? LG::SX * LG::SY : 0); }
+  // vertex index step between the thread's cells
+  __device__ __forceinline__ int vstep(const Geom& G) const { return (ND == 3) ? G.nxny : RS * G.nx; }
+  // whether step k of the tile at (x0, y0, z0) lies inside the grid
+  __device__ __forceinline__ bool inside(const Geom& G, int x0, int y0, int z0, int k) const {
+    return x0 + lx < G.nx && y0 + ly(k) < G.ny && z0 + lz(k) < G.nz;
+  }
+};
+
 // Tile terminals (k_label_tile's output, one 32-bit word per vertex): the
 // ascending terminal in the low 16 bits, the descending one in the high 16.
 // Every terminal half has kTermFlag set. With kTermExtr also set, the low 14
@@ -846,8 +871,6 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
   // the same exits by shell index (the tile's record for the label lookups)
   constexpr int kShW = LabelGeom<ND>::SHW;
   __shared__ uint32_t shx[2][kShW];
-  __shared__ uint32_t s_shell[LG::SHELL];  // shell cells' halo coordinates
-  fill_shell_table<ND>(s_shell);
   auto active = [](const Field<T>& F) {
     return F.st->action == ACT_LABELS && F.st->lstate == L_INIT && (F.st->ljob != 0) == JOB;
   };
@@ -894,15 +917,17 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
     // integral line is the steepest neighbour of the line's last tile cell,
     // so the marked cells are exactly the exits of the tile's lines.
     uint32_t live = 0;
+    const CellWalk<ND> cw;
+    const int hc0 = cw.c0(), vs = cw.vstep(G);
+    const int v0 = (x0 + cw.lx) + G.nx * ((y0 + cw.ly(0)) + G.ny * (z0 + cw.lz(0)));
 #pragma unroll
     for (int k = 0; k < LG::PER_THREAD; ++k) {
-      const int i = threadIdx.x + k * kThreads;
-      const int lx = i % LG::TX, ly = (i / LG::TX) % LG::TY, lz = i / (LG::TX * LG::TY);
-      const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-      if (x >= G.nx || y >= G.ny || z >= G.nz) continue;
+      if (!cw.inside(G, x0, y0, z0, k)) continue;
       live |= 1u << k;
-      const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
-      const int v = x + G.nx * (y + G.ny * z);
+      const int i = threadIdx.x + k * kThreads;
+      const int lx = cw.lx, ly = cw.ly(k), lz = cw.lz(k);
+      const int c = hc0 + k * CellWalk<ND>::HSTEP;
+      const int v = v0 + k * vs;
       uint32_t db;
       if (!job) {
         db = halo_dir<T, ND>(val, c);
@@ -944,9 +969,7 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
 #pragma unroll
       for (int k = 0; k < LG::PER_THREAD; ++k) {
         if (!((live >> k) & 1u)) continue;
-        const int i = threadIdx.x + k * kThreads;
-        const int lx = i % LG::TX, ly = (i / LG::TX) % LG::TY, lz = i / (LG::TX * LG::TY);
-        const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
+        const int c = hc0 + k * CellWalk<ND>::HSTEP;
         const uint32_t p = PP[c];
         const uint32_t a = p & 0xffffu, b = p >> 16;
         const uint32_t a2 = double_half(PP, a, true);
@@ -958,26 +981,11 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < LG::PER_THREAD; ++k) {
-      const int i = threadIdx.x + k * kThreads;
-      const int lx = i % LG::TX, ly = (i / LG::TX) % LG::TY, lz = i / (LG::TX * LG::TY);
-      const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-      if (x < G.nx && y < G.ny && z < G.nz) {
-        const int v = x + G.nx * (y + G.ny * z);
-        const uint32_t p = PP[(lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0)];
+      if (cw.inside(G, x0, y0, z0, k)) {
+        const int lx = cw.lx, ly = cw.ly(k), lz = cw.lz(k);
+        const int v = v0 + k * vs;
+        const uint32_t p = PP[hc0 + k * CellWalk<ND>::HSTEP];
         F.term[v] = p;
-        // a face cell can be another tile's exit: its terminals as global
-        // indices for the exit table
-        const bool face = lx == 0 || lx == LG::TX - 1 || ly == 0 || ly == LG::TY - 1 ||
-                          (ND == 3 && (lz == 0 || lz == LG::TZ - 1));
-        if (face) {
-#pragma unroll
-          for (int d = 0; d < 2; ++d) {
-            const uint32_t t = (p >> (16 * d)) & 0xffffu;
-            F.tface[d][v] = (t & kTermExtr)
-                                ? ((uint32_t)extremum_vertex<ND>(G, t, x0, y0, z0) | kExt)
-                                : (uint32_t)shell_vertex<ND>(G, s_shell, (int)(t & kTermIdx), x0, y0, z0);
-          }
-        }
       }
     }
     // the tile's exit record
@@ -1011,14 +1019,9 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
       cp_async_wait_all();
       __syncthreads();
 #pragma unroll
-      for (int k = 0; k < LG::PER_THREAD; ++k) {
-        const int i = threadIdx.x + k * kThreads;
-        const int lx = i % LG::TX, ly = (i / LG::TX) % LG::TY, lz = i / (LG::TX * LG::TY);
-        const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-        if (x >= G.nx || y >= G.ny || z >= G.nz) continue;
-        const int c = (lx + 1) + HS * (ly + 1) + ((ND == 3) ? HSS * (lz + 1) : 0);
-        F.gdir[x + G.nx * (y + G.ny * z)] = (uint8_t)halo_dir<T, ND>(val, c);
-      }
+      for (int k = 0; k < LG::PER_THREAD; ++k)
+        if (cw.inside(G, x0, y0, z0, k))
+          F.gdir[v0 + k * vs] = (uint8_t)halo_dir<T, ND>(val, hc0 + k * CellWalk<ND>::HSTEP);
     }
     // recomputed, for the R-check to examine (f's pass leaves every tile
     // dirty for g's first)
@@ -1163,13 +1166,17 @@ __global__ void __launch_bounds__(1024) k_escan(GroupArgs<T> A) {
 
 // One bitmap word per thread; the word's exits (ranks r, r + 1, ...) are
 // handled in batches of kBatch so that their loads are in flight together.
-// An exit's entry comes from its tile terminal (a tile-face vertex: the
-// global index k_label_tile wrote for it): the rank of the exit where its
-// line leaves that tile, or (kRes) the extremum it ends at inside.
-constexpr int kBatch = 8;
+// An exit's entry comes from its own tile terminal, decoded against its
+// tile's origin (the word's row gives the coordinates; the shell cells'
+// halo coordinates come from a shared table): the rank of the exit where
+// its line leaves that tile, or (kRes) the extremum it ends at inside.
+constexpr int kBatch = 4;
 template <class T, int ND>
 __global__ void __launch_bounds__(kThreads, 6) k_efill(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
+  __shared__ uint32_t s_shell[LabelGeom<ND>::SHELL];
+  fill_shell_table<ND>(s_shell);
+  __syncthreads();
   auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_FILL; };
   auto none = [](DevState*) {};
   auto done = [&](DevState* st) {
@@ -1188,6 +1195,8 @@ __global__ void __launch_bounds__(kThreads, 6) k_efill(GroupArgs<T> A) {
     const int w = u * kThreads + threadIdx.x;
     uint32_t nex = 0;
     if (w < nw) {
+      int xw, yw, zw;
+      coords(F.G, w << 5, xw, yw, zw);
       uint32_t m2[2], r2[2];  // both directions' words, loaded before any table store
 #pragma unroll
       for (int d = 0; d < 2; ++d) {
@@ -1196,7 +1205,6 @@ __global__ void __launch_bounds__(kThreads, 6) k_efill(GroupArgs<T> A) {
       }
 #pragma unroll
       for (int d = 0; d < 2; ++d) {
-        const uint32_t* Tt = F.tface[d];
         const uint32_t *ex = F.ex[d], *ep = F.ep[d], *ub = F.ub[d];
         uint32_t* lc = F.lc[d];
         uint32_t r = r2[d];
@@ -1216,7 +1224,19 @@ __global__ void __launch_bounds__(kThreads, 6) k_efill(GroupArgs<T> A) {
             }
           }
 #pragma unroll
-          for (int j = 0; j < kBatch; ++j) t[j] = (e[j] >= 0) ? Tt[e[j]] : kExt;
+          for (int j = 0; j < kBatch; ++j) t[j] = (e[j] >= 0) ? (F.term[e[j]] >> (16 * d)) & 0xffffu : 0u;
+#pragma unroll
+          for (int j = 0; j < kBatch; ++j) {
+            uint32_t g = kExt;
+            if (j < c) {
+              int x = xw + (e[j] - (w << 5)), y = yw, z = zw, x0, y0, z0;
+              if (x >= F.G.nx) coords(F.G, e[j], x, y, z);
+              tile_origin_of<ND>(x, y, z, x0, y0, z0);
+              g = (t[j] & kTermExtr) ? ((uint32_t)extremum_vertex<ND>(F.G, t[j], x0, y0, z0) | kExt)
+                                     : (uint32_t)shell_vertex<ND>(F.G, s_shell, (int)(t[j] & kTermIdx), x0, y0, z0);
+            }
+            t[j] = g;
+          }
           // every entry of the batch before any store: a store to the table
           // may alias the bitmap and prefix words as far as the compiler
           // knows, so interleaving them would run the rank loads one by one
@@ -1444,15 +1464,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_rcheck(GroupArgs<T> A) {
     // kRB vertices per thread and iteration, their loads issued together
     constexpr int kRB = 4;
     static_assert(LG::PER_THREAD % kRB == 0, "whole batches");
+    const CellWalk<ND> cw;
+    const int vs = cw.vstep(G);
+    const int v0 = (x0 + cw.lx) + G.nx * ((y0 + cw.ly(0)) + G.ny * (z0 + cw.lz(0)));
     if (!job) {
+#pragma unroll
       for (int kb = 0; kb < LG::PER_THREAD; kb += kRB) {
         int vv[kRB];
         uint32_t tt[kRB];
 #pragma unroll
         for (int k = 0; k < kRB; ++k) {
-          const int c = threadIdx.x + (kb + k) * kThreads;
-          const int x = x0 + c % LG::TX, y = y0 + (c / LG::TX) % LG::TY, z = z0 + c / (LG::TX * LG::TY);
-          vv[k] = (x < G.nx && y < G.ny && z < G.nz) ? x + G.nx * (y + G.ny * z) : -1;
+          vv[k] = cw.inside(G, x0, y0, z0, kb + k) ? v0 + (kb + k) * vs : -1;
           tt[k] = vv[k] >= 0 ? F.term[vv[k]] : 0u;
         }
 #pragma unroll
@@ -1478,15 +1500,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_rcheck(GroupArgs<T> A) {
       else request<T, ND>(F, a, t, ts);  // list full: the same freeze, vertex by vertex
     };
     uint32_t any_wrong = 0;
+#pragma unroll 1
     for (int kb = 0; kb < LG::PER_THREAD; kb += kRB) {
       int vv[kRB];
       uint32_t tt[kRB];
       int32_t M[kRB], m[kRB];
 #pragma unroll
       for (int k = 0; k < kRB; ++k) {
-        const int c = threadIdx.x + (kb + k) * kThreads;
-        const int x = x0 + c % LG::TX, y = y0 + (c / LG::TX) % LG::TY, z = z0 + c / (LG::TX * LG::TY);
-        vv[k] = (x < G.nx && y < G.ny && z < G.nz) ? x + G.nx * (y + G.ny * z) : -1;
+        vv[k] = cw.inside(G, x0, y0, z0, kb + k) ? v0 + (kb + k) * vs : -1;
         const bool in = vv[k] >= 0;
         tt[k] = in ? F.term[vv[k]] : 0u;
         M[k] = in ? F.Mf[vv[k]] : 0;
