@@ -135,10 +135,10 @@ def kernel_bytes(name, st, n, es):
     kernels whose traffic is dominated by scattered L2 accesses:
     k_csweep      the stencil sweep's minimum: g (es) and f's direction byte
                   read, one byte of g's classification written per vertex;
-    k_label_tile  g's direction byte read + two tile terminals (8) written per
-                  vertex of the tiles recomputed (f's evaluation, once per fix,
-                  also reads f and g and writes both direction bytes: not
-                  counted);
+    k_label_tile  g's direction byte read + the packed tile terminals (4)
+                  written per vertex of the tiles recomputed (f's evaluation,
+                  once per fix, also reads f and g and writes both direction
+                  bytes: not counted);
     k_ecount      per bitmap word: two exit-bitmap words read, two prefix
                   words written (16);
     k_efill       bitmaps and prefixes read, (bitmap word, prefix) pairs
@@ -146,14 +146,15 @@ def kernel_bytes(name, st, n, es):
                   written (8) per exit;
     k_jump        4 bytes per exit-table access (entry read; gather and write
                   of the entries still holding a rank);
-    k_rcheck      the R-check's minimum: four label words (16), both
-                  direction bytes (2) read and one request byte written (1)
-                  per vertex."""
+    k_rcheck      counted by the kernel (its units are bytes): per exit label
+                  looked up, the (bitmap word, prefix) pair, the table entry
+                  and the tile's snapshot of it (16); per vertex of the tiles
+                  it examines, the terminal word and f's two labels (12)."""
     u, w = st["units"], st["work_launches"]
     if name == "k_csweep":
         return u * (es + 2)
     if name == "k_label_tile":
-        return u * 9
+        return u * 5
     if name == "k_ecount":
         return u * 16
     if name == "k_efill":
@@ -161,7 +162,7 @@ def kernel_bytes(name, st, n, es):
     if name == "k_jump":
         return u * 4
     if name == "k_rcheck":
-        return u * 19
+        return u
     return None
 
 
@@ -340,8 +341,10 @@ def edit_coding(torch, msz, stream, f, fh, xi, r):
 def run_batched(torch, msz, dev, count=64):
     """Batched form: 64 fields of uneven sizes (2D sides 64..1024, 3D sides
     32..192; float32 for even i, float64 for odd i; xi log-uniform in
-    [1e-5, 1e-3] x range; seeds 100..163) in one batch, against the same
-    fields corrected one at a time. Both forms give identical results."""
+    [1e-5, 1e-3] x range; seeds 100..163) in one batch, timed under the
+    default launch parameters and under those the autotuner picks on these
+    fields, against the same fields corrected one at a time. Every form gives
+    identical results."""
     from paper_2406_09423_gb300 import synth
 
     fields = list(synth.batch_fields(count, 100))
@@ -350,15 +353,24 @@ def run_batched(torch, msz, dev, count=64):
     xis = [x for _, _, x in fields]
     n = sum(f.numel() for f in fs)
     b = msz.Batch([f.shape for f in fs], [f.dtype for f in fs])
-    b.fix(fs, hs, xis, copy=False)  # warm-up (graph capture)
-    times = []
-    for _ in range(2):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        st, res = b.fix(fs, hs, xis, copy=False)
-        torch.cuda.synchronize()
-        times.append(time.perf_counter() - t)
-    assert st == 0
+
+    def timed_batch():
+        b.fix(fs, hs, xis, copy=False)  # warm-up (graph capture)
+        times = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            st, res = b.fix(fs, hs, xis, copy=False)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t)
+        assert st == 0
+        return min(times), res
+
+    t_default, _ = timed_batch()
+    t0 = time.perf_counter()
+    tuned, tried = b.autotune(fs, hs, xis, force=True)
+    t_autotune = time.perf_counter() - t0
+    tb, res = timed_batch()
     plans = [msz.Plan(f.shape, f.dtype) for f in fs]
     for p, f, h, x in zip(plans, fs, hs, xis):  # warm-up
         p.fix(f, h, x, copy=False)
@@ -371,10 +383,12 @@ def run_batched(torch, msz, dev, count=64):
     for p in plans:
         p.close()
     b.close()
-    tb = min(times)
     return {"fields": count, "vertices": n, "batched_s": tb, "batched_mvps": n / tb / 1e6,
             "plain_s": t_plain, "plain_mvps": n / t_plain / 1e6, "speedup": t_plain / tb,
-            "identical_to_plain": bool(same), "max_sweeps": max(r.counts["sweeps"] for r in res)}
+            "identical_to_plain": bool(same), "max_sweeps": max(r.counts["sweeps"] for r in res),
+            "default_tuning_s": t_default, "default_tuning_mvps": n / t_default / 1e6,
+            "tuning": tuned, "tuning_default": msz.native.msz_tuning_default(), "autotune_settings_timed": tried,
+            "autotune_s": t_autotune}
 
 
 def run_served(torch, msz, dev, arrivals=300, rate=200.0, pool=8, budget_gb=60.0):

@@ -90,10 +90,32 @@ typedef struct {
 typedef struct {
   uint64_t max_rounds;   /* cap on C + R edit rounds; 0 = default (10^7). A fix that applies
                             round max_rounds + 1 stops there with MSZ_ERR_NOCONVERGE */
-  int32_t  label_tile;   /* reserved, 0 = automatic */
+  int32_t  autotune;     /* batches: nonzero = the first msz_batch_fix first runs
+                            msz_batch_autotune on its inputs (plans: ignored) */
   uint32_t flags;        /* MSZ_OPT_* bits */
   int32_t  reserved[6];
 } msz_options;
+
+/* Launch parameters of the correction loop (no counterpart in the paper:
+ * they decide how the work is scheduled on the GPU, never what is computed;
+ * every valid setting gives bit-identical results). */
+typedef struct {
+  int32_t jumps_per_step;  /* label propagation launches per loop step, 1-4 (default 2) */
+  int32_t chase_steps;     /* exit-table steps an entry follows per propagation launch, 4-256 (32) */
+  int32_t small_rounds;    /* C-loop rounds one thread-block cluster launch may run, 0-1024; 0 = every
+                              round on the grid kernels (64) */
+  int32_t small_cases;     /* largest round (cases) the cluster takes, 1-65536 (65536) */
+  int32_t graph_steps;     /* loop steps per captured CUDA graph, 1-8 (4) */
+  int32_t sweep_chunk;     /* planes per tile of the full classification sweep, 4-64 (64) */
+  int32_t blocks_per_sm;   /* blocks per SM of the grid-wide kernels, at most their occupancy;
+                              0 = their occupancy (0) */
+  int32_t reserved[5];     /* zero */
+} msz_tuning;
+
+/* Fills *t with the defaults above. */
+void msz_tuning_default(msz_tuning* t);
+/* MSZ_OK if every field of *t is in range, else MSZ_ERR_ARG (host only). */
+int msz_tuning_valid(const msz_tuning* t);
 
 /* Results of msz_fix / msz_fix_host. For msz_fix the arrays are DEVICE
  * memory owned by the plan: valid until the next msz_fix on that plan or
@@ -131,8 +153,10 @@ int msz_plan_destroy(msz_plan p);
  * launch of a loop step is bracketed by CUDA events; a launch "works" when it
  * completes a stage of the field's state machine (the others find the field
  * in another stage and return at once). units counts the work of the working
- * launches: vertices (k_csweep, k_rcheck, k_label_tile: vertices of the tiles
- * recomputed), bitmap words (k_ecount), exits (k_efill), exit-table
+ * launches: vertices (k_csweep; k_label_tile: vertices of the tiles
+ * recomputed), algorithmic bytes (k_rcheck: 16 per exit label looked up,
+ * 12 per vertex of the tiles examined), bitmap words (k_ecount), exits
+ * (k_efill), exit-table
  * accesses (k_jump), fields (k_escan), cases (k_gather, k_mark),
  * touched vertices (k_apply), ring items (k_reclass), C-loop rounds run
  * whole in one thread-block cluster per field (k_csmall: requests, apply and
@@ -190,6 +214,27 @@ int msz_batch_create(msz_batch* out, int n, const int* ndim, const int64_t* dims
 int msz_batch_fix(msz_batch b, const void* const* orig_dev, const void* const* decomp_dev, const double* xi,
                   void* stream, msz_result* results);
 int msz_batch_destroy(msz_batch b);
+
+/* Launch parameters of a batch (or plan): set (validated; takes effect at
+ * the next fix) and read. */
+int msz_batch_set_tuning(msz_batch b, const msz_tuning* t);
+int msz_batch_get_tuning(msz_batch b, msz_tuning* t);
+int msz_plan_set_tuning(msz_plan p, const msz_tuning* t);
+int msz_plan_get_tuning(msz_plan p, msz_tuning* t);
+
+/* Autotuner of the batched form: times the batch on these inputs under the
+ * current launch parameters and under candidates for one parameter at a time
+ * (coordinate descent over jumps_per_step, chase_steps, small_rounds,
+ * small_cases, graph_steps, sweep_chunk, blocks_per_sm; two timed fixes per
+ * candidate, the faster counts), keeps a candidate only when it is faster by
+ * more than 2%, and applies the best setting to the batch. The result is
+ * cached for the process under a signature of the batch (per field: dtype,
+ * dimension and log2 of the vertex count); a batch with a cached signature
+ * takes the cached setting without timing unless force is nonzero. *out
+ * receives the applied setting, *tried (nullable) the number of settings
+ * timed. Results of later fixes are identical to untuned ones. */
+int msz_batch_autotune(msz_batch b, const void* const* orig_dev, const void* const* decomp_dev, const double* xi,
+                       int force, void* stream, msz_tuning* out, int* tried);
 
 /* Served form: continuous batching. A worker thread owned by the server
  * admits submitted fields while slots (max_slots) and device memory

@@ -84,11 +84,28 @@ class Batch:
     together (msz_batch_create / msz_batch_fix); each result equals msz_fix
     on that field alone."""
 
-    def __init__(self, shapes, dtypes, max_rounds: int = 0, use_tma: bool = True, flags: int = 0):
+    def __init__(self, shapes, dtypes, max_rounds: int = 0, use_tma: bool = True, flags: int = 0,
+                 autotune: bool = False):
         self.shapes = [tuple(int(v) for v in s_) for s_ in shapes]
         self.dtypes = list(dtypes)
         flags |= 0 if use_tma else native.MSZ_OPT_NO_TMA
-        self._b = native.msz_batch_create(self.shapes, self.dtypes, max_rounds, flags)
+        self._b = native.msz_batch_create(self.shapes, self.dtypes, max_rounds, flags, autotune)
+
+    def autotune(self, fs, fhats, xis, force: bool = False):
+        """msz_batch_autotune on these inputs: (applied tuning, settings timed)."""
+        torch = _torch()
+        fs = [f.contiguous() for f in fs]
+        fhats = [h.contiguous() for h in fhats]
+        return native.msz_batch_autotune(self._b, [f.data_ptr() for f in fs], [h.data_ptr() for h in fhats], xis,
+                                         force, torch.cuda.current_stream().cuda_stream)
+
+    @property
+    def tuning(self) -> dict:
+        return native.msz_get_tuning(self._b)
+
+    @tuning.setter
+    def tuning(self, d: dict):
+        native.msz_set_tuning(self._b, d)
 
     def fix(self, fs, fhats, xis, copy: bool = True):
         torch = _torch()
@@ -199,6 +216,14 @@ class Plan:
         if check:
             native.check(r.status, "msz_fix")
         return _result(torch, r, self.shape, f.dtype, copy)
+
+    @property
+    def tuning(self) -> dict:
+        return native.msz_get_tuning(self._p, plan=True)
+
+    @tuning.setter
+    def tuning(self, d: dict):
+        native.msz_set_tuning(self._p, d, plan=True)
 
     def kernel_stats(self) -> list[dict]:
         """Per-kernel launches, device times and work units of the last fix

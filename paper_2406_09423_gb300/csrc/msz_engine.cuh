@@ -140,6 +140,11 @@ struct GroupArgs {
   // block completing a field's work sets bit `slot` of steplog[step].
   uint32_t* steplog;
   int step, slot;
+  // launch parameters (msz_tuning): exit-table steps an entry follows per
+  // k_jump launch; C-loop rounds a k_csmall launch may run and the largest
+  // round (cases) it takes
+  int chase, small_rounds;
+  uint32_t small_cases;
 };
 
 // ---------------------------------------------------------------------------

@@ -259,10 +259,10 @@ struct Group {
     d_maps = (CUtensorMap*)b.take(sizeof(CUtensorMap) * 2 * std::max(nf, 1), 128);
   }
 
-  static SweepTiling tiling(const Geom& G) {
+  static SweepTiling tiling(const Geom& G, int max_chunk) {
     SweepTiling TL;
     const int axis = (ND == 3) ? G.nz : G.ny;  // marching axis
-    const int nchunks = (axis + 63) / 64;
+    const int nchunks = (axis + max_chunk - 1) / max_chunk;
     TL.chunk = (axis + nchunks - 1) / nchunks;
     TL.chunk += (4 - TL.chunk % 3) % 3;  // chunk + 2 planes per tile must be a multiple of 3
     TL.chunks = (axis + TL.chunk - 1) / TL.chunk;
@@ -296,7 +296,7 @@ struct Group {
   }
 
   // Builds descriptors, tensor maps, prefix sums and launch shapes.
-  int setup(const Geom* geoms, const FieldBufs* bufs, DevState* d_states, bool allow_tma) {
+  int setup(const Geom* geoms, const FieldBufs* bufs, DevState* d_states, bool allow_tma, const msz_tuning& tn) {
     std::memset(h_maps, 0, sizeof(CUtensorMap) * 2 * nf);
     std::memset(h_prefix, 0, sizeof(int) * NKIND * (nf + 1));
     tma = allow_tma;
@@ -336,7 +336,7 @@ struct Group {
       F.edit_val = (T*)B.edit_val;
       F.st = d_states + fi;
       F.G = G;
-      F.TL = tiling(G);
+      F.TL = tiling(G, tn.sweep_chunk);
       F.units[K_DENSE] = (G.n + kDenseChunk - 1) / kDenseChunk;
       F.units[K_SWEEP] = F.TL.ntiles;
       F.units[K_LABEL] = label_tiles(G);
@@ -353,11 +353,17 @@ struct Group {
     args.nf = nf;
     for (int k = 0; k < NKIND; ++k) args.total[k] = h_prefix[k * (nf + 1) + nf];
     // launch shapes: persistent grids over units
+    args.chase = tn.chase_steps;
+    args.small_rounds = tn.small_rounds;
+    args.small_cases = (uint32_t)tn.small_cases;
     const int sms = num_sms();
+    // persistent grids: the kernel's occupancy (or fewer blocks per SM, as
+    // the tuning asks) times the SMs, at most one block per unit
     auto occ_grid = [&](const void* fn, int threads, size_t smem, int units) {
       int occ = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
       if (occ < 1) occ = 1;
+      if (tn.blocks_per_sm > 0) occ = std::min(occ, tn.blocks_per_sm);
       return std::max(1, std::min(units, occ * sms));
     };
     grid[K_DENSE] = occ_grid((const void*)k_jump<T>, kThreads, 0, args.total[K_DENSE]);
@@ -414,9 +420,8 @@ struct Group {
   }
 
   // csweep, (gather, csmall, mark, apply, reclass), gather, mark, label_tile
-  // (f's, g's), ecount, escan, efill, jump x kJumpsPerStep, rcheck, apply,
-  // reclass
-  int launches_per_step() const { return empty() ? 0 : kStepSlots; }
+  // (f's, g's), ecount, escan, efill, jump x jumps, rcheck, apply, reclass
+  int launches_per_step(int jumps) const { return empty() ? 0 : 16 + jumps; }
 
   void init(cudaStream_t s) {
     if (empty()) return;
@@ -427,7 +432,7 @@ struct Group {
   // Kernel timing (single-field plans with MSZ_OPT_TIME_KERNELS): e holds
   // kStepEvents events, one before each launch and one after the last; each
   // launch gets the step's log slot.
-  void step(cudaStream_t s, cudaEvent_t* e = nullptr, uint32_t* steplog = nullptr, int si = 0) {
+  void step(cudaStream_t s, int jumps, cudaEvent_t* e = nullptr, uint32_t* steplog = nullptr, int si = 0) {
     if (empty()) return;
     int slot = 0;
     auto a = [&]() {
@@ -445,7 +450,7 @@ struct Group {
     gather(s, a, true);
     tail(s, a);
     gather(s, a, false);
-    labels(s, a);
+    labels(s, a, jumps);
     tail(s, a);
     if (e) cudaEventRecord(e[slot], s);
   }
@@ -461,18 +466,18 @@ struct Group {
     k_gather<T, ND><<<grid[K_CASE], kThreads, 0, s>>>(a());
     if (small) {
       const GroupArgs<T> x = a();  // the slot counts even when the kernel is left out
-      if (small_ok) k_csmall<T, ND><<<nf * kSmallCluster, kSmallThreads, 0, s>>>(x);
+      if (small_ok && args.small_rounds > 0) k_csmall<T, ND><<<nf * kSmallCluster, kSmallThreads, 0, s>>>(x);
     }
     k_mark<T, ND><<<grid[K_SPARSE], kThreads, 0, s>>>(a());
   }
   template <class A>
-  void labels(cudaStream_t s, A&& a) {
+  void labels(cudaStream_t s, A&& a, int jumps) {
     k_label_tile<T, ND, false><<<grid_label[0], kThreads, label_smem[0], s>>>(a());
     k_label_tile<T, ND, true><<<grid_label[1], kThreads, label_smem[1], s>>>(a());
     k_ecount<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
     k_escan<T><<<nf, 1024, 0, s>>>(a());
     k_efill<T, ND><<<grid[K_DENSE], kThreads, 0, s>>>(a());
-    for (int j = 0; j < kJumpsPerStep; ++j) k_jump<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
+    for (int j = 0; j < jumps; ++j) k_jump<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
     k_rcheck<T, ND><<<grid_rcheck, kThreads, 0, s>>>(a());
   }
   template <class A>
@@ -492,7 +497,17 @@ struct Group {
 constexpr int kMaxChunk = 32;
 constexpr int kKinds = 4;
 
-constexpr int kGraphSteps = 4;
+// Defaults and ranges of msz_tuning.
+constexpr msz_tuning kDefaultTuning = {kJumpsPerStep, 32, 64, (int32_t)kSmallCases, 4, 64, 0, {0, 0, 0, 0, 0}};
+
+bool tuning_ok(const msz_tuning& t) {
+  for (int k = 0; k < 5; ++k)
+    if (t.reserved[k] != 0) return false;
+  return t.jumps_per_step >= 1 && t.jumps_per_step <= 4 && t.chase_steps >= 4 && t.chase_steps <= 256 &&
+         t.small_rounds >= 0 && t.small_rounds <= 1024 && t.small_cases >= 1 && t.small_cases <= (int)kSmallCases &&
+         t.graph_steps >= 1 && t.graph_steps <= 8 && t.sweep_chunk >= 4 && t.sweep_chunk <= 64 &&
+         t.blocks_per_sm >= 0 && t.blocks_per_sm <= 64;
+}
 
 }  // namespace
 }  // namespace msz
@@ -506,6 +521,7 @@ struct msz_engine_s {
   int nf = 0;
   int device = 0;
   msz_options opt{};
+  msz_tuning tune = kDefaultTuning;
   Geom* geoms = nullptr;
   int* dtypes = nullptr;
   FieldBufs* bufs = nullptr;
@@ -543,9 +559,9 @@ struct msz_engine_s {
     fn(gd2);
     fn(gd3);
   }
-  int launches_per_step() {
+  int launches_per_step(int jumps) {
     int n = 0;
-    each_group([&](auto& g) { n += g.launches_per_step(); });
+    each_group([&](auto& g) { n += g.launches_per_step(jumps); });
     return n;
   }
 };
@@ -609,7 +625,7 @@ int setup_groups(msz_engine_s* E) {
   int rc = MSZ_OK;
   const bool allow_tma = !(E->opt.flags & MSZ_OPT_NO_TMA);
   E->each_group([&](auto& g) {
-    if (rc == MSZ_OK && !g.empty()) rc = g.setup(E->geoms, E->bufs, E->d_states, allow_tma);
+    if (rc == MSZ_OK && !g.empty()) rc = g.setup(E->geoms, E->bufs, E->d_states, allow_tma, E->tune);
   });
   return rc;
 }
@@ -732,12 +748,15 @@ int64_t engine_bytes(int nf, const int* ndim, const int64_t* dims, const int* dt
   return bytes;
 }
 
+// Timed runs keep kJumpsPerStep jump launches per step (the slot table of
+// the per-kernel statistics).
 void launch_steps(msz_engine_s* E, cudaStream_t s, int steps, bool timed) {
+  const int jumps = timed ? kJumpsPerStep : E->tune.jumps_per_step;
   for (int i = 0; i < steps; ++i) {
     cudaEvent_t* e = timed ? E->tev[i] : nullptr;
-    E->each_group([&](auto& g) { g.step(s, e, E->d_steplog, i); });
+    E->each_group([&](auto& g) { g.step(s, jumps, e, E->d_steplog, i); });
   }
-  E->launches += (uint64_t)steps * E->launches_per_step();
+  E->launches += (uint64_t)steps * E->launches_per_step(jumps);
 }
 
 // Per-launch device times of a timed chunk, split into launches that did work
@@ -764,7 +783,7 @@ void collect_times(msz_engine_s* E, int steps) {
   }
 }
 
-// Captures kGraphSteps steps of every group once (on a private stream). Each
+// Captures tune.graph_steps steps of every group once (on a private stream). Each
 // step launches every kernel; a kernel whose fields are all in other stages
 // returns at once (about a microsecond in a graph).
 int ensure_graph(msz_engine_s* E) {
@@ -773,7 +792,8 @@ int ensure_graph(msz_engine_s* E) {
     return MSZ_ERR_CUDA;
   cudaGraph_t gr = nullptr;
   if (cudaStreamBeginCapture(E->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MSZ_ERR_CUDA;
-  for (int i = 0; i < kGraphSteps; ++i) E->each_group([&](auto& g) { g.step(E->cap_stream); });
+  for (int i = 0; i < E->tune.graph_steps; ++i)
+    E->each_group([&](auto& g) { g.step(E->cap_stream, E->tune.jumps_per_step); });
   if (cudaStreamEndCapture(E->cap_stream, &gr) != cudaSuccess) return MSZ_ERR_CUDA;
   const cudaError_t r = cudaGraphInstantiate(&E->graph, gr, 0);
   cudaGraphDestroy(gr);
@@ -823,12 +843,13 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
   // field's state machine moved means a stall.
   int chunk = 1;
   uint64_t last_ticks = ~0ull;
+  const int gsteps = E->tune.graph_steps;
   for (;;) {
     if (graph) {
       for (int i = 0; i < chunk; ++i) cudaGraphLaunch(E->graph, s);
-      E->launches += (uint64_t)chunk * kGraphSteps * E->launches_per_step();
+      E->launches += (uint64_t)chunk * gsteps * E->launches_per_step(E->tune.jumps_per_step);
     } else {
-      launch_steps(E, s, std::min(chunk * kGraphSteps, kMaxChunk), timed);
+      launch_steps(E, s, std::min(chunk * gsteps, kMaxChunk), timed);
     }
     if (cudaMemcpyAsync(H, E->d_states, sizeof(DevState) * nf, cudaMemcpyDeviceToHost, s) != cudaSuccess)
       return MSZ_ERR_CUDA;
@@ -837,7 +858,7 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
                   cudaMemsetAsync(E->d_steplog, 0, sizeof(uint32_t) * kMaxChunk, s) != cudaSuccess))
       return MSZ_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return MSZ_ERR_CUDA;
-    if (timed) collect_times(E, std::min(chunk * kGraphSteps, kMaxChunk));
+    if (timed) collect_times(E, std::min(chunk * gsteps, kMaxChunk));
     bool all = true;
     uint64_t ticks = 0;
     for (int i = 0; i < nf; ++i) {
@@ -856,7 +877,7 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
       break;
     }
     last_ticks = ticks;
-    chunk = std::min(chunk * 2, kMaxChunk / kGraphSteps);
+    chunk = std::max(1, std::min(chunk * 2, kMaxChunk / gsteps));
   }
   E->each_group([&](auto& g) { g.emit(s); });
   E->launches += 3ull * ((E->gf2.empty() ? 0 : 1) + (E->gf3.empty() ? 0 : 1) + (E->gd2.empty() ? 0 : 1) +
@@ -869,7 +890,7 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
   if (timed && nf == 1) {
     for (int k = 0; k < NKID; ++k) E->ks_units[k] = H[0].kunits[k];
     E->ks_units[KID_SWEEP] = (uint64_t)E->geoms[0].n * E->ks_work[KID_SWEEP];
-    E->ks_units[KID_RCHECK] = (uint64_t)E->geoms[0].n * E->ks_work[KID_RCHECK];
+
   }
   float ms = 0.f;
   if (E->ev0 && E->ev1 && cudaEventElapsedTime(&ms, E->ev0, E->ev1) != cudaSuccess) ms = 0.f;
@@ -898,6 +919,116 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
   return worst;
 }
 
+// Applies launch parameters to an engine that owns its fields (plans,
+// batches): group grids and sweep tiling are recomputed, and the step graph
+// is captured again at the next fix.
+int set_tuning(msz_engine_s* E, const msz_tuning& t) {
+  if (!tuning_ok(t)) return MSZ_ERR_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return MSZ_ERR_CUDA;  // no fix of this engine in flight
+  E->tune = t;
+  if (E->graph) {
+    cudaGraphExecDestroy(E->graph);
+    E->graph = nullptr;
+  }
+  return setup_groups(E) == MSZ_OK ? MSZ_OK : MSZ_ERR_CUDA;
+}
+
+// Device time of one whole fix of every field under the engine's current
+// launch parameters: the faster of two runs after one that captures the
+// step graph (ev0 .. ev1 of run_engine).
+int time_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, const double* xi, cudaStream_t s,
+                float* ms) {
+  float best = 0.f;
+  for (int r = 0; r < 3; ++r) {
+    const int rc = run_engine(E, f, fhat, xi, s, nullptr);
+    if (rc != MSZ_OK) return rc;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, E->ev0, E->ev1) != cudaSuccess) return MSZ_ERR_CUDA;
+    if (r > 0 && (r == 1 || t < best)) best = t;
+  }
+  *ms = best;
+  return MSZ_OK;
+}
+
+// Tuned settings of this process, by batch signature.
+std::mutex g_tune_mu;
+std::vector<std::pair<std::vector<int64_t>, msz_tuning>> g_tune_cache;
+
+// Per field: dtype, dimension and log2 of the vertex count, sorted.
+std::vector<int64_t> tune_signature(const msz_engine_s* E) {
+  std::vector<int64_t> sig;
+  for (int i = 0; i < E->nf; ++i) {
+    int lg = 0;
+    while ((1ll << (lg + 1)) <= (int64_t)E->geoms[i].n) ++lg;
+    sig.push_back(((int64_t)E->dtypes[i] << 40) | ((int64_t)E->geoms[i].nd << 32) | lg);
+  }
+  std::sort(sig.begin(), sig.end());
+  return sig;
+}
+
+// Coordinate descent over the launch parameters (see msz_batch_autotune).
+int autotune(msz_engine_s* E, const void* const* f, const void* const* fhat, const double* xi, bool force,
+             cudaStream_t s, msz_tuning* out, int* tried) {
+  if (tried) *tried = 0;
+  const std::vector<int64_t> sig = tune_signature(E);
+  if (!force) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& c : g_tune_cache)
+      if (c.first == sig) {
+        *out = c.second;
+        return set_tuning(E, c.second);
+      }
+  }
+  msz_tuning best = E->tune;
+  float t_best = 0.f;
+  int rc = time_engine(E, f, fhat, xi, s, &t_best);
+  if (rc != MSZ_OK) return rc;
+  int n = 1;
+  struct Knob {
+    int32_t msz_tuning::*field;
+    std::vector<int32_t> values;
+  };
+  const std::vector<Knob> knobs = {
+      {&msz_tuning::small_rounds, {0, 16, 64, 256}},
+      {&msz_tuning::small_cases, {4096, 16384, (int32_t)kSmallCases}},
+      {&msz_tuning::graph_steps, {2, 4, 8}},
+      {&msz_tuning::jumps_per_step, {1, 2, 3}},
+      {&msz_tuning::chase_steps, {16, 32, 64}},
+      {&msz_tuning::sweep_chunk, {16, 32, 64}},
+      {&msz_tuning::blocks_per_sm, {0, 2, 4}},
+  };
+  for (const Knob& k : knobs) {
+    for (const int32_t v : k.values) {
+      if (best.*(k.field) == v) continue;
+      msz_tuning cand = best;
+      cand.*(k.field) = v;
+      if (!tuning_ok(cand)) continue;
+      if ((rc = set_tuning(E, cand)) != MSZ_OK) return rc;
+      float t = 0.f;
+      if ((rc = time_engine(E, f, fhat, xi, s, &t)) != MSZ_OK) return rc;
+      ++n;
+      if (t < 0.98f * t_best) {
+        best = cand;
+        t_best = t;
+      }
+    }
+  }
+  if ((rc = set_tuning(E, best)) != MSZ_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    bool found = false;
+    for (auto& c : g_tune_cache)
+      if (c.first == sig) {
+        c.second = best;
+        found = true;
+      }
+    if (!found) g_tune_cache.emplace_back(sig, best);
+  }
+  *out = best;
+  if (tried) *tried = n;
+  return MSZ_OK;
+}
+
 }  // namespace
 }  // namespace msz
 
@@ -907,6 +1038,7 @@ struct msz_plan_s {
 };
 struct msz_batch_s {
   msz_engine_s* E;
+  bool tuned = false;  // msz_batch_autotune has run on it
 };
 
 extern "C" {
@@ -1031,7 +1163,7 @@ int msz_batch_create(msz_batch* out, int n, const int* ndim, const int64_t* dims
   msz_engine_s* E = nullptr;
   const int rc = create_engine(&E, n, ndim, dims, dtype, opt);
   if (rc != MSZ_OK) return rc;
-  msz_batch_s* b = new (std::nothrow) msz_batch_s{E};
+  msz_batch_s* b = new (std::nothrow) msz_batch_s{E, false};
   if (!b) {
     free_engine(E);
     return MSZ_ERR_OOM;
@@ -1043,7 +1175,48 @@ int msz_batch_create(msz_batch* out, int n, const int* ndim, const int64_t* dims
 int msz_batch_fix(msz_batch b, const void* const* orig_dev, const void* const* decomp_dev, const double* xi,
                   void* stream, msz_result* results) {
   if (!b || !orig_dev || !decomp_dev || !xi) return MSZ_ERR_ARG;
+  if (b->E->opt.autotune && !b->tuned) {
+    msz_tuning t;
+    const int rc = msz_batch_autotune(b, orig_dev, decomp_dev, xi, 0, stream, &t, nullptr);
+    if (rc != MSZ_OK) return rc;
+  }
   return run_engine(b->E, orig_dev, decomp_dev, xi, static_cast<cudaStream_t>(stream), results);
+}
+
+void msz_tuning_default(msz_tuning* t) {
+  if (t) *t = kDefaultTuning;
+}
+
+int msz_tuning_valid(const msz_tuning* t) { return (t && tuning_ok(*t)) ? MSZ_OK : MSZ_ERR_ARG; }
+
+int msz_batch_set_tuning(msz_batch b, const msz_tuning* t) {
+  if (!b || !t) return MSZ_ERR_ARG;
+  return set_tuning(b->E, *t);
+}
+
+int msz_batch_get_tuning(msz_batch b, msz_tuning* t) {
+  if (!b || !t) return MSZ_ERR_ARG;
+  *t = b->E->tune;
+  return MSZ_OK;
+}
+
+int msz_plan_set_tuning(msz_plan p, const msz_tuning* t) {
+  if (!p || !t) return MSZ_ERR_ARG;
+  return set_tuning(p->E, *t);
+}
+
+int msz_plan_get_tuning(msz_plan p, msz_tuning* t) {
+  if (!p || !t) return MSZ_ERR_ARG;
+  *t = p->E->tune;
+  return MSZ_OK;
+}
+
+int msz_batch_autotune(msz_batch b, const void* const* orig_dev, const void* const* decomp_dev, const double* xi,
+                       int force, void* stream, msz_tuning* out, int* tried) {
+  if (!b || !orig_dev || !decomp_dev || !xi || !out) return MSZ_ERR_ARG;
+  const int rc = autotune(b->E, orig_dev, decomp_dev, xi, force != 0, static_cast<cudaStream_t>(stream), out, tried);
+  if (rc == MSZ_OK) b->tuned = true;
+  return rc;
 }
 
 int msz_batch_destroy(msz_batch b) {
@@ -1494,9 +1667,10 @@ void srv_worker(msz_server_s* S) {
     }
     // one chunk: init of newly admitted fields, steps, emission of converged ones
     E->each_group([&](auto& g) { g.init(S->stream); });
-    for (int k = 0; k < S->steps_per_chunk; ++k) E->each_group([&](auto& g) { g.step(S->stream, nullptr); });
+    for (int k = 0; k < S->steps_per_chunk; ++k)
+      E->each_group([&](auto& g) { g.step(S->stream, E->tune.jumps_per_step); });
     E->each_group([&](auto& g) { g.emit(S->stream); });
-    S->launches += (uint64_t)S->steps_per_chunk * E->launches_per_step();
+    S->launches += (uint64_t)S->steps_per_chunk * E->launches_per_step(E->tune.jumps_per_step);
     cudaMemcpyAsync(E->h_states, E->d_states, sizeof(DevState) * S->slots_n, cudaMemcpyDeviceToHost, S->stream);
     const bool ok = cudaStreamSynchronize(S->stream) == cudaSuccess;
     const uint64_t t = now_ns();

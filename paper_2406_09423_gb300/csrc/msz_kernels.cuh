@@ -1257,13 +1257,13 @@ __global__ void __launch_bounds__(kThreads, 6) k_efill(GroupArgs<T> A) {
 
 // One round of label propagation on the compact exit tables. Each entry
 // that holds a rank follows its line through the exits of the tiles it
-// crosses until it reaches a label (or kChase steps), storing every pointer
+// crosses until it reaches a label (or A.chase steps), storing every pointer
 // it reaches in its own entry. All entries do so at once: a value read is the
 // entry of an exit further along the same line, or the line's label, whether
 // it was read before or after its owner advanced it, so every step makes
 // progress and the other entries' stores shorten the walk. Loads bypass L1 to
-// see those stores. A round that leaves no rank ends the labelling.
-constexpr int kChase = 32;
+// see those stores. A round that leaves no rank ends the labelling. An entry
+// follows at most A.chase steps per launch.
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
@@ -1299,7 +1299,7 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
           x[k] = in ? lc[rb + k * kThreads] : kRes;
           acc += in ? 1u : 0u;
         }
-        for (int h = 0; h < kChase; ++h) {
+        for (int h = 0; h < A.chase; ++h) {
           uint32_t walk = 0;  // bit k: entry k still holds a rank
 #pragma unroll
           for (int k = 0; k < kJB; ++k) walk |= (x[k] & kRes) ? 0u : (1u << k);
@@ -1456,6 +1456,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_rcheck(GroupArgs<T> A) {
     // it holds no troublemaker and adds nothing to the counts.
     const uint8_t tstate = job ? F.tdirty[tile] : 0;
     const bool examine = __syncthreads_or(relabel) || !job || (tstate & 2) || F.twrong[tile];
+    // algorithmic bytes (kernel timing runs): each exit's (bitmap word,
+    // prefix) pair, table entry and snapshot, and, for an examined tile, each
+    // vertex's terminal word and f's two labels
+    if (threadIdx.x == 0)
+      log_units(A, st, KID_RCHECK,
+                16ull * nxl + (examine ? 12ull * min(LG::TX, G.nx - x0) * min(LG::TY, G.ny - y0) *
+                                             min(LG::TZ, G.nz - z0)
+                                       : 0ull));
     if (!examine) continue;
     // label of one terminal half t (direction d) of a vertex of this tile
     auto label_of = [&](uint32_t t, int d) -> int32_t {
@@ -1642,15 +1650,14 @@ __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
 // lost the type plus those the reclassification gave it: every vertex of the
 // type, the set a gather lists. The field goes back to the grid kernels (with
 // its cases listed, a type to gather, or the R-loop) when a round outgrows
-// the cluster, the type changes, or after kSmallRounds rounds. The cluster's
+// the cluster, the type changes, or after A.small_rounds rounds. The cluster's
 // counters live in the shared memory of its block 0.
 // ---------------------------------------------------------------------------
 constexpr int kSmallThreads = 1024;
 constexpr int kSmallCluster = 16;  // blocks per field (a non-portable cluster size)
 constexpr uint32_t kSmallSpan = (uint32_t)kSmallThreads * kSmallCluster;
 constexpr int kSmallPer = 4;  // cases per thread
-constexpr uint32_t kSmallCases = kSmallSpan * kSmallPer;
-constexpr int kSmallRounds = 64;
+constexpr uint32_t kSmallCases = kSmallSpan * kSmallPer;  // the most a launch can hold (A.small_cases <= this)
 
 // Barrier of the cluster, release / acquire at cluster scope: every memory
 // access (global or shared) before it happens before those after it in all
@@ -1688,7 +1695,8 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
   const Field<T>& F = A.fields[fi];
   DevState* st = F.st;
   // the same for the whole cluster: nothing writes the state before the first barrier
-  if (!(st->phase == PH_C && st->action == ACT_REQUEST && st->ncase <= kSmallCases)) return;
+  const uint32_t cap = min(A.small_cases, kSmallCases);
+  if (!(st->phase == PH_C && st->action == ACT_REQUEST && st->ncase <= cap)) return;
   constexpr int R = 2 * Slots<ND>::NPOS + 1;
   // block 0's: touched count, freezes, next list length, go, apply sums (2), count changes (4)
   __shared__ uint32_t s_ctl[10];
@@ -1701,7 +1709,7 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
     C[3] = 1;
   }
   uint32_t rounds = 0;
-  for (int it = 0; it < kSmallRounds; ++it) {
+  for (int it = 0; it < A.small_rounds; ++it) {
     cluster_barrier();  // the round's case list, state and counters are in place
     if (!C[3]) break;
     const uint32_t type = st->T, nc = st->ncase;
@@ -1777,7 +1785,7 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
       // holds every vertex of the type; otherwise the grid's gather lists it
       const uint32_t len = C[2];
       const bool go = st->phase == PH_C && st->action == ACT_GATHER && st->T == type &&
-                      st->counts[type] <= kSmallCases && len == st->counts[type];
+                      st->counts[type] <= cap && len == st->counts[type];
       if (go) {
         st->ncase = len;
         st->action = ACT_REQUEST;

@@ -66,8 +66,27 @@ class MszCounts(ctypes.Structure):
 
 
 class MszOptions(ctypes.Structure):
-    _fields_ = [("max_rounds", ctypes.c_uint64), ("label_tile", ctypes.c_int32),
+    _fields_ = [("max_rounds", ctypes.c_uint64), ("autotune", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32 * 6)]
+
+
+TUNING_FIELDS = ("jumps_per_step", "chase_steps", "small_rounds", "small_cases", "graph_steps", "sweep_chunk",
+                 "blocks_per_sm")
+
+
+class MszTuning(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in TUNING_FIELDS] + [("reserved", ctypes.c_int32 * 5)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k in TUNING_FIELDS}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "MszTuning":
+        t = cls()
+        lib().msz_tuning_default(ctypes.byref(t))
+        for k, v in d.items():
+            setattr(t, k, int(v))
+        return t
 
 
 class MszResult(ctypes.Structure):
@@ -161,6 +180,15 @@ def lib() -> ctypes.CDLL:
         L.msz_server_cancel.restype = I
         L.msz_server_destroy.argtypes = [P]
         L.msz_server_destroy.restype = I
+        L.msz_tuning_default.argtypes = [ctypes.POINTER(MszTuning)]
+        L.msz_tuning_default.restype = None
+        L.msz_tuning_valid.argtypes = [ctypes.POINTER(MszTuning)]
+        L.msz_tuning_valid.restype = I
+        for nm in ("msz_batch_set_tuning", "msz_batch_get_tuning", "msz_plan_set_tuning", "msz_plan_get_tuning"):
+            getattr(L, nm).argtypes = [P, ctypes.POINTER(MszTuning)]
+            getattr(L, nm).restype = I
+        L.msz_batch_autotune.argtypes = [P, P, P, P, I, P, ctypes.POINTER(MszTuning), ctypes.POINTER(I)]
+        L.msz_batch_autotune.restype = I
         L.msz_fix_noalloc.argtypes = [I, P, I, P, P, D, P, P, P, P, P, ctypes.POINTER(MszResult)]
         L.msz_fix_noalloc.restype = I
         L.msz_strerror.argtypes = [I]
@@ -260,11 +288,12 @@ def msz_batch_bytes(shapes, dtypes) -> int:
     return int(lib().msz_batch_bytes(n, nd, dims, dts))
 
 
-def msz_batch_create(shapes, dtypes, max_rounds: int = 0, flags: int = 0):
+def msz_batch_create(shapes, dtypes, max_rounds: int = 0, flags: int = 0, autotune: bool = False):
     n, nd, dims, dts = _batch_arrays(shapes, dtypes)
     opt = MszOptions()
     opt.max_rounds = max_rounds
     opt.flags = flags
+    opt.autotune = 1 if autotune else 0
     b = ctypes.c_void_p()
     check(lib().msz_batch_create(ctypes.byref(b), n, nd, dims, dts, ctypes.byref(opt)), "msz_batch_create")
     return b
@@ -279,6 +308,41 @@ def msz_batch_fix(batch, orig_ptrs, decomp_ptrs, xis, stream: int = 0):
     res = (MszResult * n)()
     st = lib().msz_batch_fix(batch, fa, ha, xa, ctypes.c_void_p(stream), res)
     return st, list(res)
+
+
+def msz_tuning_default() -> dict:
+    t = MszTuning()
+    lib().msz_tuning_default(ctypes.byref(t))
+    return t.as_dict()
+
+
+def msz_tuning_valid(d: dict) -> int:
+    return lib().msz_tuning_valid(ctypes.byref(MszTuning.from_dict(d)))
+
+
+def msz_set_tuning(handle, d: dict, plan: bool = False):
+    fn = lib().msz_plan_set_tuning if plan else lib().msz_batch_set_tuning
+    check(fn(handle, ctypes.byref(MszTuning.from_dict(d))), "msz_set_tuning")
+
+
+def msz_get_tuning(handle, plan: bool = False) -> dict:
+    t = MszTuning()
+    fn = lib().msz_plan_get_tuning if plan else lib().msz_batch_get_tuning
+    check(fn(handle, ctypes.byref(t)), "msz_get_tuning")
+    return t.as_dict()
+
+
+def msz_batch_autotune(batch, orig_ptrs, decomp_ptrs, xis, force: bool = False, stream: int = 0):
+    """(tuning dict, settings timed)."""
+    n = len(orig_ptrs)
+    fa = (ctypes.c_void_p * n)(*orig_ptrs)
+    ha = (ctypes.c_void_p * n)(*decomp_ptrs)
+    xa = (ctypes.c_double * n)(*[float(x) for x in xis])
+    t = MszTuning()
+    tried = ctypes.c_int(0)
+    check(lib().msz_batch_autotune(batch, fa, ha, xa, 1 if force else 0, ctypes.c_void_p(stream), ctypes.byref(t),
+                                   ctypes.byref(tried)), "msz_batch_autotune")
+    return t.as_dict(), int(tried.value)
 
 
 def msz_batch_destroy(batch):

@@ -72,3 +72,18 @@ def test_no_device_is_an_error_not_a_fallback():
         msz.fix(f, f.clone(), 0.1)
     with pytest.raises(RuntimeError):
         msz.directions(f)
+
+
+def test_tuning_defaults_and_validation_without_gpu():
+    from paper_2406_09423_gb300 import native
+
+    d = native.msz_tuning_default()
+    assert d == {"jumps_per_step": 2, "chase_steps": 32, "small_rounds": 64, "small_cases": 65536,
+                 "graph_steps": 4, "sweep_chunk": 64, "blocks_per_sm": 0}
+    assert native.msz_tuning_valid(d) == 0
+    for k, bad in (("jumps_per_step", 5), ("chase_steps", 3), ("small_rounds", -1), ("small_cases", 0),
+                   ("graph_steps", 0), ("sweep_chunk", 3), ("blocks_per_sm", 65)):
+        assert native.msz_tuning_valid(dict(d, **{k: bad})) == -1, k
+    t = native.MszTuning.from_dict(d)
+    t.reserved[2] = 1
+    assert native.lib().msz_tuning_valid(ctypes.byref(t)) == -1
