@@ -871,6 +871,9 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
   // the same exits by shell index (the tile's record for the label lookups)
   constexpr int kShW = LabelGeom<ND>::SHW;
   __shared__ uint32_t shx[2][kShW];
+  // halo-index offset of each stencil slot (slot 15: the cell itself)
+  __shared__ int s_off[16];
+  if (threadIdx.x < 16) s_off[threadIdx.x] = slot_offset((int)threadIdx.x, ND, HS, HSS);
   auto active = [](const Field<T>& F) {
     return F.st->action == ACT_LABELS && F.st->lstate == L_INIT && (F.st->ljob != 0) == JOB;
   };
@@ -936,7 +939,7 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
         db = F.gdir[v];
       }
       const int sa = (int)(db & 15u), sd = (int)(db >> 4);
-      const int ca = c + slot_offset(sa, ND, HS, HSS), cd = c + slot_offset(sd, ND, HS, HSS);
+      const int ca = c + s_off[sa], cd = c + s_off[sd];
       const uint32_t self = kTermFlag | kTermExtr | (uint32_t)i;  // i: the tile cell index
       PP[c] = (sa == kSelf ? self : (uint32_t)ca) | ((sd == kSelf ? self : (uint32_t)cd) << 16);
       const uint32_t bhi = (uint32_t)(lx == LG::TX - 1) | ((uint32_t)(ly == LG::TY - 1) << 1) |
@@ -966,9 +969,9 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
     __syncthreads();
     // pointer doubling until every cell of the tile holds its two terminals
     for (int round = 0; round < 2 * LG::TV && __syncthreads_or(live != 0u); ++round) {
-#pragma unroll
-      for (int k = 0; k < LG::PER_THREAD; ++k) {
-        if (!((live >> k) & 1u)) continue;
+      // the thread's live cells only
+      for (uint32_t lm = live; lm; lm &= lm - 1) {
+        const int k = __ffs(lm) - 1;
         const int c = hc0 + k * CellWalk<ND>::HSTEP;
         const uint32_t p = PP[c];
         const uint32_t a = p & 0xffffu, b = p >> 16;
