@@ -362,13 +362,15 @@ int msz_decode_edits(const void* in_dev, uint64_t in_bytes, const void* fhat_dev
  * Inputs (orig_dev, decomp_dev: N values) and outputs are the caller's
  * device buffers: edit_idx_dev / edit_val_dev hold N entries (worst case),
  * label_max_dev / label_min_dev hold N labels. out->edit_idx etc. point to
- * them. Every other array of the loop lives in one static device array of
- * 64 MiB that each GPU loading the library holds until exit; a field needs
- * about 37 bytes per vertex (float32) or 41 (float64) of it, so up to about
- * 1.8 M (float32) / 1.6 M (float64) vertices. Larger fields are rejected
- * with MSZ_ERR_TOO_LARGE before any work. The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture. All calls share
+ * them (the label buffers also serve as scratch during the call). Every
+ * other array of the loop lives in one static device array of 64 MiB that
+ * each GPU loading the library holds until exit; a field needs about 41
+ * bytes per vertex (float32, 3D; 38 in 2D) or 45 (float64, 3D; 42 in 2D) of
+ * it, so up to about 1.66 M (float32) / 1.51 M (float64) vertices in 3D.
+ * Larger fields are rejected with MSZ_ERR_TOO_LARGE before any work. The
+ * first call on a device (and the first after the device's context was
+ * reset) looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture. All calls share
  * the array: calls that overlap on the GPU race and must be serialised by
  * the caller. No timing (device_ms = 0). Returns out->status. */
 int msz_fix_noalloc(int ndim, const int64_t dims[3], int dtype, const void* orig_dev,
