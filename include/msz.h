@@ -54,7 +54,10 @@ typedef enum {
   MSZ_ERR_CUDA = -8,       /* a CUDA runtime call failed */
   MSZ_ERR_BUSY = -9,       /* server: no free slot / request id unknown or not finished */
   MSZ_ERR_TOO_LARGE = -10, /* msz_fix_noalloc: the field does not fit its static scratch */
-  MSZ_ERR_CANCELLED = -11  /* server: the request was cancelled (msz_server_cancel) */
+  MSZ_ERR_CANCELLED = -11, /* server: the request was cancelled (msz_server_cancel) */
+  MSZ_ERR_CHECK = -12      /* checked build only (libmsz_checked.so, compiled with MSZ_CHECKED):
+                              an index read from device data was out of range; the access was
+                              skipped and the fix stopped being meaningful */
 } msz_status;
 
 /* Counters of one fix. The same quantities are computed by the reference

@@ -1,10 +1,12 @@
 """Builds libmsz.so (the CUDA library behind include/msz.h) in-tree.
 
 Every .cu under csrc/ is compiled for sm_103a in parallel and linked into
-paper_2406_09423_gb300/_build/libmsz.so. Device code is compiled without
-FMA contraction (-fmad=false) and host code with -ffp-contract=off, so every
-floating-point step of the edit arithmetic is one IEEE round-to-nearest
-operation.
+paper_2406_09423_gb300/_build/libmsz.so, and a second time with MSZ_CHECKED
+(bounds checks of every index read from device data, recording an error
+instead of accessing) into libmsz_checked.so. Device code is compiled
+without FMA contraction (-fmad=false) and host code with -ffp-contract=off,
+so every floating-point step of the edit arithmetic is one IEEE
+round-to-nearest operation.
 """
 from __future__ import annotations
 
@@ -19,6 +21,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmsz.so")
+LIB_CHECKED = os.path.join(OUT, "libmsz_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -40,22 +43,26 @@ def sources():
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(LIB_CHECKED)):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(LIB_CHECKED))
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "msz.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+    """Builds both libraries (in parallel); returns the normal one's path."""
     if not force and not _stale():
         return LIB
     os.makedirs(OUT, exist_ok=True)
     cc = nvcc()
+    variants = {LIB: (), LIB_CHECKED: ("-DMSZ_CHECKED",)}
 
-    def compile_one(src):
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *_flags(extra), "-c", src, "-o", obj]
+    def compile_one(job):
+        src, lib, defs = job
+        tag = "_checked" if defs else ""
+        obj = os.path.join(OUT, os.path.basename(src)[:-3] + tag + ".o")
+        cmd = [cc, *_flags(tuple(extra) + defs), "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -63,16 +70,19 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
         if verbose and r.stderr:
             print(r.stderr, flush=True)
-        return obj
+        return lib, obj
 
-    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    jobs = [(src, lib, defs) for lib, defs in variants.items() for src in sources()]
+    with ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
+        done = list(ex.map(compile_one, jobs))
+    for lib in variants:
+        objs = [o for l, o in done if l == lib]
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -48,7 +48,7 @@ constexpr uint32_t kExt = 0x80000000u;
 // Compact exit table entry flag: the entry holds the exit's label (an
 // extremum), else the rank of the next exit on its line.
 constexpr uint32_t kRes = 0x80000000u;
-enum : uint32_t { E_NONFINITE = 1, E_ARG = 2, E_BOUND = 4, E_TIMEOUT = 8 };
+enum : uint32_t { E_NONFINITE = 1, E_ARG = 2, E_BOUND = 4, E_TIMEOUT = 8, E_CHECK = 16 };
 
 // Work-unit kinds.
 enum { K_DENSE = 0, K_SWEEP = 1, K_LABEL = 2, K_SPARSE = 3, K_EMIT = 4, K_CASE = 5, NKIND = 6 };
@@ -151,6 +151,22 @@ struct GroupArgs {
 // Device helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t vload(const uint32_t* p) { return *(volatile const uint32_t*)p; }
+
+// Bounds checks of the checked build (compiled with -DMSZ_CHECKED): an index
+// read from data (a list entry, a list slot, a pointer, a table rank) that
+// lies outside [0, n) sets E_CHECK in the field's error bits and the access
+// it guards is skipped; the fix then ends with MSZ_ERR_CHECK. The normal
+// build compiles the checks away.
+#ifdef MSZ_CHECKED
+__device__ __forceinline__ bool msz_in_range(DevState* st, long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(&st->err_bits, E_CHECK);
+  return false;
+}
+#define MSZ_IN(st, i, n) msz_in_range((st), (long long)(i), (long long)(n))
+#else
+#define MSZ_IN(st, i, n) true
+#endif
 
 // Field owning global unit u of a kind: pre[i] <= u < pre[i + 1].
 __device__ __forceinline__ int field_of_unit(const int* pre, int nf, int u) {
@@ -470,10 +486,12 @@ __device__ __forceinline__ void mark(const Field<T>& F, int u, uint8_t bit, cons
       return;
     }
   } else if (ts.n) {
-    F.touched[atomicAdd(ts.n, 1u)] = (uint32_t)u;
+    const uint32_t q = atomicAdd(ts.n, 1u);
+    if (MSZ_IN(F.st, q, F.G.n)) F.touched[q] = (uint32_t)u;
     return;
   }
-  F.touched[list_slot(&F.st->ntouch)] = (uint32_t)u;
+  const uint32_t q = list_slot(&F.st->ntouch);
+  if (MSZ_IN(F.st, q, F.G.n)) F.touched[q] = (uint32_t)u;
 }
 
 // What a request for target t does: RQ_DEC decreases t; otherwise its

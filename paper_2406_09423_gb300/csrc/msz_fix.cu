@@ -896,7 +896,8 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
   if (E->ev0 && E->ev1 && cudaEventElapsedTime(&ms, E->ev0, E->ev1) != cudaSuccess) ms = 0.f;
   int worst = MSZ_OK;
   for (int i = 0; i < nf; ++i) {
-    const int st = (H[i].phase == PH_DONE) ? MSZ_OK : (H[i].status ? H[i].status : MSZ_ERR_CUDA);
+    int st = (H[i].phase == PH_DONE) ? MSZ_OK : (H[i].status ? H[i].status : MSZ_ERR_CUDA);
+    if (H[i].err_bits & E_CHECK) st = MSZ_ERR_CHECK;  // a bounds check of the checked build fired
     if (st != MSZ_OK && worst == MSZ_OK) worst = st;
     if (!out) continue;
     msz_result& R = out[i];
@@ -1290,6 +1291,7 @@ const char* msz_strerror(int status) {
     case MSZ_ERR_BUSY: return "no free slot or request not ready";
     case MSZ_ERR_TOO_LARGE: return "field too large for the static scratch of msz_fix_noalloc";
     case MSZ_ERR_CANCELLED: return "request cancelled";
+    case MSZ_ERR_CHECK: return "bounds check failed (checked build)";
     default: return "unknown status";
   }
 }
@@ -1684,6 +1686,7 @@ void srv_worker(msz_server_s* S) {
       else if (H.phase == PH_DONE && H.emitted) st = MSZ_OK;
       else if (H.phase == PH_ERR) st = H.status ? H.status : MSZ_ERR_CUDA;
       else if (H.ticks == sl.last_ticks && ++sl.still >= 2) st = MSZ_ERR_TIMEOUT;
+      if (st != 1 && (H.err_bits & E_CHECK)) st = MSZ_ERR_CHECK;
       if (H.ticks != sl.last_ticks) sl.still = 0;
       sl.last_ticks = H.ticks;
       if (st == 1) continue;

@@ -592,7 +592,8 @@ __global__ void __launch_bounds__(kThreads) k_gather(GroupArgs<T> A) {
         uint32_t at = 0;
         if (lane == 31) at = atomicAdd(&F.st->ncase, total);
         at = __shfl_sync(kFull, at, 31) + incl - c;
-        for (; hits; hits &= hits - 1) F.cases[at++] = (uint32_t)(base + __ffs(hits) - 1);
+        for (; hits; hits &= hits - 1, ++at)
+          if (MSZ_IN(F.st, at, F.G.n)) F.cases[at] = (uint32_t)(base + __ffs(hits) - 1);
         ncases += c;
       }
     }
@@ -630,8 +631,10 @@ __global__ void __launch_bounds__(kThreads) k_mark(GroupArgs<T> A) {
     const int lane = threadIdx.x & 31;
     for (uint64_t j = b + (threadIdx.x >> 5); j < e; j += kThreads / 32) {
       const int v = (int)F.cases[j];
+      if (!MSZ_IN(st, v, F.G.n)) continue;
       const uint8_t d = F.gdir[v];  // exact: reclassified after every apply
       const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny);
+      if (!MSZ_IN(st, t, F.G.n)) continue;
       request_warp<T, ND>(F, v, t, lane, (int)type);
     }
   }
@@ -747,8 +750,10 @@ __global__ void __launch_bounds__(kThreads) k_reclass(GroupArgs<T> A) {
         reclass_vertex<T, ND>(F, (int)j, x, y, z, acc, vc);
       }
     } else {
-      for (uint64_t j = b + threadIdx.x; j < e; j += blockDim.x)
-        reclass_item<T, ND>(F, (int)F.touched[j / R], (int)(j % R), stamp, acc, vc);
+      for (uint64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
+        const uint32_t u = F.touched[j / R];
+        if (MSZ_IN(st, u, F.G.n)) reclass_item<T, ND>(F, (int)u, (int)(j % R), stamp, acc, vc);
+      }
     }
   }
   tl.flush(A, K_SPARSE, pre_flush, done);
@@ -939,7 +944,9 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
         db = F.gdir[v];
       }
       const int sa = (int)(db & 15u), sd = (int)(db >> 4);
-      const int ca = c + s_off[sa], cd = c + s_off[sd];
+      int ca = c + s_off[sa], cd = c + s_off[sd];
+      if (!MSZ_IN(st, ca, LG::HALO)) ca = c;
+      if (!MSZ_IN(st, cd, LG::HALO)) cd = c;
       const uint32_t self = kTermFlag | kTermExtr | (uint32_t)i;  // i: the tile cell index
       PP[c] = (sa == kSelf ? self : (uint32_t)ca) | ((sd == kSelf ? self : (uint32_t)cd) << 16);
       const uint32_t bhi = (uint32_t)(lx == LG::TX - 1) | ((uint32_t)(ly == LG::TY - 1) << 1) |
@@ -974,7 +981,9 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
         const int k = __ffs(lm) - 1;
         const int c = hc0 + k * CellWalk<ND>::HSTEP;
         const uint32_t p = PP[c];
-        const uint32_t a = p & 0xffffu, b = p >> 16;
+        uint32_t a = p & 0xffffu, b = p >> 16;
+        if (!MSZ_IN(st, a & kTermIdx, LG::HALO)) a = kTermFlag;
+        if (!MSZ_IN(st, b & kTermIdx, LG::HALO)) b = kTermFlag;
         const uint32_t a2 = double_half(PP, a, true);
         const uint32_t b2 = double_half(PP, b, false);
         if (a2 != a || b2 != b) PP[c] = a2 | (b2 << 16);
@@ -1238,6 +1247,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_efill(GroupArgs<T> A) {
               g = (t[j] & kTermExtr) ? ((uint32_t)extremum_vertex<ND>(F.G, t[j], x0, y0, z0) | kExt)
                                      : (uint32_t)shell_vertex<ND>(F.G, s_shell, (int)(t[j] & kTermIdx), x0, y0, z0);
             }
+            if (!(g & kExt) && !MSZ_IN(st, g, F.G.n)) g = kExt;
             t[j] = g;
           }
           // every entry of the batch before any store: a store to the table
@@ -1248,7 +1258,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_efill(GroupArgs<T> A) {
             t[j] = (t[j] & kExt) ? ((t[j] & ~kExt) | kRes) : exit_rank(ex, ep, ub, (int)t[j]);
 #pragma unroll
           for (int j = 0; j < kBatch; ++j)
-            if (j < c) lc[r + j] = t[j];
+            if (j < c && MSZ_IN(st, r + j, F.G.n)) lc[r + j] = t[j];
           r += c;
         }
       }
@@ -1309,7 +1319,7 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
           if (!walk) break;
 #pragma unroll
           for (int k = 0; k < kJB; ++k)
-            if ((walk >> k) & 1u) x[k] = __ldcg(lc + x[k]);
+            if ((walk >> k) & 1u) x[k] = MSZ_IN(st, x[k], ne) ? __ldcg(lc + x[k]) : kRes;
 #pragma unroll
           for (int k = 0; k < kJB; ++k)
             if ((walk >> k) & 1u) {
@@ -1430,7 +1440,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_rcheck(GroupArgs<T> A) {
         const uint32_t j = j0 + k * kThreads;
         q[k] = j < nxl ? (int)s_xl[j] : -1;
         const int d = q[k] >= kShW * 32 ? 1 : 0, s = q[k] - d * kShW * 32;
-        const int e = q[k] >= 0 ? shell_vertex<ND>(G, s_shell, s, x0, y0, z0) : 0;
+        int e = q[k] >= 0 ? shell_vertex<ND>(G, s_shell, s, x0, y0, z0) : 0;
+        if (!MSZ_IN(st, e, G.n)) e = 0;
         p[k] = F.xr[d][e >> 5];
         p[k].x &= (1u << (e & 31)) - 1u;
       }
@@ -1438,7 +1449,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_rcheck(GroupArgs<T> A) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int d = q[k] >= kShW * 32 ? 1 : 0, s = q[k] - d * kShW * 32;
-        lab[k] = q[k] >= 0 ? F.lc[d][p[k].y + (uint32_t)__popc(p[k].x)] & ~kRes : 0u;
+        const uint32_t rk = p[k].y + (uint32_t)__popc(p[k].x);
+        lab[k] = (q[k] >= 0 && MSZ_IN(st, rk, st->nexit[d])) ? F.lc[d][rk] & ~kRes : 0u;
         old[k] = (q[k] >= 0 && job) ? F.tsnap[((size_t)tile * 2 + d) * LG::SHELL + s] : 0u;
       }
 #pragma unroll
@@ -1584,7 +1596,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_rcheck(GroupArgs<T> A) {
         s_ntv = 0;
       }
       __syncthreads();
-      for (uint32_t j = threadIdx.x; j < ntv; j += kThreads) F.touched[s_base + j] = s_tv[j];
+      for (uint32_t j = threadIdx.x; j < ntv; j += kThreads)
+        if (MSZ_IN(st, s_base + j, G.n)) F.touched[s_base + j] = s_tv[j];
       __syncthreads();  // the buffer is free for the next unit
     }
   }
@@ -1637,7 +1650,10 @@ __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
     tl.target = act;
     const uint32_t b = (uint32_t)b64, e = (uint32_t)e64;
     if (threadIdx.x == 0) log_units(A, st, KID_APPLY, e - b);
-    for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) apply_vertex(F, (int)F.touched[j], acc);
+    for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) {
+      const uint32_t u = F.touched[j];
+      if (MSZ_IN(st, u, F.G.n)) apply_vertex(F, (int)u, acc);
+    }
   }
   tl.flush(A, K_SPARSE, pre_flush, done);
 }
@@ -1725,6 +1741,7 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
     for (int k = 0; k < kSmallPer; ++k) {
       const uint32_t j = gt + (uint32_t)k * kSmallSpan;
       cv[k] = j < nc ? (int)F.cases[j] : -1;
+      if (cv[k] >= 0 && !MSZ_IN(st, cv[k], F.G.n)) cv[k] = -1;
     }
 #pragma unroll
     for (int k = 0; k < kSmallPer; ++k) {
@@ -1736,7 +1753,8 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
         mark(F, t, FL_DEC, ts);
       } else {
         count_freeze_req(st, (int)type, cause);
-        F.lc[0][atomicAdd(&C[1], 1u)] = (uint32_t)v;
+        const uint32_t q = atomicAdd(&C[1], 1u);
+        if (MSZ_IN(st, q, F.G.n)) F.lc[0][q] = (uint32_t)v;
       }
     }
     cluster_barrier();
@@ -1749,7 +1767,10 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
     const uint32_t nt = C[0];
     {
       uint32_t acc[2] = {0, 0};
-      for (uint32_t j = gt; j < nt; j += kSmallSpan) apply_vertex(F, (int)F.touched[j], acc);
+      for (uint32_t j = gt; j < nt; j += kSmallSpan) {
+        const uint32_t u = F.touched[j];
+        if (MSZ_IN(st, u, F.G.n)) apply_vertex(F, (int)u, acc);
+      }
       warp_add_shared<2>(acc, C + 4);
     }
     cluster_barrier();
@@ -1767,8 +1788,12 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
       uint32_t acc[4] = {0, 0, 0, 0};
       for (uint32_t j = gt; j < nt * R; j += kSmallSpan) {
         int vc = 0;
-        const uint32_t ch = reclass_item<T, ND>(F, (int)F.touched[j / R], (int)(j % R), stamp, acc, vc);
-        if (((ch >> type) & 1u) && !((ch >> (8 + type)) & 1u)) F.cases[atomicAdd(&C[2], 1u)] = (uint32_t)vc;
+        const uint32_t u = F.touched[j / R];
+        const uint32_t ch = MSZ_IN(st, u, F.G.n) ? reclass_item<T, ND>(F, (int)u, (int)(j % R), stamp, acc, vc) : 0u;
+        if (((ch >> type) & 1u) && !((ch >> (8 + type)) & 1u)) {
+          const uint32_t q = atomicAdd(&C[2], 1u);
+          if (MSZ_IN(st, q, F.G.n)) F.cases[q] = (uint32_t)vc;
+        }
       }
       warp_add_shared<4>(acc, C + 6);
     }
@@ -1776,7 +1801,10 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
     // then this round's cases that kept the type
 #pragma unroll
     for (int k = 0; k < kSmallPer; ++k)
-      if (cv[k] >= 0 && ((F.cls[cv[k]] >> type) & 1u)) F.cases[atomicAdd(&C[2], 1u)] = (uint32_t)cv[k];
+      if (cv[k] >= 0 && ((F.cls[cv[k]] >> type) & 1u)) {
+        const uint32_t q = atomicAdd(&C[2], 1u);
+        if (MSZ_IN(st, q, F.G.n)) F.cases[q] = (uint32_t)cv[k];
+      }
     if (gt == 0) {
       for (int c = 0; c < 4; ++c) st->counts[c] += C[6 + c];
       ctrl_after_classify_counted(st);
@@ -1944,8 +1972,10 @@ __global__ void __launch_bounds__(kThreads) k_emit_write(GroupArgs<T> A) {
       const int k = __ffs(mm) - 1;
       mm &= mm - 1;
       const int v = base + k;
-      F.edit_idx[off] = (uint32_t)v;
-      F.edit_val[off] = F.g[v];
+      if (MSZ_IN(st, off, F.G.n)) {
+        F.edit_idx[off] = (uint32_t)v;
+        F.edit_val[off] = F.g[v];
+      }
       ++off;
     }
     if (unit_done(st, F.units[K_EMIT]) && threadIdx.x == 0) {

@@ -12,7 +12,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libmsz.so")
+# MSZ_LIBRARY=checked selects the bounds-checked build (libmsz_checked.so)
+LIB_PATH = os.path.join(HERE, "_build", "libmsz_checked.so" if os.environ.get("MSZ_LIBRARY") == "checked"
+                        else "libmsz.so")
 
 MSZ_F32, MSZ_F64 = 0, 1
 MSZ_OPT_NO_TMA = 1
@@ -26,6 +28,7 @@ STATUS = {
     0: "MSZ_OK", -1: "MSZ_ERR_ARG", -2: "MSZ_ERR_DTYPE", -3: "MSZ_ERR_NONFINITE",
     -4: "MSZ_ERR_BOUND", -5: "MSZ_ERR_OOM", -6: "MSZ_ERR_NOCONVERGE", -7: "MSZ_ERR_TIMEOUT",
     -8: "MSZ_ERR_CUDA", -9: "MSZ_ERR_BUSY", -10: "MSZ_ERR_TOO_LARGE", -11: "MSZ_ERR_CANCELLED",
+    -12: "MSZ_ERR_CHECK",
 }
 
 COUNT_FIELDS = (

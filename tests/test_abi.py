@@ -31,15 +31,17 @@ def test_library_exports_every_declared_symbol():
     from paper_2406_09423_gb300 import build
 
     lib_path = build.build()
-    lib = ctypes.CDLL(lib_path)
-    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
-    assert not missing, missing
+    for path in (lib_path, build.LIB_CHECKED):  # the normal and the bounds-checked build
+        lib = ctypes.CDLL(path)
+        missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+        assert not missing, (path, missing)
 
 
 def test_strerror_without_gpu():
     from paper_2406_09423_gb300 import native
 
     assert native.msz_strerror(-4) == "decompressed value outside the error bound"
+    assert native.msz_strerror(-12) == "bounds check failed (checked build)"
     assert native.msz_version().startswith("msz-gb300")
 
 
