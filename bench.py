@@ -119,7 +119,7 @@ def peaks():
 # with the most working time among them); k_label_tile is bound by
 # instruction issue in its shared-memory pointer doubling, the sparse
 # C-loop kernels by L2 latency.
-HBM_BOUND = ("k_csweep", "k_ecount", "k_efill", "k_jump", "k_rcheck")
+HBM_BOUND = ("k_csweep", "k_jump", "k_rcheck")
 
 # DRAM bytes per work unit from one ncu capture of a working launch on the
 # 320^3 field of the same workload (dram__bytes_read.sum +
@@ -136,29 +136,21 @@ def kernel_bytes(name, st, n, es):
     k_csweep      the stencil sweep's minimum: g (es) and f's direction byte
                   read, one byte of g's classification written per vertex;
     k_label_tile  g's direction byte read + the packed tile terminals (4)
-                  written per vertex of the tiles recomputed (f's evaluation,
-                  once per fix, also reads f and g and writes both direction
-                  bytes: not counted);
-    k_ecount      per bitmap word: two exit-bitmap words read, two prefix
-                  words written (16);
-    k_efill       bitmaps and prefixes read, (bitmap word, prefix) pairs
-                  written (n bytes per launch) + terminal read and table entry
-                  written (8) per exit;
+                  written per vertex of the tiles recomputed, and the two
+                  first-level exit-table entries (8) of each of the tile's
+                  1352 face cells (f's evaluation, once per fix, also reads f
+                  and g and writes both direction bytes: not counted);
     k_jump        4 bytes per exit-table access (entry read; gather and write
-                  of the entries still holding a rank);
+                  of the entries still holding a pointer);
     k_rcheck      counted by the kernel (its units are bytes): per exit label
-                  looked up, the (bitmap word, prefix) pair, the table entry
-                  and the tile's snapshot of it (16); per vertex of the tiles
-                  it examines, the terminal word and f's two labels (12)."""
-    u, w = st["units"], st["work_launches"]
+                  looked up, the table entry and the tile's snapshot of it
+                  (8); per vertex of the tiles it examines, the terminal word
+                  and f's two labels (12)."""
+    u = st["units"]
     if name == "k_csweep":
         return u * (es + 2)
     if name == "k_label_tile":
-        return u * 5
-    if name == "k_ecount":
-        return u * 16
-    if name == "k_efill":
-        return w * n + u * 8
+        return u * 5 + (u * 8 * 1352) // 4096
     if name == "k_jump":
         return u * 4
     if name == "k_rcheck":

@@ -157,14 +157,13 @@ int msz_plan_destroy(msz_plan p);
  * completes a stage of the field's state machine (the others find the field
  * in another stage and return at once). units counts the work of the working
  * launches: vertices (k_csweep; k_label_tile: vertices of the tiles
- * recomputed), algorithmic bytes (k_rcheck: 16 per exit label looked up,
- * 12 per vertex of the tiles examined), bitmap words (k_ecount), exits
- * (k_efill), exit-table
- * accesses (k_jump), fields (k_escan), cases (k_gather, k_mark),
+ * recomputed), algorithmic bytes (k_rcheck: 8 per exit label looked up,
+ * 12 per vertex of the tiles examined), exit-table
+ * accesses (k_jump), cases (k_gather, k_mark),
  * touched vertices (k_apply), ring items (k_reclass), C-loop rounds run
  * whole in one thread-block cluster per field (k_csmall: requests, apply and
  * reclassification of rounds with few cases). */
-#define MSZ_NUM_KERNELS 12
+#define MSZ_NUM_KERNELS 9
 typedef struct {
   const char* name;        /* kernel name, static string */
   uint64_t launches;       /* launches inside the loop's steps */
@@ -175,8 +174,8 @@ typedef struct {
 } msz_kernel_stat;
 
 /* Fills out[0 .. min(n, MSZ_NUM_KERNELS) - 1] in the order k_csweep,
- * k_gather, k_mark, k_label_tile, k_ecount, k_escan, k_efill, k_jump,
- * k_rcheck, k_apply, k_reclass, k_csmall;
+ * k_gather, k_mark, k_label_tile, k_jump, k_rcheck, k_apply, k_reclass,
+ * k_csmall;
  * returns the number filled, or MSZ_ERR_ARG (no plan / out, or a plan made
  * without MSZ_OPT_TIME_KERNELS). Host memory only. */
 int msz_plan_kernel_stats(msz_plan p, msz_kernel_stat* out, int n);
@@ -367,9 +366,9 @@ int msz_decode_edits(const void* in_dev, uint64_t in_bytes, const void* fhat_dev
  * label_max_dev / label_min_dev hold N labels. out->edit_idx etc. point to
  * them (the label buffers also serve as scratch during the call). Every
  * other array of the loop lives in one static device array of 64 MiB that
- * each GPU loading the library holds until exit; a field needs about 41
- * bytes per vertex (float32, 3D; 38 in 2D) or 45 (float64, 3D; 42 in 2D) of
- * it, so up to about 1.66 M (float32) / 1.51 M (float64) vertices in 3D.
+ * each GPU loading the library holds until exit; a field needs about 37
+ * bytes per vertex (float32, 3D; 30 in 2D) or 41 (float64, 3D; 34 in 2D) of
+ * it, so up to about 1.79 M (float32) / 1.62 M (float64) vertices in 3D.
  * Larger fields are rejected with MSZ_ERR_TOO_LARGE before any work. The
  * first call on a device (and the first after the device's context was
  * reset) looks up the array's device address (cudaGetSymbolAddress) with

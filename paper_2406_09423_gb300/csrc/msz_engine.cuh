@@ -39,14 +39,15 @@ enum : uint32_t { PH_INIT = 0, PH_FLABELS = 1, PH_C = 2, PH_R = 3, PH_DONE = 4, 
 enum : uint32_t {
   ACT_NONE = 0, ACT_MARK_C = 1, ACT_LABELS = 2, ACT_APPLY_R = 3, ACT_GATHER = 4, ACT_RECLASS = 5, ACT_REQUEST = 6
 };
-// Stages of one label evaluation (job 0: f, job 1: g): tile terminals, exit
-// counts, exit ranks, compact exit table, pointer jumping on it, then f's
-// labels in place (job 0) or the R-loop check.
-enum : uint32_t { L_INIT = 0, L_COUNT = 1, L_SCAN = 2, L_FILL = 3, L_JUMP = 4, L_DONE = 5 };
+// Stages of one label evaluation (job 0: f, job 1: g): tile terminals with
+// the first-level exit-table entries of the recomputed tiles, pointer
+// jumping on the exit tables, then f's labels in place (job 0) or the
+// R-loop check.
+enum : uint32_t { L_INIT = 0, L_JUMP = 1, L_DONE = 2 };
 // Tile terminal flag: the terminal is an extremum (else a tile exit).
 constexpr uint32_t kExt = 0x80000000u;
-// Compact exit table entry flag: the entry holds the exit's label (an
-// extremum), else the rank of the next exit on its line.
+// Exit-table entry flag: the entry holds the exit's label (an extremum),
+// else the slot of the next exit on its line.
 constexpr uint32_t kRes = 0x80000000u;
 enum : uint32_t { E_NONFINITE = 1, E_ARG = 2, E_BOUND = 4, E_TIMEOUT = 8, E_CHECK = 16 };
 
@@ -60,8 +61,7 @@ constexpr int kCaseTiles = kTilesPerWarp * kThreads / 32;  // case-count tiles p
 
 // Kernels of a loop step, in launch order of their kinds (per-kernel timing).
 enum {
-  KID_SWEEP = 0, KID_GATHER, KID_MARK, KID_LABEL, KID_ECOUNT, KID_ESCAN, KID_EFILL, KID_JUMP, KID_RCHECK,
-  KID_APPLY, KID_RECLASS, KID_CSMALL, NKID
+  KID_SWEEP = 0, KID_GATHER, KID_MARK, KID_LABEL, KID_JUMP, KID_RCHECK, KID_APPLY, KID_RECLASS, KID_CSMALL, NKID
 };
 
 constexpr int kStripes = 16;
@@ -81,7 +81,6 @@ struct DevState {
   // folds the stripes into the counters above (see fold_stripes).
   uint32_t stripe[kStripes][4];
   uint32_t jump_rounds, emitted;
-  uint32_t nexit[2];  // tile exits (ascending, descending lines) of the current evaluation
   uint64_t rounds, max_rounds, n_edits;
   uint64_t ticks;  // advanced by every state transition (stall detection)
   uint64_t kunits[NKID];  // work units per kernel (kernel timing runs only)
@@ -104,11 +103,12 @@ struct Field {
   uint32_t* term; // tile terminals (kTermFlag form) of the current evaluation; Pup's memory
                   // (the outputs are written only at emission)
   // per direction (0: ascending lines / max labels, 1: descending / min)
-  uint32_t* ex[2];  // bitmap of tile-exit vertices
-  uint32_t* ep[2];  // per bitmap word: exits before it within its dense unit
-  uint32_t* ub[2];  // per dense unit: exits before it (after the scan; counts before)
-  uint2* xr[2];     // per bitmap word: (bitmap word, exits before it): one load gives a rank
-  uint32_t* lc[2];  // compact exit table, indexed by exit rank
+  // exit tables, one slot per face cell of every label tile (exit_slot)
+  uint32_t* lf[2];  // first-level entries: a label (kRes) or the slot of the next exit on the line
+  uint32_t* lw[2];  // entries being resolved by the jumping; lw[0] is the C-loop's freeze list
+  uint8_t* xm[2];   // 1: the slot is an exit of some tile's lines (cleared when a fix starts)
+  uint32_t nface;   // slots per direction (label tiles times face cells, a multiple of 16)
+  uint32_t fz_cap;  // entries of lw[0] (at least nface; room for a launch's freezes in k_csmall)
   uint8_t* tdirty;  // per label tile: bit 0 terminals to recompute, bit 1 recomputed and not yet checked
   uint32_t* texit;  // per label tile and direction: bitmap over the shell cells its lines leave through
   uint32_t* tsnap;  // per label tile, direction and shell cell: the exit's label at the tile's last check

@@ -137,11 +137,9 @@ struct FieldBufs {
   int32_t* mf = nullptr;
   int32_t* Pup = nullptr;
   int32_t* Pdn = nullptr;
-  uint32_t* ex[2] = {nullptr, nullptr};
-  uint32_t* ep[2] = {nullptr, nullptr};
-  uint32_t* ub[2] = {nullptr, nullptr};
-  uint2* xr[2] = {nullptr, nullptr};
-  uint32_t* lc[2] = {nullptr, nullptr};
+  uint32_t* lf[2] = {nullptr, nullptr};
+  uint32_t* lw[2] = {nullptr, nullptr};
+  uint8_t* xm[2] = {nullptr, nullptr};
   uint8_t* tdirty = nullptr;
   uint32_t* texit = nullptr;
   uint32_t* tsnap = nullptr;
@@ -167,6 +165,19 @@ int label_tiles(const Geom& G) {
   return ((G.nx + LG::TX - 1) / LG::TX) * ((G.ny + LG::TY - 1) / LG::TY);
 }
 
+// Exit-table slots per direction: a slot per face cell of every label tile,
+// rounded up to 16 (the marks are cleared by words).
+size_t exit_slots(const Geom& G) {
+  const size_t nf = (size_t)label_tiles(G) * (size_t)(G.nd == 3 ? LabelGeom<3>::NFACE : LabelGeom<2>::NFACE);
+  return (nf + 15) / 16 * 16;
+}
+
+// Entries of lw[0]: its slots, and room for the freezes of a k_csmall launch
+// (at most one per case it holds).
+size_t freeze_cap(const Geom& G) {
+  return std::max(exit_slots(G), std::min((size_t)G.n, (size_t)kSmallCases));
+}
+
 // Carves a field's buffers. Outputs (labels Pup/Pdn, edit list) are carved
 // too unless the caller supplies them (with_outputs = false).
 void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs& B) {
@@ -177,13 +188,11 @@ void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs
   B.flags = (uint8_t*)b.take(nt * kEmitTile);
   B.Mf = (int32_t*)b.take(n * 4);
   B.mf = (int32_t*)b.take(n * 4);
-  const size_t nw = (n + 31) / 32, nu = (n + kDenseChunk - 1) / kDenseChunk;
+  const size_t nf = exit_slots(G);
   for (int d = 0; d < 2; ++d) {
-    B.ex[d] = (uint32_t*)b.take(nw * 4);
-    B.ep[d] = (uint32_t*)b.take(nw * 4);
-    B.ub[d] = (uint32_t*)b.take(nu * 4);
-    B.xr[d] = (uint2*)b.take(nw * 8);
-    B.lc[d] = (uint32_t*)b.take(n * 4);
+    B.lf[d] = (uint32_t*)b.take(nf * 4);
+    B.lw[d] = (uint32_t*)b.take((d == 0 ? freeze_cap(G) : nf) * 4);
+    B.xm[d] = (uint8_t*)b.take(nf);
   }
   B.tdirty = (uint8_t*)b.take((size_t)label_tiles(G));
   B.texit = (uint32_t*)b.take((size_t)label_tiles(G) * 2 * (G.nd == 3 ? LabelGeom<3>::SHW : LabelGeom<2>::SHW) * 4);
@@ -210,17 +219,16 @@ constexpr int kJumpsPerStep = 2;
 // A step holds two C-loop rounds (gather, mark, apply, reclassify): most
 // steps of a fix are C-loop rounds, and every launch of a stage that no field
 // is in still costs a few microseconds.
-constexpr int kStepSlots = 16 + kJumpsPerStep;  // launches per step
+constexpr int kStepSlots = 13 + kJumpsPerStep;  // launches per step
 constexpr int kStepEvents = kStepSlots + 1;
 static_assert(kStepSlots <= 32, "the step log holds one bit per launch slot");
 // kernel of each launch slot of a step
-constexpr int kSlotKernel[kStepSlots] = {KID_SWEEP,  KID_GATHER, KID_CSMALL, KID_MARK,  KID_APPLY,  KID_RECLASS,
-                                         KID_GATHER, KID_MARK,   KID_LABEL,  KID_LABEL, KID_ECOUNT, KID_ESCAN,
-                                         KID_EFILL,  KID_JUMP,   KID_JUMP,   KID_RCHECK, KID_APPLY, KID_RECLASS};
+constexpr int kSlotKernel[kStepSlots] = {KID_SWEEP, KID_GATHER, KID_CSMALL, KID_MARK,   KID_APPLY,
+                                         KID_RECLASS, KID_GATHER, KID_MARK,  KID_LABEL,  KID_LABEL,
+                                         KID_JUMP,  KID_JUMP,   KID_RCHECK, KID_APPLY, KID_RECLASS};
 static_assert(kJumpsPerStep == 2, "slot table assumes two jump launches per step");
 static_assert(NKID == MSZ_NUM_KERNELS, "kernel table and ABI disagree");
-const char* const kKernelNames[NKID] = {"k_csweep", "k_gather", "k_mark",   "k_label_tile",
-                                        "k_ecount", "k_escan",  "k_efill",  "k_jump",
+const char* const kKernelNames[NKID] = {"k_csweep", "k_gather", "k_mark",    "k_label_tile", "k_jump",
                                         "k_rcheck", "k_apply",  "k_reclass", "k_csmall"};
 
 template <class T, int ND>
@@ -264,7 +272,6 @@ struct Group {
     const int axis = (ND == 3) ? G.nz : G.ny;  // marching axis
     const int nchunks = (axis + max_chunk - 1) / max_chunk;
     TL.chunk = (axis + nchunks - 1) / nchunks;
-    TL.chunk += (4 - TL.chunk % 3) % 3;  // chunk + 2 planes per tile must be a multiple of 3
     TL.chunks = (axis + TL.chunk - 1) / TL.chunk;
     TL.tiles_x = (G.nx + SG::TX - 1) / SG::TX;
     TL.tiles_y = (ND == 3) ? (G.ny + SG::TY - 1) / SG::TY : 1;
@@ -316,12 +323,12 @@ struct Group {
       F.Pdn = B.Pdn;
       F.term = reinterpret_cast<uint32_t*>(B.Pup);
       for (int d = 0; d < 2; ++d) {
-        F.ex[d] = B.ex[d];
-        F.ep[d] = B.ep[d];
-        F.ub[d] = B.ub[d];
-        F.xr[d] = B.xr[d];
-        F.lc[d] = B.lc[d];
+        F.lf[d] = B.lf[d];
+        F.lw[d] = B.lw[d];
+        F.xm[d] = B.xm[d];
       }
+      F.nface = (uint32_t)exit_slots(G);
+      F.fz_cap = (uint32_t)freeze_cap(G);
       F.tdirty = B.tdirty;
       F.texit = B.texit;
       F.tsnap = B.tsnap;
@@ -420,8 +427,8 @@ struct Group {
   }
 
   // csweep, (gather, csmall, mark, apply, reclass), gather, mark, label_tile
-  // (f's, g's), ecount, escan, efill, jump x jumps, rcheck, apply, reclass
-  int launches_per_step(int jumps) const { return empty() ? 0 : 16 + jumps; }
+  // (f's, g's), jump x jumps, rcheck, apply, reclass
+  int launches_per_step(int jumps) const { return empty() ? 0 : 13 + jumps; }
 
   void init(cudaStream_t s) {
     if (empty()) return;
@@ -474,9 +481,6 @@ struct Group {
   void labels(cudaStream_t s, A&& a, int jumps) {
     k_label_tile<T, ND, false><<<grid_label[0], kThreads, label_smem[0], s>>>(a());
     k_label_tile<T, ND, true><<<grid_label[1], kThreads, label_smem[1], s>>>(a());
-    k_ecount<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
-    k_escan<T><<<nf, 1024, 0, s>>>(a());
-    k_efill<T, ND><<<grid[K_DENSE], kThreads, 0, s>>>(a());
     for (int j = 0; j < jumps; ++j) k_jump<T><<<grid[K_DENSE], kThreads, 0, s>>>(a());
     k_rcheck<T, ND><<<grid_rcheck, kThreads, 0, s>>>(a());
   }

@@ -34,8 +34,75 @@ struct LabelGeom {
   static constexpr int RING = 2 * SX + 2 * (SY - 2);
   static constexpr int SHELL = (ND == 3) ? 2 * SX * SY + TZ * RING : RING;
   static constexpr int SHW = (SHELL + 31) / 32;  // 32-bit words of a shell bitmap
+  // The tile's face cells (the tile cells with a neighbour in another tile;
+  // every tile exit is one): in 3D the two end planes (TX * TY cells each),
+  // then per inner plane a ring of 2 TX + 2 (TY - 2) cells; in 2D one ring.
+  static constexpr int PLANE = TX * TY;
+  static constexpr int RINGF = 2 * TX + 2 * (TY - 2);
+  static constexpr int NFACE = (ND == 3) ? 2 * PLANE + (TZ - 2) * RINGF : RINGF;
   static_assert(HALO <= 0x4000 && TV <= 0x4000, "pointers, indices and the terminal flags share 16 bits");
 };
+
+// Face index of the face cell at tile coordinates (lx, ly, lz).
+template <int ND>
+__host__ __device__ __forceinline__ int face_index(int lx, int ly, int lz) {
+  using LG = LabelGeom<ND>;
+  int base = 0;
+  if (ND == 3) {
+    if (lz == 0) return ly * LG::TX + lx;
+    if (lz == LG::TZ - 1) return LG::PLANE + ly * LG::TX + lx;
+    base = 2 * LG::PLANE + (lz - 1) * LG::RINGF;
+  }
+  if (ly == 0) return base + lx;
+  if (ly == LG::TY - 1) return base + LG::TX + lx;
+  return base + 2 * LG::TX + 2 * (ly - 1) + (lx != 0);
+}
+
+// Tile coordinates of face cell f (the inverse of face_index).
+template <int ND>
+__host__ __device__ __forceinline__ void face_cell(int f, int& lx, int& ly, int& lz) {
+  using LG = LabelGeom<ND>;
+  int q = f;
+  lz = 0;
+  if (ND == 3) {
+    if (f < 2 * LG::PLANE) {
+      lz = (f < LG::PLANE) ? 0 : LG::TZ - 1;
+      const int r = f - (f < LG::PLANE ? 0 : LG::PLANE);
+      ly = r / LG::TX;
+      lx = r % LG::TX;
+      return;
+    }
+    const int r = f - 2 * LG::PLANE;
+    lz = 1 + r / LG::RINGF;
+    q = r - (lz - 1) * LG::RINGF;
+  }
+  if (q < LG::TX) {
+    ly = 0;
+    lx = q;
+  } else if (q < 2 * LG::TX) {
+    ly = LG::TY - 1;
+    lx = q - LG::TX;
+  } else {
+    const int w = q - 2 * LG::TX;
+    ly = 1 + (w >> 1);
+    lx = (w & 1) * (LG::TX - 1);
+  }
+}
+
+// Slot of a face vertex in its field's exit tables: its tile's index times
+// NFACE plus its face index. A slot depends only on the vertex, so a tile's
+// entries stay where they are while other tiles are recomputed.
+template <int ND>
+__host__ __device__ __forceinline__ uint32_t exit_slot(const Geom& G, int x, int y, int z) {
+  using LG = LabelGeom<ND>;
+  static_assert((LG::TX & (LG::TX - 1)) == 0 && (LG::TY & (LG::TY - 1)) == 0 && (LG::TZ & (LG::TZ - 1)) == 0,
+                "power-of-two tile sides");
+  const uint32_t ux = (uint32_t)x, uy = (uint32_t)y, uz = (uint32_t)z;
+  const uint32_t tx = ((uint32_t)G.nx + LG::TX - 1) / LG::TX, ty = ((uint32_t)G.ny + LG::TY - 1) / LG::TY;
+  const uint32_t tile = ux / LG::TX + tx * (uy / LG::TY + ty * (ND == 3 ? uz / LG::TZ : 0u));
+  return tile * (uint32_t)LG::NFACE +
+         (uint32_t)face_index<ND>((int)(ux % LG::TX), (int)(uy % LG::TY), ND == 3 ? (int)(uz % LG::TZ) : 0);
+}
 
 // The cells of a label tile that one thread owns: cell i = threadIdx.x +
 // k kThreads for k < PER_THREAD. kThreads is a multiple of TX, so the thread
@@ -152,24 +219,35 @@ __device__ __forceinline__ int extremum_vertex(const Geom& G, uint32_t t, int x0
   return (x0 + ci % LG::TX) + G.nx * ((y0 + (ci / LG::TX) % LG::TY) + G.ny * (z0 + ci / (LG::TX * LG::TY)));
 }
 
-// Shell cells' halo coordinates packed hx | hy << 8 | hz << 16, for a
-// block's shared decode table (filled by every thread, then synchronised).
+// Exit-table slot of shell cell s of a tile, less the tile's own first slot
+// (tile index times NFACE), in a field of tx by ty (by any) label tiles: the
+// cell lies in the neighbouring tile a fixed index step away, at a fixed face
+// cell of it. Valid for shell cells inside the grid.
 template <int ND>
-__device__ __forceinline__ void fill_shell_table(uint32_t* tab) {
-  for (int s = threadIdx.x; s < LabelGeom<ND>::SHELL; s += blockDim.x) {
-    int hx, hy, hz;
-    shell_cell<ND>(s, hx, hy, hz);
-    tab[s] = (uint32_t)hx | ((uint32_t)hy << 8) | ((uint32_t)hz << 16);
-  }
+__host__ __device__ __forceinline__ int shell_slot_delta(int s, int tx, int ty) {
+  using LG = LabelGeom<ND>;
+  int hx, hy, hz;
+  shell_cell<ND>(s, hx, hy, hz);
+  // halo coordinate h: tile step -1 (h = 0), 0 (1 .. side), +1 (side + 1),
+  // and the coordinate within that tile
+  auto split = [](int h, int side, int& step, int& l) {
+    step = (h == 0) ? -1 : (h == side + 1 ? 1 : 0);
+    l = h - 1 - step * side;
+  };
+  int sx, lx, sy, ly, sz = 0, lz = 0;
+  split(hx, LG::TX, sx, lx);
+  split(hy, LG::TY, sy, ly);
+  if (ND == 3) split(hz, LG::TZ, sz, lz);
+  return (sx + tx * (sy + ty * sz)) * LG::NFACE + face_index<ND>(lx, ly, lz);
 }
 
-// Global index of shell cell s of the tile starting at (x0, y0, z0), from
-// the shared decode table.
+// A block's table of shell_slot_delta for the field of geometry G (filled by
+// every thread, then synchronised).
 template <int ND>
-__device__ __forceinline__ int shell_vertex(const Geom& G, const uint32_t* tab, int s, int x0, int y0, int z0) {
-  const uint32_t c = tab[s];
-  return (x0 - 1 + (int)(c & 0xffu)) +
-         G.nx * ((y0 - 1 + (int)((c >> 8) & 0xffu)) + G.ny * (ND == 3 ? z0 - 1 + (int)(c >> 16) : 0));
+__device__ __forceinline__ void fill_slot_table(int* tab, const Geom& G) {
+  using LG = LabelGeom<ND>;
+  const int tx = (G.nx + LG::TX - 1) / LG::TX, ty = (G.ny + LG::TY - 1) / LG::TY;
+  for (int s = threadIdx.x; s < LG::SHELL; s += blockDim.x) tab[s] = shell_slot_delta<ND>(s, tx, ty);
 }
 
 // Marks every label tile whose tile or one-vertex halo contains vertex u:
@@ -258,13 +336,15 @@ __global__ void __launch_bounds__(kThreads) k_init(GroupArgs<T> A) {
       F.epoch[v] = 0;
     }
     if (err) atomicOr(&st->err_bits, err);
-    // tile-exit bitmaps start empty; every label tile starts dirty
-    for (int w = (v0 >> 5) + threadIdx.x; w < ((v1 + 31) >> 5); w += blockDim.x) {
-      F.ex[0][w] = 0;
-      F.ex[1][w] = 0;
-    }
     {
       const int ntl = F.units[K_LABEL], nu = F.units[K_DENSE], lu = u_ - pre[i];
+      // no exit is marked yet (the marks' words, shared out over the units)
+      const int nxw = (int)(F.nface / 4u), pw = (nxw + nu - 1) / nu;
+      for (int w = lu * pw + threadIdx.x; w < min(nxw, (lu + 1) * pw); w += blockDim.x) {
+        reinterpret_cast<uint32_t*>(F.xm[0])[w] = 0u;
+        reinterpret_cast<uint32_t*>(F.xm[1])[w] = 0u;
+      }
+      // every label tile starts dirty
       const int per = (ntl + nu - 1) / nu;
       for (int t = lu * per + threadIdx.x; t < min(ntl, (lu + 1) * per); t += blockDim.x) {
         F.tdirty[t] = 1;
@@ -278,20 +358,24 @@ __global__ void __launch_bounds__(kThreads) k_init(GroupArgs<T> A) {
 }
 
 // ---------------------------------------------------------------------------
-// C-loop sweep (msz_sweep.cuh): extremum flags of g per vertex, false critical
-// points of every type counted with warp ballots and appended to the field's
-// case list. Units are tiles (x-y tile by a chunk of planes). With kTMA a
-// producer warp streams the planes of the block's active tiles through a
-// ring of TMA stages (full/empty mbarriers, bounded waits); otherwise the
-// consumers fill one stage with plain loads.
+// C-loop sweep (msz_sweep.cuh): extremum flags of g per vertex; the false
+// critical points get their class bits, and their counts per type go to the
+// field and to the per-tile counts (one warp reduction of byte-packed counts
+// per warp and plane that holds any). Units are tiles (x-y tile by a chunk of
+// planes). With kTMA a producer warp streams the planes of the block's
+// active tiles through a ring of TMA stages (full/empty mbarriers, bounded
+// waits); otherwise the consumers fill one stage with plain loads. A thread
+// owns VX vertices of one row (16 bytes of g: one vector load per staged
+// row) and carries the previous plane's partial extrema from plane to plane,
+// so each plane is read from shared memory once.
 // ---------------------------------------------------------------------------
 template <class T, int ND, bool kTMA>
 __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND>::NT)
     k_csweep(GroupArgs<T> A) {
   using SG = SweepGeom<T, ND>;
-  constexpr int RPT = SG::RPT;
+  constexpr int VX = SG::VX;
   constexpr int NCW = SG::NT / 32;  // consumer warps
-  using PV = PlaneVals<T, RPT>;
+  using PV = Partials<T, VX>;
   static_assert((SG::STAGES & (SG::STAGES - 1)) == 0, "power-of-two stages");
   constexpr int SM1 = SG::STAGES - 1;
   __shared__ alignas(128) unsigned char smem[(kTMA ? SG::STAGES : 1) * SG::STAGE_BYTES];
@@ -302,7 +386,8 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
   const int* pre = A.prefix + K_SWEEP * (A.nf + 1);
   const int tid = threadIdx.x;
   const bool producer = kTMA && tid >= SG::NT;
-  const int tx = tid % SG::TX, w = (tid / SG::TX) % (SG::NT / SG::TX);
+  // the thread's first column in the tile and its row
+  const int tx = (tid % SG::TPR) * VX, w = (tid / SG::TPR) % SG::TY;
   const int lane = tid & 31;
 
   // Next active tile of this block at or after global unit u: field index,
@@ -395,43 +480,45 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
       const Geom G = F.G;
       const int chunk = t.ppt - 2;
       const int axis_n = (ND == 3) ? G.nz : G.ny;
-      uint32_t vmask = 0;  // this thread's vertices inside the grid in x and y
-      {
-        const int x = t.x0 + tx;
+      const int x = t.x0 + tx;                     // the thread's first vertex
+      const int y = (ND == 3) ? t.y0 + w : 0;
+      uint32_t vmask = 0;  // bits 8k, 8k + 4: vertex k is inside the grid in x and y
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-          const int y = (ND == 3) ? t.y0 + RPT * w + k : 0;
-          if (x < G.nx && y < G.ny) vmask |= 0x11u << (8 * k);
-        }
-      }
+      for (int k = 0; k < VX; ++k)
+        if (x + k < G.nx && y < G.ny) vmask |= 0x11u << (8 * k);
+      // vertex range of the warp's row segment (contiguous indices), for the
+      // per-tile type counts
+      const int wx0 = t.x0 + ((tid % SG::TPR) & ~31) * VX;
+      const int wx1 = min(G.nx, wx0 + 32 * VX) - 1;
       uint32_t cnt[4] = {0, 0, 0, 0};
-
-      // One plane p of the tile: stage it, derive its quantities into dst
-      // (role B), then classify the vertices of plane A (Cv previous).
-      auto step = [&](int qq, int p, PV& dst, uint32_t& fd_dst, const PV& Cv, const PV& Av, uint32_t fdA) -> bool {
+      PV prev;                               // the previous plane's partials
+      T prevLM[VX], prevLm[VX];              // max / min over L*(v) of the previous plane
+      uint32_t prev_fd = 0;
+#pragma unroll
+      for (int k = 0; k < VX; ++k) prevLM[k] = prevLm[k] = qnan<T>();
+      for (int p = 0; p < t.ppt; ++p, ++q) {
         const int pcoord = t.c0 - 1 + p;  // plane coordinate (z in 3D, y in 2D)
-        unsigned char* sp = smem + (kTMA ? (qq & SM1) * SG::STAGE_BYTES : 0);
+        unsigned char* sp = smem + (kTMA ? (q & SM1) * SG::STAGE_BYTES : 0);
         const T* stage = reinterpret_cast<const T*>(sp);
+        PV cur;
+        uint32_t fd = 0;
         if (kTMA) {
           // lane 0 waits for the stage; the warp follows its decision
           bool got = true;
-          if (lane == 0) got = mbar_wait_or_abort(&full[qq & SM1], (uint32_t)((qq / SG::STAGES) & 1), &s_abort);
+          if (lane == 0) got = mbar_wait_or_abort(&full[q & SM1], (uint32_t)((q / SG::STAGES) & 1), &s_abort);
           got = __shfl_sync(kFull, got, 0);
           if (!got) {
             if (lane == 0) atomicExch(&s_abort, 1);
-            return false;
+            ok = false;
+            break;
           }
-          dst = plane_vals<T, ND>(stage, tx, w);
-          if (ND == 3) {
-            uint32_t fd = 0;
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) fd |= (uint32_t)sp[SG::G_BYTES + (RPT * w + k) * SG::TX + tx] << (8 * k);
-            fd_dst = fd;
-          } else {
-            fd_dst = sp[SG::G_BYTES + tx];
-          }
+          plane_partials<T, ND>(stage, SG::PADX + tx, w, cur);
+          const unsigned char* dp = sp + SG::G_BYTES + w * SG::TX + tx;
+          if constexpr (VX == 4) fd = *reinterpret_cast<const uint32_t*>(dp);
+          else if constexpr (VX == 2) fd = *reinterpret_cast<const uint16_t*>(dp);
+          else fd = *dp;
           __syncwarp();
-          if (lane == 0) mbar_arrive(&empty[qq & SM1]);
+          if (lane == 0) mbar_arrive(&empty[q & SM1]);
         } else {
           __syncthreads();
           T* wst = reinterpret_cast<T*>(sp);
@@ -444,72 +531,93 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
             wst[k] = in ? F.g[gx + G.nx * (gy + G.ny * gz)] : qnan<T>();
           }
           __syncthreads();
-          dst = plane_vals<T, ND>(stage, tx, w);
-          uint32_t fd = 0;
+          plane_partials<T, ND>(stage, SG::PADX + tx, w, cur);
+          const int vy = (ND == 3) ? y : pcoord, vz = (ND == 3) ? pcoord : 0;
 #pragma unroll
-          for (int k = 0; k < RPT; ++k) {
-            const int vx = t.x0 + tx, vy = (ND == 3) ? t.y0 + RPT * w + k : pcoord, vz = (ND == 3) ? pcoord : 0;
-            if (vx < G.nx && vy >= 0 && vy < G.ny && vz >= 0 && vz < G.nz)
-              fd |= (uint32_t)F.fdir[vx + G.nx * (vy + G.ny * vz)] << (8 * k);
-          }
-          fd_dst = fd;
+          for (int k = 0; k < VX; ++k)
+            if (x + k < G.nx && vy >= 0 && vy < G.ny && vz >= 0 && vz < G.nz)
+              fd |= (uint32_t)F.fdir[(x + k) + G.nx * (vy + G.ny * vz)] << (8 * k);
         }
-        if (p >= 2) {
-          // g's extremum flags and f's, packed at bits 8k (max) and 8k+4
-          // (min) for vertex k; a vertex is a case when they differ.
-          uint32_t gb = 0;
+        if (p >= 1) {
+          if (p >= 2) {
+            // Plane p - 1 (A; this plane B, the one before C): g's extremum
+            // flags and f's, at bits 8k (max) and 8k + 4 (min) for vertex k;
+            // a vertex is a case when they differ.
+            uint32_t gb = 0;
 #pragma unroll
-          for (int k = 0; k < RPT; ++k)
-            gb |= ((uint32_t)is_max_at<T, RPT>(Cv, Av, dst, k) << (8 * k)) |
-                  ((uint32_t)is_min_at<T, RPT>(Cv, Av, dst, k) << (8 * k + 4));
-          const uint32_t fa = fdA;
-          const uint32_t fb = fa & (fa >> 1) & (fa >> 2) & (fa >> 3) & 0x11111111u;  // nibble == 15
-          uint32_t diff = (gb ^ fb) & vmask;
-          if (!(p - 2 < chunk && pcoord - 1 < axis_n)) diff = 0;
-          if (__any_sync(kFull, diff != 0)) {
-            const int x = t.x0 + tx;
-            const int z = (ND == 3) ? pcoord - 1 : 0;
+            for (int k = 0; k < VX; ++k) {
+              const T g = prev.a0[k];
+              const T maxU = vmax3(prev.uM[k], cur.a0[k], cur.uM[k]);
+              const T minU = vmin3(prev.um[k], cur.a0[k], cur.um[k]);
+              const bool gmax = !(maxU >= g) && !(prevLM[k] > g);
+              const bool gmin = !(minU < g) && !(prevLm[k] <= g);
+              gb |= ((uint32_t)gmax << (8 * k)) | ((uint32_t)gmin << (8 * k + 4));
+            }
+            const uint32_t fa = prev_fd;
+            const uint32_t fb = fa & (fa >> 1) & (fa >> 2) & (fa >> 3) & 0x11111111u;  // nibble == 15
+            uint32_t diff = (gb ^ fb) & vmask;
+            if (!(p - 2 < chunk && pcoord - 1 < axis_n)) diff = 0;
+            if (__any_sync(kFull, diff != 0)) {
+              // false types of the thread's vertices: bit 0 FPmax, 1 FPmin,
+              // 2 FNmax, 3 FNmin (byte k for vertex k); type counts packed
+              // one per byte for a single warp reduction
+              const int z = (ND == 3) ? pcoord - 1 : 0;
+              const int yy = (ND == 3) ? y : pcoord - 1;
+              const int v0 = x + G.nx * (yy + G.ny * z);
+              uint32_t codes = 0, packed = 0;
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-              const int y = (ND == 3) ? t.y0 + RPT * w + k : pcoord - 1;
-              const uint32_t gk = gb >> (8 * k), fk = fb >> (8 * k), dk = diff >> (8 * k);
-              unsigned bits = 0;
-              if (dk & 0x11u) {
-                const unsigned gmx = gk & 1u, gmn = (gk >> 4) & 1u, fmx = fk & 1u, fmn = (fk >> 4) & 1u;
-                bits = (gmx & ~fmx) | ((gmn & ~fmn) << 1) | ((fmx & ~gmx) << 2) | ((fmn & ~gmn) << 3);
+              for (int k = 0; k < VX; ++k) {
+                const uint32_t gk = gb >> (8 * k), fk = fb >> (8 * k);
+                uint32_t bits = 0;
+                if ((diff >> (8 * k)) & 0x11u) {
+                  const uint32_t gmx = gk & 1u, gmn = (gk >> 4) & 1u, fmx = fk & 1u, fmn = (fk >> 4) & 1u;
+                  bits = (gmx & ~fmx) | ((gmn & ~fmn) << 1) | ((fmx & ~gmx) << 2) | ((fmn & ~gmn) << 3);
+                }
+                codes |= bits << (8 * k);
+                packed += (bits & 1u) | ((bits & 2u) << 7) | ((bits & 4u) << 14) | ((bits & 8u) << 21);
+                // class bits of the false vertices (cls starts zeroed)
+                if (bits) F.cls[v0 + k] = (uint8_t)bits;
               }
-              uint32_t bc[4];
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                bc[c] = __ballot_sync(kFull, (bits >> c) & 1u);
-                if (lane == 0) cnt[c] += __popc(bc[c]);
-              }
-              if (__any_sync(kFull, bits != 0)) {
-                // class bits of the false vertices (cls starts zeroed) and the
-                // per-tile type counts: one atomic per (tile, type) of the warp
-                const int v = x + G.nx * (y + G.ny * z);
-                if (bits) F.cls[v] = (uint8_t)bits;
-                const int ct = bits ? v / kEmitTile : -1;
-                const uint32_t grp = __match_any_sync(kFull, ct);
-                if (bits && lane == __ffs(grp) - 1) {
+              const uint32_t tot = __reduce_add_sync(kFull, packed);
+              // per-tile type counts: one atomic per type when the warp's
+              // row segment lies in one count tile, else one per vertex
+              const int wv0 = wx0 + G.nx * (yy + G.ny * z), wv1 = wx1 + G.nx * (yy + G.ny * z);
+              const int ct = wv0 / kEmitTile;
+              if (ct == wv1 / kEmitTile) {
+                if (lane == 0) {
 #pragma unroll
                   for (int c = 0; c < 4; ++c) {
-                    const uint32_t nc = __popc(bc[c] & grp);
+                    const uint32_t nc = (tot >> (8 * c)) & 0xffu;
                     if (nc) atomicAdd(&F.ccnt[ct * 4 + c], nc);
                   }
                 }
+              } else {
+#pragma unroll
+                for (int k = 0; k < VX; ++k) {
+                  const uint32_t bits = (codes >> (8 * k)) & 15u;
+#pragma unroll
+                  for (int c = 0; c < 4; ++c)
+                    if ((bits >> c) & 1u) atomicAdd(&F.ccnt[((v0 + k) / kEmitTile) * 4 + c], 1u);
+                }
+              }
+              if (lane == 0) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) cnt[c] += (tot >> (8 * c)) & 0xffu;
               }
             }
           }
+          // L*(v) extrema of this plane (its LLL corner, the previous plane's
+          // centre and LLL corner)
+#pragma unroll
+          for (int k = 0; k < VX; ++k) {
+            const T LM = vmax3(cur.lM[k], prev.a0[k], prev.lM[k]);
+            const T Lm = vmin3(cur.lm[k], prev.a0[k], prev.lm[k]);
+            prevLM[k] = LM;
+            prevLm[k] = Lm;
+          }
         }
-        return true;
-      };
-
-      PV P0{}, P1{}, P2{};
-      uint32_t f0 = 0, f1 = 0, f2 = 0;
-      for (int p = 0; p < t.ppt && ok; p += 3, q += 3) {  // planes rotate through P0, P1, P2
-        ok = step(q, p, P0, f0, P1, P2, f2) && step(q + 1, p + 1, P1, f1, P2, P0, f0) &&
-             step(q + 2, p + 2, P2, f2, P0, P1, f1);
+        prev = cur;
+        prev_fd = fd;
       }
       if (!ok) break;
       // Tile done by this warp: flush its counts; the last consumer warp to
@@ -869,22 +977,22 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
   uint32_t* PP = reinterpret_cast<uint32_t*>(lsm + (JOB ? 0 : ((LG::HALO * sizeof(T) + 15) / 16) * 16));
   const int* pre = A.prefix + K_LABEL * (A.nf + 1);
   constexpr int HS = LG::SX, HSS = LG::SX * LG::SY;
-  // halo-cell exit bits (ascending, descending); padded for the two-word reads
-  constexpr int kExWords = (LG::HALO + 31) / 32 + 2;
-  constexpr int kSegs = (LG::SX + 31) / 32;
-  __shared__ uint32_t exs[2][kExWords];
-  // the same exits by shell index (the tile's record for the label lookups)
+  // the tile's exits by shell index (ascending, descending lines): the
+  // tile's record for the label lookups
   constexpr int kShW = LabelGeom<ND>::SHW;
   __shared__ uint32_t shx[2][kShW];
   // halo-index offset of each stencil slot (slot 15: the cell itself)
   __shared__ int s_off[16];
   if (threadIdx.x < 16) s_off[threadIdx.x] = slot_offset((int)threadIdx.x, ND, HS, HSS);
+  __shared__ int s_slotd[LG::SHELL];  // shell cells' exit-table slots, relative (shell_slot_delta)
+  int slot_field = -1;                // the field s_slotd was filled for
   auto active = [](const Field<T>& F) {
     return F.st->action == ACT_LABELS && F.st->lstate == L_INIT && (F.st->ljob != 0) == JOB;
   };
   auto none = [](DevState*) {};
   auto done = [&](DevState* st) {
-    st->lstate = L_COUNT;
+    st->lstate = L_JUMP;
+    st->jump_rounds = 0;
     st->ticks++;
     log_work(A);
   };
@@ -902,10 +1010,13 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
     const bool redo = !job || (F.tdirty[tile] & 1);
     __syncthreads();  // the block's previous tile is done with the shared arrays
     if (!redo) continue;
+    if (fi != slot_field) {  // the same for every thread of the block
+      fill_slot_table<ND>(s_slotd, G);
+      slot_field = fi;
+    }
     const int x0 = (tile % tiles_x) * LG::TX;
     const int y0 = ((tile / tiles_x) % tiles_y) * LG::TY;
     const int z0 = (tile / (tiles_x * tiles_y)) * LG::TZ;
-    for (int k = threadIdx.x; k < 2 * kExWords; k += kThreads) exs[k / kExWords][k % kExWords] = 0u;
     for (int k = threadIdx.x; k < 2 * kShW; k += kThreads) shx[k / kShW][k % kShW] = 0u;
     // Job 0 reads f's values with the halo; job 1 needs no values: g's
     // direction bytes are kept exact by the classification that follows
@@ -954,8 +1065,7 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
       const uint32_t blo = (uint32_t)(lx == 0) | ((uint32_t)(ly == 0) << 1) | ((uint32_t)(ND == 3 && lz == 0) << 2);
       if (bhi | blo) {
         // the exit's halo coordinates from the cell's and the slot's
-        auto mark_exit = [&](int d, int sl, int ch) {
-          atomicOr(&exs[d][ch >> 5], 1u << (ch & 31));
+        auto mark_exit = [&](int d, int sl) {
           constexpr int npos = Slots<ND>::NPOS;
           const bool neg = sl >= npos;
           const int m = slot_mask(ND, neg ? sl - npos : sl), sg = neg ? -1 : 1;
@@ -963,8 +1073,8 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
                                          (ND == 3) ? lz + 1 + sg * ((m >> 2) & 1) : 0);
           atomicOr(&shx[d][sh >> 5], 1u << (sh & 31));
         };
-        if (leaves_tile<ND>(sa, bhi, blo)) mark_exit(0, sa, ca);
-        if (leaves_tile<ND>(sd, bhi, blo)) mark_exit(1, sd, cd);
+        if (leaves_tile<ND>(sa, bhi, blo)) mark_exit(0, sa);
+        if (leaves_tile<ND>(sd, bhi, blo)) mark_exit(1, sd);
       }
     }
     if (!job) {
@@ -1003,27 +1113,33 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
     // the tile's exit record
     for (int k = threadIdx.x; k < 2 * kShW; k += kThreads)
       F.texit[(size_t)tile * 2 * kShW + k] = shx[k / kShW][k % kShW];
-    // Exit bits into the field's bitmaps: one atomic per global word that a
-    // halo-row segment (at most 32 cells, contiguous in x) touches.
-    for (int it = threadIdx.x; it < 2 * LG::ROWS * kSegs; it += kThreads) {
-      const int d = it / (LG::ROWS * kSegs), r = it % (LG::ROWS * kSegs), row = r / kSegs;
-      const int hx0 = (r % kSegs) * 32, len = min(32, LG::SX - hx0);
-      const int bit0 = row * LG::SX + hx0, w0 = bit0 >> 5, off = bit0 & 31;
-      uint32_t m = exs[d][w0] >> off;
-      if (off) m |= exs[d][w0 + 1] << (32 - off);
-      if (len < 32) m &= (1u << len) - 1u;
-      if (!m) continue;
-      const int hy = row % LG::SY, hz = row / LG::SY;
-      // cells with bits are in the grid, so the first one's index is >= 0
-      const long long e0 =
-          (long long)(x0 - 1 + hx0) + (long long)G.nx * ((y0 - 1 + hy) + (long long)G.ny * ((ND == 3) ? z0 - 1 + hz : 0));
-      const long long first = e0 + __ffs(m) - 1;
-      const long long w = first >> 5;
-      const int shift = (int)(e0 - (w << 5));  // position of segment bit 0 in word w (-31 .. 31)
-      const uint64_t M = shift >= 0 ? ((uint64_t)m << shift) : ((uint64_t)m >> -shift);
-      uint32_t* ex = F.ex[d];
-      if ((uint32_t)M) atomicOr(&ex[w], (uint32_t)M);
-      if ((uint32_t)(M >> 32)) atomicOr(&ex[w + 1], (uint32_t)(M >> 32));
+    // First-level exit-table entries of the tile's face cells (a slot per
+    // face cell, see exit_slot): a line that ends inside the tile gives its
+    // label (kRes), one that leaves it the slot of the exit it leaves
+    // through. Entries of tiles that are not recomputed stay valid.
+    const uint32_t tbase = (uint32_t)tile * (uint32_t)LG::NFACE;
+    auto exit_of = [&](uint32_t s) -> uint32_t {
+      if (!MSZ_IN(st, s, LG::SHELL)) s = 0;
+      const uint32_t sl = tbase + (uint32_t)s_slotd[s];
+      return MSZ_IN(st, sl, F.nface) ? sl : 0u;
+    };
+    for (int f = threadIdx.x; f < LG::NFACE; f += kThreads) {
+      int lx, ly, lz;
+      face_cell<ND>(f, lx, ly, lz);
+      if (x0 + lx >= G.nx || y0 + ly >= G.ny || z0 + lz >= G.nz) continue;
+      const uint32_t p = PP[(lx + 1) + HS * ((ly + 1) + LG::SY * ((ND == 3) ? lz + 1 : 0))];
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const uint32_t t = d ? (p >> 16) : (p & 0xffffu);
+        F.lf[d][tbase + f] = (t & kTermExtr) ? ((uint32_t)extremum_vertex<ND>(G, t, x0, y0, z0) | kRes)
+                                             : exit_of(t & kTermIdx);
+      }
+    }
+    // Exit marks (the entries the jumping resolves): the slot of each exit
+    // of the tile's lines. Marks are cleared only when a fix starts.
+    for (int k = threadIdx.x; k < 2 * kShW; k += kThreads) {
+      const int d = k / kShW, wd = k % kShW;
+      for (uint32_t b = shx[d][wd]; b; b &= b - 1) F.xm[d][exit_of((uint32_t)(wd * 32 + __ffs(b) - 1))] = 1;
     }
     if (!job) {
       // g's first direction bytes; from here on the classification after
@@ -1045,238 +1161,25 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
   tl.flush(A, K_LABEL, none, done);
 }
 
-// Labels, second level (Sec. 5.2, across tiles). The tile exits of a
-// direction are ranked in bitmap order: k_ecount counts them per bitmap word
-// and dense unit, k_escan turns the unit counts into offsets. k_efill writes
-// the compact exit table: entry rank(e) holds e's label when e's tile
-// terminal is an extremum (flag kRes), else the rank of that terminal (an
-// exit of e's tile). k_jump does pointer jumping on the table, one thread per
-// entry, until every entry holds a label, which label resolution then reads
-// by the exit's rank.
-__device__ __forceinline__ uint32_t exit_rank(const uint32_t* ex, const uint32_t* ep, const uint32_t* ub, int e) {
-  const int w = e >> 5;
-  return ub[e / kDenseChunk] + ep[w] + (uint32_t)__popc(ex[w] & ((1u << (e & 31)) - 1u));
-}
-
-// The same from the (bitmap word, exits before it) pairs that k_efill writes.
-__device__ __forceinline__ uint32_t exit_rank2(const uint2* xr, int e) {
-  const uint2 p = xr[e >> 5];
-  return p.y + (uint32_t)__popc(p.x & ((1u << (e & 31)) - 1u));
-}
-
-template <class T>
-__global__ void __launch_bounds__(kThreads) k_ecount(GroupArgs<T> A) {
-  static_assert(kDenseChunk == 32 * kThreads, "one bitmap word per thread and dense unit");
-  const int* pre = A.prefix + K_DENSE * (A.nf + 1);
-  __shared__ uint32_t wsum[2][kThreads / 32];
-  auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_COUNT; };
-  auto none = [](DevState*) {};
-  auto done = [&](DevState* st) {
-    st->lstate = L_SCAN;
-    st->ticks++;
-    log_work(A);
-  };
-  UnitTally tl;
-  MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
-    tl.enter(A, K_DENSE, i, none, done);
-    __syncthreads();  // wsum of the block's previous unit is read
-    const Field<T>& F = A.fields[i];
-    DevState* st = F.st;
-    const int u = u_ - pre[i];
-    const int nw = (F.G.n + 31) >> 5;
-    const int w = u * kThreads + threadIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t c[2], incl[2];
-#pragma unroll
-    for (int d = 0; d < 2; ++d) {
-      c[d] = (w < nw) ? (uint32_t)__popc(F.ex[d][w]) : 0u;
-      incl[d] = c[d];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, incl[d], o);
-        if (lane >= o) incl[d] += y;
-      }
-      if (lane == 31) wsum[d][warp] = incl[d];
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-#pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        uint32_t x = (lane < kThreads / 32) ? wsum[d][lane] : 0u, y = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t z = __shfl_up_sync(kFull, y, o);
-          if (lane >= o) y += z;
-        }
-        if (lane < kThreads / 32) wsum[d][lane] = y - x;  // exclusive warp offsets
-        if (lane == kThreads / 32 - 1) F.ub[d][u] = y;     // unit total (scanned by k_escan)
-      }
-    }
-    __syncthreads();
-    if (w < nw) {
-      F.ep[0][w] = wsum[0][warp] + incl[0] - c[0];
-      F.ep[1][w] = wsum[1][warp] + incl[1] - c[1];
-    }
-    log_units_warp(A, st, KID_ECOUNT, (w < nw) ? 1u : 0u);
-  }
-  tl.flush(A, K_DENSE, none, done);
-}
-
-// Exclusive scan of the unit exit counts of both directions, one block per
-// field of the group (grid = number of fields).
-template <class T>
-__global__ void __launch_bounds__(1024) k_escan(GroupArgs<T> A) {
-  __shared__ uint32_t ws[32];
-  __shared__ uint32_t carry;
-  if ((int)blockIdx.x >= A.nf) return;
-  const Field<T>& F = A.fields[blockIdx.x];
-  DevState* st = F.st;
-  if (!(st->action == ACT_LABELS && st->lstate == L_SCAN)) return;
-  const int U = F.units[K_DENSE];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int d = 0; d < 2; ++d) {
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int b = 0; b < U; b += blockDim.x) {
-      const int k = b + threadIdx.x;
-      const uint32_t x = (k < U) ? F.ub[d][k] : 0u;
-      uint32_t y = x;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t z = __shfl_up_sync(kFull, y, o);
-        if (lane >= o) y += z;
-      }
-      if (lane == 31) ws[warp] = y;
-      __syncthreads();
-      if (warp == 0) {
-        const uint32_t a = (lane < (int)(blockDim.x >> 5)) ? ws[lane] : 0u;
-        uint32_t q = a;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t z = __shfl_up_sync(kFull, q, o);
-          if (lane >= o) q += z;
-        }
-        ws[lane] = q - a;
-      }
-      __syncthreads();
-      const uint32_t c0 = carry;
-      if (k < U) F.ub[d][k] = c0 + ws[warp] + y - x;
-      __syncthreads();
-      if (threadIdx.x == blockDim.x - 1) carry = c0 + ws[warp] + y;
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) st->nexit[d] = carry;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    st->lstate = L_FILL;
-    st->ticks++;
-    log_units(A, st, KID_ESCAN, 1);
-    log_work(A);
-  }
-}
-
-// One bitmap word per thread; the word's exits (ranks r, r + 1, ...) are
-// handled in batches of kBatch so that their loads are in flight together.
-// An exit's entry comes from its own tile terminal, decoded against its
-// tile's origin (the word's row gives the coordinates; the shell cells'
-// halo coordinates come from a shared table): the rank of the exit where
-// its line leaves that tile, or (kRes) the extremum it ends at inside.
-constexpr int kBatch = 4;
-template <class T, int ND>
-__global__ void __launch_bounds__(kThreads, 6) k_efill(GroupArgs<T> A) {
-  const int* pre = A.prefix + K_DENSE * (A.nf + 1);
-  __shared__ uint32_t s_shell[LabelGeom<ND>::SHELL];
-  fill_shell_table<ND>(s_shell);
-  __syncthreads();
-  auto active = [](const Field<T>& F) { return F.st->action == ACT_LABELS && F.st->lstate == L_FILL; };
-  auto none = [](DevState*) {};
-  auto done = [&](DevState* st) {
-    st->lstate = L_JUMP;
-    st->jump_rounds = 0;
-    st->ticks++;
-    log_work(A);
-  };
-  UnitTally tl;
-  MSZ_ACTIVE_UNITS(A, K_DENSE, pre, i, active) {
-    tl.enter(A, K_DENSE, i, none, done);
-    const Field<T>& F = A.fields[i];
-    DevState* st = F.st;
-    const int u = u_ - pre[i];
-    const int nw = (F.G.n + 31) >> 5;
-    const int w = u * kThreads + threadIdx.x;
-    uint32_t nex = 0;
-    if (w < nw) {
-      int xw, yw, zw;
-      coords(F.G, w << 5, xw, yw, zw);
-      uint32_t m2[2], r2[2];  // both directions' words, loaded before any table store
-#pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        m2[d] = F.ex[d][w];
-        r2[d] = F.ub[d][u] + F.ep[d][w];
-      }
-#pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        const uint32_t *ex = F.ex[d], *ep = F.ep[d], *ub = F.ub[d];
-        uint32_t* lc = F.lc[d];
-        uint32_t r = r2[d];
-        uint32_t m = m2[d];
-        F.xr[d][w] = make_uint2(m, r);  // for label resolution after the jumping
-        nex += __popc(m);
-        while (m) {
-          int e[kBatch];
-          uint32_t t[kBatch];
-          int c = 0;
-#pragma unroll
-          for (int j = 0; j < kBatch; ++j) {
-            e[j] = m ? (w << 5) + __ffs(m) - 1 : -1;
-            if (m) {
-              m &= m - 1;
-              ++c;
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < kBatch; ++j) t[j] = (e[j] >= 0) ? (F.term[e[j]] >> (16 * d)) & 0xffffu : 0u;
-#pragma unroll
-          for (int j = 0; j < kBatch; ++j) {
-            uint32_t g = kExt;
-            if (j < c) {
-              int x = xw + (e[j] - (w << 5)), y = yw, z = zw, x0, y0, z0;
-              if (x >= F.G.nx) coords(F.G, e[j], x, y, z);
-              tile_origin_of<ND>(x, y, z, x0, y0, z0);
-              g = (t[j] & kTermExtr) ? ((uint32_t)extremum_vertex<ND>(F.G, t[j], x0, y0, z0) | kExt)
-                                     : (uint32_t)shell_vertex<ND>(F.G, s_shell, (int)(t[j] & kTermIdx), x0, y0, z0);
-            }
-            if (!(g & kExt) && !MSZ_IN(st, g, F.G.n)) g = kExt;
-            t[j] = g;
-          }
-          // every entry of the batch before any store: a store to the table
-          // may alias the bitmap and prefix words as far as the compiler
-          // knows, so interleaving them would run the rank loads one by one
-#pragma unroll
-          for (int j = 0; j < kBatch; ++j)
-            t[j] = (t[j] & kExt) ? ((t[j] & ~kExt) | kRes) : exit_rank(ex, ep, ub, (int)t[j]);
-#pragma unroll
-          for (int j = 0; j < kBatch; ++j)
-            if (j < c && MSZ_IN(st, r + j, F.G.n)) lc[r + j] = t[j];
-          r += c;
-        }
-      }
-    }
-    log_units_warp(A, st, KID_EFILL, nex);
-  }
-  tl.flush(A, K_DENSE, none, done);
-}
-
-// One round of label propagation on the compact exit tables. Each entry
-// that holds a rank follows its line through the exits of the tiles it
-// crosses until it reaches a label (or A.chase steps), storing every pointer
-// it reaches in its own entry. All entries do so at once: a value read is the
-// entry of an exit further along the same line, or the line's label, whether
-// it was read before or after its owner advanced it, so every step makes
-// progress and the other entries' stores shorten the walk. Loads bypass L1 to
-// see those stores. A round that leaves no rank ends the labelling. An entry
-// follows at most A.chase steps per launch.
+// Labels, second level (Sec. 5.2, across tiles). Each direction has two
+// exit tables with one slot per face cell of every label tile (exit_slot):
+// lf holds the first-level entries that k_label_tile writes for the face
+// cells of each tile it recomputes (a label with kRes, or the slot of the
+// exit where the cell's line leaves its tile), lw the entries being resolved.
+// xm marks the slots that are exits of some tile's lines; only those are
+// resolved (and looked up).
+//
+// k_jump: label propagation by pointer jumping over the marked slots. The
+// evaluation's first launch starts each marked entry in lw from lf, one step
+// along its line already taken (lw still holds the previous evaluation's
+// entries, so that launch reads lf only). Later launches walk lw: a walk
+// stores each pointer it reaches in its own entry, and all entries walk at
+// once. A value read is the entry of an exit further along the same line, or
+// the line's label, whether it was read before or after its owner advanced
+// it, so every step makes progress and the other entries' stores shorten the
+// walk (each read skips the steps its owner has taken). Loads of lw bypass
+// L1 to see those stores. An entry takes at most A.chase steps per launch; a
+// launch that leaves no pointer ends the labelling.
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
   const int* pre = A.prefix + K_DENSE * (A.nf + 1);
@@ -1296,36 +1199,54 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
     const uint64_t u = (uint64_t)(u_ - pre[i]), U = (uint64_t)F.units[K_DENSE];
+    // the evaluation's first launch (the state only changes once every unit
+    // of the launch is done)
+    const bool first = st->jump_rounds == 0;
     uint32_t acc = 0;
     constexpr int kJB = 4;  // entries per thread and iteration, their walks advanced together
+    const uint32_t ne = F.nface, chunk = (ne + (uint32_t)U - 1u) / (uint32_t)U;
+    const uint32_t r0 = min(ne, chunk * (uint32_t)u), re = min(ne, r0 + chunk);  // this unit's share
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
-      // this unit's equal share of the direction's table
-      const uint32_t ne = st->nexit[d], chunk = (ne + (uint32_t)U - 1u) / (uint32_t)U;
-      const uint32_t r0 = min(ne, chunk * (uint32_t)u), re = min(ne, r0 + chunk);
-      uint32_t* lc = F.lc[d];
+      const uint32_t* lf = F.lf[d];
+      uint32_t* lw = F.lw[d];
+      const uint8_t* xm = F.xm[d];
       for (uint32_t rb = r0 + threadIdx.x; rb < re; rb += kJB * kThreads) {
-        uint32_t x[kJB];
+        uint32_t x[kJB], mk = 0;  // mk bit k: entry k is an exit
 #pragma unroll
         for (int k = 0; k < kJB; ++k) {
-          const bool in = rb + k * kThreads < re;
-          x[k] = in ? lc[rb + k * kThreads] : kRes;
-          acc += in ? 1u : 0u;
+          const uint32_t r = rb + k * kThreads;
+          if (r < re && xm[r]) mk |= 1u << k;
         }
-        for (int h = 0; h < A.chase; ++h) {
-          uint32_t walk = 0;  // bit k: entry k still holds a rank
+#pragma unroll
+        for (int k = 0; k < kJB; ++k) {
+          const uint32_t r = rb + k * kThreads;
+          x[k] = ((mk >> k) & 1u) ? (first ? __ldg(lf + r) : __ldcg(lw + r)) : kRes;
+        }
+        acc += (uint32_t)__popc(mk);
+        const int steps = first ? 1 : A.chase;
+        for (int h = 0; h < steps; ++h) {
+          uint32_t walk = 0;  // bit k: entry k still holds a pointer
 #pragma unroll
           for (int k = 0; k < kJB; ++k) walk |= (x[k] & kRes) ? 0u : (1u << k);
           if (!walk) break;
 #pragma unroll
           for (int k = 0; k < kJB; ++k)
-            if ((walk >> k) & 1u) x[k] = MSZ_IN(st, x[k], ne) ? __ldcg(lc + x[k]) : kRes;
+            if ((walk >> k) & 1u)
+              x[k] = MSZ_IN(st, x[k], ne) ? (first ? __ldg(lf + x[k]) : __ldcg(lw + x[k])) : kRes;
+          acc += (uint32_t)__popc(walk);
+          if (!first) {
+#pragma unroll
+            for (int k = 0; k < kJB; ++k)
+              if ((walk >> k) & 1u) lw[rb + k * kThreads] = x[k];
+            acc += (uint32_t)__popc(walk);
+          }
+        }
+        if (first) {
 #pragma unroll
           for (int k = 0; k < kJB; ++k)
-            if ((walk >> k) & 1u) {
-              lc[rb + k * kThreads] = x[k];
-              acc += 2;
-            }
+            if ((mk >> k) & 1u) lw[rb + k * kThreads] = x[k];
+          acc += (uint32_t)__popc(mk);
         }
 #pragma unroll
         for (int k = 0; k < kJB; ++k) open[0] += (x[k] & kRes) ? 0u : 1u;
@@ -1365,8 +1286,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_rcheck(GroupArgs<T> A) {
   // tile's exit record (which of them its lines leave through)
   __shared__ uint32_t s_lab[2][LG::SHELL];
   __shared__ uint32_t s_shx[2 * LabelGeom<ND>::SHW];
-  __shared__ uint32_t s_shell[LG::SHELL];  // shell cells' halo coordinates
-  fill_shell_table<ND>(s_shell);
+  __shared__ int s_slotd[LG::SHELL];  // shell cells' exit-table slots, relative (shell_slot_delta)
+  int slot_field = -1;                // the field s_slotd was filled for
   // the tile's exits as bit positions of its record (direction * SHW * 32 +
   // shell index), and the scan sums that list them
   __shared__ uint16_t s_xl[2 * LG::SHELL];
@@ -1406,6 +1327,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_rcheck(GroupArgs<T> A) {
     const int z0 = (tile / (tiles_x * tiles_y)) * LG::TZ;
     constexpr int kShW = LabelGeom<ND>::SHW;
     __syncthreads();  // the previous tile's tables have been read
+    if (i != slot_field) {  // the same for every thread of the block
+      fill_slot_table<ND>(s_slotd, G);
+      slot_field = i;
+    }
     for (int k = threadIdx.x; k < 2 * kShW; k += kThreads) s_shx[k] = F.texit[(size_t)tile * 2 * kShW + k];
     __syncthreads();
     // The tile's exits (the shell cells its lines leave through) listed in
@@ -1434,23 +1359,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_rcheck(GroupArgs<T> A) {
     const uint32_t nxl = s_nxl;
     for (uint32_t j0 = threadIdx.x; j0 < nxl; j0 += 4 * kThreads) {
       int q[4];
-      uint2 p[4];
+      uint32_t lab[4], old[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const uint32_t j = j0 + k * kThreads;
         q[k] = j < nxl ? (int)s_xl[j] : -1;
         const int d = q[k] >= kShW * 32 ? 1 : 0, s = q[k] - d * kShW * 32;
-        int e = q[k] >= 0 ? shell_vertex<ND>(G, s_shell, s, x0, y0, z0) : 0;
-        if (!MSZ_IN(st, e, G.n)) e = 0;
-        p[k] = F.xr[d][e >> 5];
-        p[k].x &= (1u << (e & 31)) - 1u;
-      }
-      uint32_t lab[4], old[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int d = q[k] >= kShW * 32 ? 1 : 0, s = q[k] - d * kShW * 32;
-        const uint32_t rk = p[k].y + (uint32_t)__popc(p[k].x);
-        lab[k] = (q[k] >= 0 && MSZ_IN(st, rk, st->nexit[d])) ? F.lc[d][rk] & ~kRes : 0u;
+        uint32_t sl = q[k] >= 0 ? (uint32_t)tile * (uint32_t)LG::NFACE + (uint32_t)s_slotd[s] : 0u;
+        if (!MSZ_IN(st, sl, F.nface)) sl = 0;
+        lab[k] = q[k] >= 0 ? F.lw[d][sl] & ~kRes : 0u;
         old[k] = (q[k] >= 0 && job) ? F.tsnap[((size_t)tile * 2 + d) * LG::SHELL + s] : 0u;
       }
 #pragma unroll
@@ -1471,12 +1388,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_rcheck(GroupArgs<T> A) {
     // it holds no troublemaker and adds nothing to the counts.
     const uint8_t tstate = job ? F.tdirty[tile] : 0;
     const bool examine = __syncthreads_or(relabel) || !job || (tstate & 2) || F.twrong[tile];
-    // algorithmic bytes (kernel timing runs): each exit's (bitmap word,
-    // prefix) pair, table entry and snapshot, and, for an examined tile, each
-    // vertex's terminal word and f's two labels
+    // algorithmic bytes (kernel timing runs): each exit's table entry and
+    // snapshot, and, for an examined tile, each vertex's terminal word and
+    // f's two labels
     if (threadIdx.x == 0)
       log_units(A, st, KID_RCHECK,
-                16ull * nxl + (examine ? 12ull * min(LG::TX, G.nx - x0) * min(LG::TY, G.ny - y0) *
+                8ull * nxl + (examine ? 12ull * min(LG::TX, G.nx - x0) * min(LG::TY, G.ny - y0) *
                                              min(LG::TZ, G.nz - z0)
                                        : 0ull));
     if (!examine) continue;
@@ -1734,7 +1651,7 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
     const uint32_t type = st->T, nc = st->ncase;
     const uint64_t r1 = st->rounds + 1;  // the round's number once applied
     // requests (Eqs. 2-5) for this thread's cases, all from one snapshot of
-    // g: decreases at once; freezes are listed (lc[0], idle in the C-loop)
+    // g: decreases at once; freezes are listed (lw[0], idle in the C-loop)
     // for the warps below, since a freeze marks a whole ring
     int cv[kSmallPer];
 #pragma unroll
@@ -1754,14 +1671,14 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
       } else {
         count_freeze_req(st, (int)type, cause);
         const uint32_t q = atomicAdd(&C[1], 1u);
-        if (MSZ_IN(st, q, F.G.n)) F.lc[0][q] = (uint32_t)v;
+        if (MSZ_IN(st, q, F.fz_cap)) F.lw[0][q] = (uint32_t)v;
       }
     }
     cluster_barrier();
     if (const uint32_t nfz = C[1]) {
       // a warp per freeze, a lane per vertex of the anchor's closed ring
       for (uint32_t q = gt >> 5; q < nfz; q += kSmallSpan >> 5)
-        freeze_ring_warp<T, ND>(F, (int)F.lc[0][q], (int)(threadIdx.x & 31), ts);
+        freeze_ring_warp<T, ND>(F, (int)F.lw[0][q], (int)(threadIdx.x & 31), ts);
       cluster_barrier();
     }
     const uint32_t nt = C[0];

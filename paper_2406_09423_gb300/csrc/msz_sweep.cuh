@@ -17,8 +17,9 @@
 // NaN, which max/min ignore; an empty set gives NaN, which the negated
 // comparisons treat as "no neighbour".
 //
-// Data movement: a block owns an x-y tile and marches along z (3D; rows
-// along y in 2D). Each plane of the tile plus a one-vertex halo (widened in x
+// Data movement: a block owns an x-y tile (128 x 8 vertices of float32,
+// 64 x 8 of float64; a warp per row, 16 bytes of a row per thread) and
+// marches along z (3D; 128-vertex row segments along y in 2D). Each plane of the tile plus a one-vertex halo (widened in x
 // to a 16-byte multiple) is fetched by TMA (cp.async.bulk.tensor) into a
 // ring of shared-memory stages guarded by full/empty mbarriers; a producer
 // warp issues the copies and the tensor map's out-of-bounds fill supplies
@@ -61,25 +62,27 @@ __device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc0000
 template <>
 __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000ll); }
 
-// Tile geometry. PADX keeps the TMA box start and width 16-byte aligned.
-// 3D: a block of 256 threads covers 32 x 16 vertices of a plane, two rows per
-// thread (rows 2w, 2w+1 for warp w). 2D: 128 threads cover 128 vertices of a
-// row, one per thread.
+// Tile geometry. PADX keeps the TMA box start and width 16-byte aligned. In
+// 3D a thread owns VX vertices consecutive in x (16 bytes of g: one vector
+// load per staged row), a warp one row of a TX x TY tile; in 2D a thread owns
+// one vertex and 128 threads cover 128 vertices of a row.
 template <class T, int ND>
 struct SweepGeom {
   static constexpr int PADX = 16 / (int)sizeof(T);
-  static constexpr int TX = (ND == 3) ? 32 : 128;
-  static constexpr int RPT = (ND == 3) ? 2 : 1;   // rows per thread
-  static constexpr int TY = (ND == 3) ? 16 : 1;
-  static constexpr int NT = (ND == 3) ? 256 : 128;  // consumer threads
-  static constexpr int NTP = NT + 32;               // + one producer warp (TMA path)
+  static constexpr int VX = (ND == 3) ? 16 / (int)sizeof(T) : 1;  // vertices per thread
+  static constexpr int TX = (ND == 3) ? 32 * VX : 128;
+  static constexpr int TPR = TX / VX;  // threads per tile row
+  static constexpr int TY = (ND == 3) ? 8 : 1;
+  static constexpr int NT = TPR * TY;  // consumer threads (256 in 3D, 128 in 2D)
+  static constexpr int NTP = NT + 32;  // + one producer warp (TMA path)
   static constexpr int BX = TX + 2 * PADX;
   static constexpr int BY = (ND == 3) ? TY + 2 : 1;
   static constexpr int STAGE_ELEMS = BX * BY;
   static constexpr int G_BYTES = ((STAGE_ELEMS * (int)sizeof(T) + 127) / 128) * 128;
   static constexpr int D_BYTES = ((TX * TY + 127) / 128) * 128;  // f's direction bytes of the tile plane
   static constexpr int STAGE_BYTES = G_BYTES + D_BYTES;
-  static constexpr int STAGES = (ND == 3) ? 8 : 4;
+  static constexpr int STAGES = 4;
+  static_assert(VX * (int)sizeof(T) == 16 || VX == 1, "one 16-byte row load per thread");
 };
 
 struct SweepTiling {
@@ -167,68 +170,60 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// Per-plane quantities of one thread's vertices (RPT rows): the centre value
-// and the extrema of the two "L" corners (see the header comment).
-template <class T, int RPT>
-struct PlaneVals {
-  T a0[RPT];                 // g at (x, y)
-  T lurM[RPT], lurm[RPT];    // max / min of LUR
-  T lllM[RPT], lllm[RPT];    // max / min of LLL
+// The values a thread needs from one staged row: its VX vertices and one
+// more on either side (columns c - 1 .. c + VX of the stage row r).
+template <class T, int VX>
+__device__ __forceinline__ void load_row(const T* row, T (&a)[VX + 2]) {
+  if constexpr (VX == 1) {
+    a[0] = row[-1];
+    a[1] = row[0];
+    a[2] = row[1];
+  } else {
+    static_assert(VX * sizeof(T) == 16, "16-byte row segment");
+    const uint4 v = *reinterpret_cast<const uint4*>(row);  // 16-byte aligned: the stage column is
+    const T* m = reinterpret_cast<const T*>(&v);             // PADX + VX * lane
+    a[0] = row[-1];
+#pragma unroll
+    for (int k = 0; k < VX; ++k) a[k + 1] = m[k];
+    a[VX + 1] = row[VX];
+  }
+}
+
+// Per-plane quantities of a thread's VX vertices: the centre value and the
+// max / min of the two "L" corners (see the header comment).
+template <class T, int VX>
+struct Partials {
+  T a0[VX];
+  T uM[VX], um[VX];  // LUR max / min
+  T lM[VX], lm[VX];  // LLL max / min
 };
 
-// Reads the thread's neighbourhood from a staged plane. 3D: rows y-1 .. y+RPT
-// (stage rows RPT*w .. RPT*w+RPT+1) at columns x-1, x, x+1 for the RPT
-// vertices of rows y = RPT*w .. RPT*w+RPT-1 (tile-local).
+// Partials of plane P from the stage: in 3D rows y-1, y, y+1 of the
+// thread's row w (stage rows w .. w + 2) at its columns; in 2D the row.
 template <class T, int ND>
-__device__ __forceinline__ PlaneVals<T, SweepGeom<T, ND>::RPT> plane_vals(const T* s, int tx, int w) {
+__device__ __forceinline__ void plane_partials(const T* stage, int col, int w,
+                                               Partials<T, SweepGeom<T, ND>::VX>& P) {
   using SG = SweepGeom<T, ND>;
-  PlaneVals<T, SG::RPT> P;
-  const int c = tx + SG::PADX;
+  constexpr int VX = SG::VX;
   if constexpr (ND == 3) {
-    constexpr int R = SG::RPT;
-    const T* r0 = s + (R * w) * SG::BX + c;  // row y-1
-    T a[R + 2][3];
+    T a[3][VX + 2];
 #pragma unroll
-    for (int r = 0; r < R + 2; ++r) {
-      a[r][0] = r0[r * SG::BX - 1];
-      a[r][1] = r0[r * SG::BX];
-      a[r][2] = r0[r * SG::BX + 1];
-    }
+    for (int r = 0; r < 3; ++r) load_row<T, VX>(stage + (w + r) * SG::BX + col, a[r]);
 #pragma unroll
-    for (int k = 0; k < R; ++k) {  // vertex row = r k+1
-      P.a0[k] = a[k + 1][1];
-      P.lurM[k] = vmax3(a[k + 1][2], a[k + 2][1], a[k + 2][2]);
-      P.lurm[k] = vmin3(a[k + 1][2], a[k + 2][1], a[k + 2][2]);
-      P.lllM[k] = vmax3(a[k + 1][0], a[k][0], a[k][1]);
-      P.lllm[k] = vmin3(a[k + 1][0], a[k][0], a[k][1]);
+    for (int k = 0; k < VX; ++k) {  // vertex column k + 1 of row 1
+      P.a0[k] = a[1][k + 1];
+      P.uM[k] = vmax3(a[1][k + 2], a[2][k + 1], a[2][k + 2]);
+      P.um[k] = vmin3(a[1][k + 2], a[2][k + 1], a[2][k + 2]);
+      P.lM[k] = vmax3(a[1][k], a[0][k + 1], a[0][k]);
+      P.lm[k] = vmin3(a[1][k], a[0][k + 1], a[0][k]);
     }
   } else {
-    const T* m0 = s + c;
-    P.a0[0] = m0[0];
-    P.lurM[0] = P.lurm[0] = m0[1];
-    P.lllM[0] = P.lllm[0] = m0[-1];
+    T a[3];
+    load_row<T, 1>(stage + col, a);
+    P.a0[0] = a[1];
+    P.uM[0] = P.um[0] = a[2];
+    P.lM[0] = P.lm[0] = a[0];
   }
-  return P;
-}
-
-// Extremum flags of the thread's vertices of plane A (B next, C previous),
-// packed two bits per vertex: bit 4k maximum, bit 4k+2 minimum... see
-// kBitMax / kBitMin.
-template <class T, int RPT>
-__device__ __forceinline__ bool is_max_at(const PlaneVals<T, RPT>& C, const PlaneVals<T, RPT>& A,
-                                          const PlaneVals<T, RPT>& B, int k) {
-  const T maxU = vmax3(A.lurM[k], B.a0[k], B.lurM[k]);
-  const T maxL = vmax3(A.lllM[k], C.a0[k], C.lllM[k]);
-  const T g = A.a0[k];
-  return !(maxU >= g) && !(maxL > g);
-}
-template <class T, int RPT>
-__device__ __forceinline__ bool is_min_at(const PlaneVals<T, RPT>& C, const PlaneVals<T, RPT>& A,
-                                          const PlaneVals<T, RPT>& B, int k) {
-  const T minU = vmin3(A.lurm[k], B.a0[k], B.lurm[k]);
-  const T minL = vmin3(A.lllm[k], C.a0[k], C.lllm[k]);
-  const T g = A.a0[k];
-  return !(minU < g) && !(minL <= g);
 }
 
 }  // namespace msz

@@ -23,7 +23,7 @@ MSZ_OPT_TEST_STALL = 4
 # msz_result.kernel_ms: classification (full sweep + incremental), labels
 # (tile terminals + exit jumping), R-loop check, requests + apply
 KERNEL_KINDS = ("classify", "labels", "rcheck", "mark_apply")
-MSZ_NUM_KERNELS = 12
+MSZ_NUM_KERNELS = 9
 STATUS = {
     0: "MSZ_OK", -1: "MSZ_ERR_ARG", -2: "MSZ_ERR_DTYPE", -3: "MSZ_ERR_NONFINITE",
     -4: "MSZ_ERR_BOUND", -5: "MSZ_ERR_OOM", -6: "MSZ_ERR_NOCONVERGE", -7: "MSZ_ERR_TIMEOUT",

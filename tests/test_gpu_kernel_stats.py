@@ -36,8 +36,8 @@ def test_kernel_stats_consistent(shape):
     assert a.counts == b.counts
     assert torch.equal(a.edit_idx, b.edit_idx)
     st = {s["name"]: s for s in timed.kernel_stats()}
-    assert list(st) == ["k_csweep", "k_gather", "k_mark", "k_label_tile", "k_ecount", "k_escan", "k_efill",
-                        "k_jump", "k_rcheck", "k_apply", "k_reclass", "k_csmall"]
+    assert list(st) == ["k_csweep", "k_gather", "k_mark", "k_label_tile", "k_jump", "k_rcheck", "k_apply",
+                        "k_reclass", "k_csmall"]
     steps = st["k_csweep"]["launches"]
     assert steps > 0
     per_step = {"k_jump": 2, "k_gather": 2, "k_mark": 2, "k_apply": 2, "k_reclass": 2, "k_label_tile": 2}
@@ -60,15 +60,12 @@ def test_kernel_stats_consistent(shape):
     assert st["k_reclass"]["work_launches"] + small == rounds + c["r_rounds"]
     # f's labels once (k_rcheck resolves them in place), then g's at every evaluation
     evals = c["label_evals"] + 1
-    for name in ("k_label_tile", "k_ecount", "k_escan", "k_efill", "k_rcheck"):
+    for name in ("k_label_tile", "k_rcheck"):
         assert st[name]["work_launches"] == evals, name
     # the R-check counts algorithmic bytes: every vertex is examined by f's
-    # resolution and by g's first evaluation (12 bytes each), exits cost 16
+    # resolution and by g's first evaluation (12 bytes each), exits cost 8
     assert 24 * n <= st["k_rcheck"]["units"] <= evals * (12 * n + 32 * n)
-    assert st["k_ecount"]["units"] == ((n + 31) // 32) * evals
-    assert st["k_escan"]["units"] == evals
     assert 0 < st["k_label_tile"]["units"] <= n * evals
-    assert st["k_efill"]["units"] > 0
     assert st["k_jump"]["work_launches"] >= evals
     # classification sweeps: one full, one incremental per apply
     assert c["sweeps"] == 1 + rounds + c["r_rounds"]
