@@ -366,8 +366,9 @@ __global__ void __launch_bounds__(kThreads) k_init(GroupArgs<T> A) {
 // active tiles through a ring of TMA stages (full/empty mbarriers, bounded
 // waits); otherwise the consumers fill one stage with plain loads. A thread
 // owns VX vertices of one row (16 bytes of g: one vector load per staged
-// row) and carries the previous plane's partial extrema from plane to plane,
-// so each plane is read from shared memory once.
+// row) and carries from plane to plane what the next plane needs (centre
+// values, LLL extrema) and the extremum tests already decided, so each
+// plane is read from shared memory once.
 // ---------------------------------------------------------------------------
 template <class T, int ND, bool kTMA>
 __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND>::NT)
@@ -480,7 +481,7 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
       const Geom G = F.G;
       const int chunk = t.ppt - 2;
       const int axis_n = (ND == 3) ? G.nz : G.ny;
-      const int x = t.x0 + tx;                     // the thread's first vertex
+      const int x = t.x0 + tx;  // the thread's first vertex
       const int y = (ND == 3) ? t.y0 + w : 0;
       uint32_t vmask = 0;  // bits 8k, 8k + 4: vertex k is inside the grid in x and y
 #pragma unroll
@@ -491,96 +492,117 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
       const int wx0 = t.x0 + ((tid % SG::TPR) & ~31) * VX;
       const int wx1 = min(G.nx, wx0 + 32 * VX) - 1;
       uint32_t cnt[4] = {0, 0, 0, 0};
-      PV prev;                               // the previous plane's partials
-      T prevLM[VX], prevLm[VX];              // max / min over L*(v) of the previous plane
-      uint32_t prev_fd = 0;
+      // What a plane carries to the next (two register sets that alternate,
+      // no copies): its centre values and LLL extrema (for the next plane's
+      // L*(v)), and per vertex k the part of its extremum tests already
+      // decided at bits 8k (maximum) and 8k + 4 (minimum): every L*(v)
+      // neighbour and its own LUR corner compared with g. The tests against
+      // the next plane's centre and LUR corner complete them. A comparison
+      // with a max / min of several values is the conjunction of the
+      // comparisons with each (NaN halo values compare false and are never
+      // the max or min of a set with a number).
+      struct PlaneState {
+        T a0[VX], lM[VX], lm[VX];
+        uint32_t pre;  // decided tests
+        uint32_t fd;   // f's direction bytes of the thread's vertices
+      };
+      PlaneState S[2];
 #pragma unroll
-      for (int k = 0; k < VX; ++k) prevLM[k] = prevLm[k] = qnan<T>();
-      for (int p = 0; p < t.ppt; ++p, ++q) {
-        const int pcoord = t.c0 - 1 + p;  // plane coordinate (z in 3D, y in 2D)
-        unsigned char* sp = smem + (kTMA ? (q & SM1) * SG::STAGE_BYTES : 0);
-        const T* stage = reinterpret_cast<const T*>(sp);
-        PV cur;
-        uint32_t fd = 0;
-        if (kTMA) {
-          // lane 0 waits for the stage; the warp follows its decision
-          bool got = true;
-          if (lane == 0) got = mbar_wait_or_abort(&full[q & SM1], (uint32_t)((q / SG::STAGES) & 1), &s_abort);
-          got = __shfl_sync(kFull, got, 0);
-          if (!got) {
-            if (lane == 0) atomicExch(&s_abort, 1);
-            ok = false;
-            break;
-          }
-          plane_partials<T, ND>(stage, SG::PADX + tx, w, cur);
-          const unsigned char* dp = sp + SG::G_BYTES + w * SG::TX + tx;
-          if constexpr (VX == 4) fd = *reinterpret_cast<const uint32_t*>(dp);
-          else if constexpr (VX == 2) fd = *reinterpret_cast<const uint16_t*>(dp);
-          else fd = *dp;
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&empty[q & SM1]);
-        } else {
-          __syncthreads();
-          T* wst = reinterpret_cast<T*>(sp);
-          for (int k = tid; k < SG::STAGE_ELEMS; k += SG::NT) {
-            const int col = k % SG::BX, row = k / SG::BX;
-            const int gx = t.x0 - SG::PADX + col;
-            const int gy = (ND == 3) ? t.y0 - 1 + row : pcoord;
-            const int gz = (ND == 3) ? pcoord : 0;
-            const bool in = gx >= 0 && gx < G.nx && gy >= 0 && gy < G.ny && gz >= 0 && gz < G.nz;
-            wst[k] = in ? F.g[gx + G.nx * (gy + G.ny * gz)] : qnan<T>();
-          }
-          __syncthreads();
-          plane_partials<T, ND>(stage, SG::PADX + tx, w, cur);
-          const int vy = (ND == 3) ? y : pcoord, vz = (ND == 3) ? pcoord : 0;
+      for (int h = 0; h < 2; ++h) S[h].pre = S[h].fd = 0;
+      for (int p0 = 0; p0 < t.ppt && ok; p0 += 2) {
 #pragma unroll
-          for (int k = 0; k < VX; ++k)
-            if (x + k < G.nx && vy >= 0 && vy < G.ny && vz >= 0 && vz < G.nz)
-              fd |= (uint32_t)F.fdir[(x + k) + G.nx * (vy + G.ny * vz)] << (8 * k);
-        }
-        if (p >= 1) {
-          if (p >= 2) {
-            // Plane p - 1 (A; this plane B, the one before C): g's extremum
-            // flags and f's, at bits 8k (max) and 8k + 4 (min) for vertex k;
-            // a vertex is a case when they differ.
+        for (int h = 0; h < 2; ++h) {
+          const int p = p0 + h;
+          if (p >= t.ppt || !ok) continue;
+          PlaneState& cur = S[h];
+          const PlaneState& prv = S[h ^ 1];
+          const int pcoord = t.c0 - 1 + p;  // plane coordinate (z in 3D, y in 2D)
+          unsigned char* sp = smem + (kTMA ? (q & SM1) * SG::STAGE_BYTES : 0);
+          const T* stage = reinterpret_cast<const T*>(sp);
+          PV n;  // the plane's partials
+          uint32_t fd = 0;
+          if (kTMA) {
+            // every lane waits for the stage (one decision for the warp)
+            const bool got =
+                __all_sync(kFull, mbar_wait_or_abort(&full[q & SM1], (uint32_t)((q / SG::STAGES) & 1), &s_abort));
+            if (!got) {
+              if (lane == 0) atomicExch(&s_abort, 1);
+              ok = false;
+              continue;
+            }
+            plane_partials<T, ND>(stage, SG::PADX + tx, w, n);
+            const unsigned char* dp = sp + SG::G_BYTES + w * SG::TX + tx;
+            if constexpr (VX == 4) fd = *reinterpret_cast<const uint32_t*>(dp);
+            else if constexpr (VX == 2) fd = *reinterpret_cast<const uint16_t*>(dp);
+            else fd = *dp;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[q & SM1]);
+          } else {
+            __syncthreads();
+            T* wst = reinterpret_cast<T*>(sp);
+            for (int k = tid; k < SG::STAGE_ELEMS; k += SG::NT) {
+              const int col = k % SG::BX, row = k / SG::BX;
+              const int gx = t.x0 - SG::PADX + col;
+              const int gy = (ND == 3) ? t.y0 - 1 + row : pcoord;
+              const int gz = (ND == 3) ? pcoord : 0;
+              const bool in = gx >= 0 && gx < G.nx && gy >= 0 && gy < G.ny && gz >= 0 && gz < G.nz;
+              wst[k] = in ? F.g[gx + G.nx * (gy + G.ny * gz)] : qnan<T>();
+            }
+            __syncthreads();
+            plane_partials<T, ND>(stage, SG::PADX + tx, w, n);
+            const int vy = (ND == 3) ? y : pcoord, vz = (ND == 3) ? pcoord : 0;
+#pragma unroll
+            for (int k = 0; k < VX; ++k)
+              if (x + k < G.nx && vy >= 0 && vy < G.ny && vz >= 0 && vz < G.nz)
+                fd |= (uint32_t)F.fdir[(x + k) + G.nx * (vy + G.ny * vz)] << (8 * k);
+          }
+          ++q;
+          if (p >= 2 && p - 2 < chunk) {
+            // The previous plane's extremum flags (g's, completed with this
+            // plane's centre and LUR corner; f's from its direction bytes)
+            // at bits 8k (max) and 8k + 4 (min) of vertex k, and the false
+            // types from their differences, word-parallel.
             uint32_t gb = 0;
 #pragma unroll
             for (int k = 0; k < VX; ++k) {
-              const T g = prev.a0[k];
-              const T maxU = vmax3(prev.uM[k], cur.a0[k], cur.uM[k]);
-              const T minU = vmin3(prev.um[k], cur.a0[k], cur.um[k]);
-              const bool gmax = !(maxU >= g) && !(prevLM[k] > g);
-              const bool gmin = !(minU < g) && !(prevLm[k] <= g);
-              gb |= ((uint32_t)gmax << (8 * k)) | ((uint32_t)gmin << (8 * k + 4));
+              const T g = prv.a0[k];
+              gb |= ((uint32_t)!(vmax(n.a0[k], n.uM[k]) >= g) << (8 * k)) |
+                    ((uint32_t)!(vmin(n.a0[k], n.um[k]) < g) << (8 * k + 4));
             }
-            const uint32_t fa = prev_fd;
+            gb &= prv.pre;
+            const uint32_t fa = prv.fd;
             const uint32_t fb = fa & (fa >> 1) & (fa >> 2) & (fa >> 3) & 0x11111111u;  // nibble == 15
-            uint32_t diff = (gb ^ fb) & vmask;
-            if (!(p - 2 < chunk && pcoord - 1 < axis_n)) diff = 0;
-            if (__any_sync(kFull, diff != 0)) {
-              // false types of the thread's vertices: bit 0 FPmax, 1 FPmin,
-              // 2 FNmax, 3 FNmin (byte k for vertex k); type counts packed
-              // one per byte for a single warp reduction
+            const uint32_t valid = (pcoord - 1 < axis_n) ? vmask : 0u;
+            const uint32_t Pm = gb & ~fb & valid;  // g's extremum, not f's: FPmax (bit 8k), FPmin (8k + 4)
+            const uint32_t Nm = fb & ~gb & valid;  // f's extremum, not g's: FNmax, FNmin
+            if (__any_sync(kFull, (Pm | Nm) != 0u)) {
+              // byte k: the type bits of vertex k (FPmax, FPmin, FNmax, FNmin)
+              const uint32_t codes = (Pm & 0x01010101u) | ((Pm >> 3) & 0x02020202u) |
+                                     ((Nm << 2) & 0x04040404u) | ((Nm >> 1) & 0x08080808u);
+              // the thread's count of each type, one per byte, for one warp reduction
+              const uint32_t packed =
+                  (uint32_t)__popc(Pm & 0x01010101u) | ((uint32_t)__popc(Pm & 0x10101010u) << 8) |
+                  ((uint32_t)__popc(Nm & 0x01010101u) << 16) | ((uint32_t)__popc(Nm & 0x10101010u) << 24);
               const int z = (ND == 3) ? pcoord - 1 : 0;
               const int yy = (ND == 3) ? y : pcoord - 1;
               const int v0 = x + G.nx * (yy + G.ny * z);
-              uint32_t codes = 0, packed = 0;
+              // class bits of the false vertices (cls starts zeroed and each
+              // vertex has one owner): one store of the thread's bytes where
+              // the row pitch keeps it aligned
+              if (codes) {
+                if constexpr (kTMA && VX == 4) {
+                  *reinterpret_cast<uint32_t*>(F.cls + v0) = codes;
+                } else if constexpr (kTMA && VX == 2) {
+                  *reinterpret_cast<uint16_t*>(F.cls + v0) = (uint16_t)codes;
+                } else {
 #pragma unroll
-              for (int k = 0; k < VX; ++k) {
-                const uint32_t gk = gb >> (8 * k), fk = fb >> (8 * k);
-                uint32_t bits = 0;
-                if ((diff >> (8 * k)) & 0x11u) {
-                  const uint32_t gmx = gk & 1u, gmn = (gk >> 4) & 1u, fmx = fk & 1u, fmn = (fk >> 4) & 1u;
-                  bits = (gmx & ~fmx) | ((gmn & ~fmn) << 1) | ((fmx & ~gmx) << 2) | ((fmn & ~gmn) << 3);
+                  for (int k = 0; k < VX; ++k)
+                    if ((codes >> (8 * k)) & 15u) F.cls[v0 + k] = (uint8_t)((codes >> (8 * k)) & 15u);
                 }
-                codes |= bits << (8 * k);
-                packed += (bits & 1u) | ((bits & 2u) << 7) | ((bits & 4u) << 14) | ((bits & 8u) << 21);
-                // class bits of the false vertices (cls starts zeroed)
-                if (bits) F.cls[v0 + k] = (uint8_t)bits;
               }
               const uint32_t tot = __reduce_add_sync(kFull, packed);
-              // per-tile type counts: one atomic per type when the warp's
-              // row segment lies in one count tile, else one per vertex
+              // per-tile type counts: one atomic per type when the warp's row
+              // segment lies in one count tile, else one per vertex
               const int wv0 = wx0 + G.nx * (yy + G.ny * z), wv1 = wx1 + G.nx * (yy + G.ny * z);
               const int ct = wv0 / kEmitTile;
               if (ct == wv1 / kEmitTile) {
@@ -606,18 +628,26 @@ __global__ void __launch_bounds__(kTMA ? SweepGeom<T, ND>::NTP : SweepGeom<T, ND
               }
             }
           }
-          // L*(v) extrema of this plane (its LLL corner, the previous plane's
-          // centre and LLL corner)
+          // This plane's decided tests: its own LUR corner, and L*(v) (its
+          // LLL corner, the previous plane's centre and LLL corner).
+          uint32_t pre = 0;
 #pragma unroll
           for (int k = 0; k < VX; ++k) {
-            const T LM = vmax3(cur.lM[k], prev.a0[k], prev.lM[k]);
-            const T Lm = vmin3(cur.lm[k], prev.a0[k], prev.lm[k]);
-            prevLM[k] = LM;
-            prevLm[k] = Lm;
+            const T g = n.a0[k];
+            const T LM = vmax3(n.lM[k], prv.a0[k], prv.lM[k]);
+            const T Lm = vmin3(n.lm[k], prv.a0[k], prv.lm[k]);
+            pre |= ((uint32_t)(!(n.uM[k] >= g) && !(LM > g)) << (8 * k)) |
+                   ((uint32_t)(!(n.um[k] < g) && !(Lm <= g)) << (8 * k + 4));
           }
+          cur.pre = pre;
+#pragma unroll
+          for (int k = 0; k < VX; ++k) {
+            cur.a0[k] = n.a0[k];
+            cur.lM[k] = n.lM[k];
+            cur.lm[k] = n.lm[k];
+          }
+          cur.fd = fd;
         }
-        prev = cur;
-        prev_fd = fd;
       }
       if (!ok) break;
       // Tile done by this warp: flush its counts; the last consumer warp to
@@ -1204,10 +1234,15 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
     const bool first = st->jump_rounds == 0;
     uint32_t acc = 0;
     constexpr int kJB = 4;  // entries per thread and iteration, their walks advanced together
-    const uint32_t ne = F.nface, chunk = (ne + (uint32_t)U - 1u) / (uint32_t)U;
-    const uint32_t r0 = min(ne, chunk * (uint32_t)u), re = min(ne, r0 + chunk);  // this unit's share
+    // The unit's share of both directions' slots taken as one range (all of
+    // direction 0 before direction 1), so that the units in flight at a time
+    // work mostly on one direction's tables.
+    const uint32_t ne = F.nface, chunk = (2u * ne + (uint32_t)U - 1u) / (uint32_t)U;
+    const uint32_t c0 = min(2u * ne, chunk * (uint32_t)u), c1 = min(2u * ne, c0 + chunk);
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
+      const uint32_t lo = max(c0, (uint32_t)d * ne), hi = min(c1, (uint32_t)(d + 1) * ne);
+      const uint32_t r0 = lo - (uint32_t)d * ne, re = (hi > lo) ? hi - (uint32_t)d * ne : r0;
       const uint32_t* lf = F.lf[d];
       uint32_t* lw = F.lw[d];
       const uint8_t* xm = F.xm[d];
