@@ -126,7 +126,24 @@ HBM_BOUND = ("k_csweep", "k_jump", "k_rcheck")
 # dram__bytes_write.sum of the launch / its units), scaled to the bench's
 # launches by their units. Only kernels unchanged since their capture are
 # listed.
-PROFILED_TRAFFIC = {}
+PROFILED_TRAFFIC = {
+    # 320^3, xi = 1e-3 x range: the fix's dense sweep (167.61 MB read + 5.24 MB
+    # written over 32,768,000 vertices); traffic grows with the vertices swept
+    "k_csweep": (167.61e6 + 5.24e6) / 32768000,
+    # 320^3, a pass over g with every tile recomputed (45.76 MB read + 179.30 MB
+    # written over 32,768,000 vertices); traffic grows with the vertices of the
+    # tiles recomputed (f's pass, one per fix, also reads f and g)
+    "k_label_tile": (45.76e6 + 179.30e6) / 32768000,
+}
+
+# What bounds each kernel, from the ncu captures of the same build on the
+# 320^3 field (the roofline objects carry it beside their HBM fraction).
+LIMITERS = {
+    "k_label_tile": "instruction issue: 73 % issue active, ALU pipe 63 % (pointer doubling in shared memory)",
+    "k_csweep": "ALU pipe: 76.5 % active (three-input max/min and the extremum comparisons)",
+    "k_rcheck": "latency of the exit-table lookups and the tile barriers (long-scoreboard stalls)",
+    "k_jump": "latency of the dependent table loads (long-scoreboard stalls 10-13 per instruction)",
+}
 
 
 def kernel_bytes(name, st, n, es):
@@ -649,13 +666,14 @@ def main():
         traffic = per_unit * row["units"] / row["work_launches"] if per_unit else None
         return {"bound": "hbm", "achieved": row["achieved_gbs"], "peak": peak_gbs, "unit": "GB/s",
                 "frac": row["frac"], "traffic": traffic, "kernel": row["name"], "note": note,
+                "limiter": LIMITERS.get(row["name"]),
                 "avg_launch_ms": avg_ms, "bytes_per_launch": row["algorithmic_bytes"] / row["work_launches"],
                 "work_launches": row["work_launches"], "peak_source": peak_src,
                 "share_of_kernel_time": row["ms"] / total_kms}
 
     # the roofline object is the kernel with the most working time; the
     # HBM-streaming kernel with the most working time is reported beside it
-    roofline = roofline_stream = None
+    roofline = roofline_stream = roofline_stencil = None
     with_bytes = [k for k in kernels if "achieved_gbs" in k]
     if with_bytes:
         top = max(with_bytes, key=lambda k: k["work_ms"])
@@ -664,6 +682,9 @@ def main():
         if hbm_rows:
             hs = max(hbm_rows, key=lambda k: k["work_ms"])
             roofline_stream = roof(hs, "the HBM-streaming kernel with the most working time")
+        sweep = [k for k in with_bytes if k["name"] == "k_csweep"]
+        if sweep:
+            roofline_stencil = roof(sweep[0], "the dense stencil sweep (one per fix)")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -736,7 +757,7 @@ def main():
                        "form": "plain (one field per msz_fix)", "parallelism": f"replicas x{world}",
                        "l2": "inputs 2 x 537 MB > 129 MB L2, no flush"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-            "roofline_stream": roofline_stream,
+            "roofline_stream": roofline_stream, "roofline_stencil": roofline_stencil,
             "cpu_baseline": cpu,
             "latency_ms": {"p50": p50, "p99": p99}, "per_xi": per_xi,
             "step_mvps": {"min": step_rates[0], "max": step_rates[-1]},
