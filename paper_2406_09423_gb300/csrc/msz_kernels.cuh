@@ -1039,7 +1039,19 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
     // g's terminals only change in tiles whose tile or halo was edited
     const bool redo = !job || (F.tdirty[tile] & 1);
     __syncthreads();  // the block's previous tile is done with the shared arrays
-    if (!redo) continue;
+    if (!redo) {
+      // A tile that keeps its terminals keeps its first-level exit-table
+      // entries; the working table restarts from them (16-byte copies: a
+      // tile's block of slots is a multiple of 16 bytes).
+      constexpr int kQ = LG::NFACE / 4;
+      static_assert(LG::NFACE % 4 == 0, "whole 16-byte groups per tile");
+      for (int k = threadIdx.x; k < 2 * kQ; k += kThreads) {
+        const int d = k / kQ, q = k - d * kQ;
+        reinterpret_cast<uint4*>(F.lw[d] + (size_t)tile * LG::NFACE)[q] =
+            reinterpret_cast<const uint4*>(F.lf[d] + (size_t)tile * LG::NFACE)[q];
+      }
+      continue;
+    }
     if (fi != slot_field) {  // the same for every thread of the block
       fill_slot_table<ND>(s_slotd, G);
       slot_field = fi;
@@ -1161,8 +1173,10 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
 #pragma unroll
       for (int d = 0; d < 2; ++d) {
         const uint32_t t = d ? (p >> 16) : (p & 0xffffu);
-        F.lf[d][tbase + f] = (t & kTermExtr) ? ((uint32_t)extremum_vertex<ND>(G, t, x0, y0, z0) | kRes)
-                                             : exit_of(t & kTermIdx);
+        const uint32_t e = (t & kTermExtr) ? ((uint32_t)extremum_vertex<ND>(G, t, x0, y0, z0) | kRes)
+                                           : exit_of(t & kTermIdx);
+        F.lf[d][tbase + f] = e;
+        F.lw[d][tbase + f] = e;  // the working table starts from the first level
       }
     }
     // Exit marks (the entries the jumping resolves): the slot of each exit
@@ -1199,12 +1213,10 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
 // xm marks the slots that are exits of some tile's lines; only those are
 // resolved (and looked up).
 //
-// k_jump: label propagation by pointer jumping over the marked slots. The
-// evaluation's first launch starts each marked entry in lw from lf, one step
-// along its line already taken (lw still holds the previous evaluation's
-// entries, so that launch reads lf only). Later launches walk lw: a walk
-// stores each pointer it reaches in its own entry, and all entries walk at
-// once. A value read is the entry of an exit further along the same line, or
+// k_jump: label propagation by pointer jumping over the marked slots of lw,
+// which the label tiles restart from lf at every evaluation (recomputed
+// tiles write both, the others copy theirs). A walk stores each pointer it
+// reaches in its own entry, and all entries walk at once. A value read is the entry of an exit further along the same line, or
 // the line's label, whether it was read before or after its owner advanced
 // it, so every step makes progress and the other entries' stores shorten the
 // walk (each read skips the steps its owner has taken). Loads of lw bypass
@@ -1229,9 +1241,6 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
     const uint64_t u = (uint64_t)(u_ - pre[i]), U = (uint64_t)F.units[K_DENSE];
-    // the evaluation's first launch (the state only changes once every unit
-    // of the launch is done)
-    const bool first = st->jump_rounds == 0;
     uint32_t acc = 0;
     constexpr int kJB = 4;  // entries per thread and iteration, their walks advanced together
     // The unit's share of both directions' slots taken as one range (all of
@@ -1243,7 +1252,6 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
     for (int d = 0; d < 2; ++d) {
       const uint32_t lo = max(c0, (uint32_t)d * ne), hi = min(c1, (uint32_t)(d + 1) * ne);
       const uint32_t r0 = lo - (uint32_t)d * ne, re = (hi > lo) ? hi - (uint32_t)d * ne : r0;
-      const uint32_t* lf = F.lf[d];
       uint32_t* lw = F.lw[d];
       const uint8_t* xm = F.xm[d];
       for (uint32_t rb = r0 + threadIdx.x; rb < re; rb += kJB * kThreads) {
@@ -1256,32 +1264,21 @@ __global__ void __launch_bounds__(kThreads) k_jump(GroupArgs<T> A) {
 #pragma unroll
         for (int k = 0; k < kJB; ++k) {
           const uint32_t r = rb + k * kThreads;
-          x[k] = ((mk >> k) & 1u) ? (first ? __ldg(lf + r) : __ldcg(lw + r)) : kRes;
+          x[k] = ((mk >> k) & 1u) ? __ldcg(lw + r) : kRes;
         }
         acc += (uint32_t)__popc(mk);
-        const int steps = first ? 1 : A.chase;
-        for (int h = 0; h < steps; ++h) {
+        for (int h = 0; h < A.chase; ++h) {
           uint32_t walk = 0;  // bit k: entry k still holds a pointer
 #pragma unroll
           for (int k = 0; k < kJB; ++k) walk |= (x[k] & kRes) ? 0u : (1u << k);
           if (!walk) break;
 #pragma unroll
           for (int k = 0; k < kJB; ++k)
-            if ((walk >> k) & 1u)
-              x[k] = MSZ_IN(st, x[k], ne) ? (first ? __ldg(lf + x[k]) : __ldcg(lw + x[k])) : kRes;
-          acc += (uint32_t)__popc(walk);
-          if (!first) {
-#pragma unroll
-            for (int k = 0; k < kJB; ++k)
-              if ((walk >> k) & 1u) lw[rb + k * kThreads] = x[k];
-            acc += (uint32_t)__popc(walk);
-          }
-        }
-        if (first) {
+            if ((walk >> k) & 1u) x[k] = MSZ_IN(st, x[k], ne) ? __ldcg(lw + x[k]) : kRes;
 #pragma unroll
           for (int k = 0; k < kJB; ++k)
-            if ((mk >> k) & 1u) lw[rb + k * kThreads] = x[k];
-          acc += (uint32_t)__popc(mk);
+            if ((walk >> k) & 1u) lw[rb + k * kThreads] = x[k];
+          acc += 2u * (uint32_t)__popc(walk);
         }
 #pragma unroll
         for (int k = 0; k < kJB; ++k) open[0] += (x[k] & kRes) ? 0u : 1u;
