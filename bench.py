@@ -130,10 +130,9 @@ PROFILED_TRAFFIC = {
     # 320^3, xi = 1e-3 x range: the fix's dense sweep (167.61 MB read + 5.24 MB
     # written over 32,768,000 vertices); traffic grows with the vertices swept
     "k_csweep": (167.61e6 + 5.24e6) / 32768000,
-    # 320^3, a pass over g with every tile recomputed (45.76 MB read + 179.30 MB
-    # written over 32,768,000 vertices); traffic grows with the vertices of the
-    # tiles recomputed (f's pass, one per fix, also reads f and g)
-    "k_label_tile": (45.76e6 + 179.30e6) / 32768000,
+    # 320^3, a pass over g with every tile recomputed: 47.80 MB read + 267.84 MB
+    # written for 336.9 MB of algorithmic bytes (the kernel's units are bytes)
+    "k_label_tile": (47.80e6 + 267.84e6) / (32768000 * 5 + 8000 * 1352 * 16),
 }
 
 # What bounds each kernel, from the ncu captures of the same build on the
@@ -152,11 +151,13 @@ def kernel_bytes(name, st, n, es):
     kernels whose traffic is dominated by scattered L2 accesses:
     k_csweep      the stencil sweep's minimum: g (es) and f's direction byte
                   read, one byte of g's classification written per vertex;
-    k_label_tile  g's direction byte read + the packed tile terminals (4)
-                  written per vertex of the tiles recomputed, and the two
-                  first-level exit-table entries (8) of each of the tile's
-                  1352 face cells (f's evaluation, once per fix, also reads f
-                  and g and writes both direction bytes: not counted);
+    k_label_tile  counted by the kernel (its units are bytes): per vertex of
+                  a recomputed tile, g's direction byte read and the packed
+                  terminal word written (5; f's pass, once per fix: f and g
+                  read, both direction bytes and the terminal written, 14);
+                  per face cell of every tile, its entries in both exit
+                  tables of both directions (16: written by a recomputed
+                  tile, copied by the others);
     k_jump        4 bytes per exit-table access (entry read; gather and write
                   of the entries still holding a pointer);
     k_rcheck      counted by the kernel (its units are bytes): per exit label
@@ -167,7 +168,7 @@ def kernel_bytes(name, st, n, es):
     if name == "k_csweep":
         return u * (es + 2)
     if name == "k_label_tile":
-        return u * 5 + (u * 8 * 1352) // 4096
+        return u
     if name == "k_jump":
         return u * 4
     if name == "k_rcheck":

@@ -156,9 +156,10 @@ int msz_plan_destroy(msz_plan p);
  * launch of a loop step is bracketed by CUDA events; a launch "works" when it
  * completes a stage of the field's state machine (the others find the field
  * in another stage and return at once). units counts the work of the working
- * launches: vertices (k_csweep; k_label_tile: vertices of the tiles
- * recomputed), algorithmic bytes (k_rcheck: 8 per exit label looked up,
- * 12 per vertex of the tiles examined), exit-table
+ * launches: vertices (k_csweep), algorithmic bytes (k_label_tile: per
+ * vertex of a recomputed tile 5 in g's passes, 14 in f's, and 16 per face
+ * cell of every tile for the exit tables' entries; k_rcheck: 8 per exit
+ * label looked up, 12 per vertex of the tiles examined), exit-table
  * accesses (k_jump), cases (k_gather, k_mark),
  * touched vertices (k_apply), ring items (k_reclass), C-loop rounds run
  * whole in one thread-block cluster per field (k_csmall: requests, apply and

@@ -1050,6 +1050,8 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
         reinterpret_cast<uint4*>(F.lw[d] + (size_t)tile * LG::NFACE)[q] =
             reinterpret_cast<const uint4*>(F.lf[d] + (size_t)tile * LG::NFACE)[q];
       }
+      // algorithmic bytes (kernel timing runs): both tables' slots of the tile
+      if (threadIdx.x == 0) log_units(A, st, KID_LABEL, 16ull * LG::NFACE);
       continue;
     }
     if (fi != slot_field) {  // the same for every thread of the block
@@ -1198,9 +1200,14 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
     // recomputed, for the R-check to examine (f's pass leaves every tile
     // dirty for g's first)
     if (job && threadIdx.x == 0) F.tdirty[tile] = 2;
+    // algorithmic bytes (kernel timing runs): per vertex, g's direction byte
+    // read and the terminal word written (f's pass: f and g read, both
+    // direction bytes and the terminal word written); per face cell, its
+    // entries in both tables of both directions
     if (threadIdx.x == 0)
       log_units(A, st, KID_LABEL,
-                (uint64_t)min(LG::TX, G.nx - x0) * min(LG::TY, G.ny - y0) * min(LG::TZ, G.nz - z0));
+                (job ? 5ull : 14ull) * min(LG::TX, G.nx - x0) * min(LG::TY, G.ny - y0) * min(LG::TZ, G.nz - z0) +
+                    16ull * LG::NFACE);
   }
   tl.flush(A, K_LABEL, none, done);
 }

@@ -65,7 +65,15 @@ def test_kernel_stats_consistent(shape):
     # the R-check counts algorithmic bytes: every vertex is examined by f's
     # resolution and by g's first evaluation (12 bytes each), exits cost 8
     assert 24 * n <= st["k_rcheck"]["units"] <= evals * (12 * n + 32 * n)
-    assert 0 < st["k_label_tile"]["units"] <= n * evals
+    # the label tiles count bytes: at most 14 per vertex and 16 per face cell
+    # of every tile, per evaluation (and f's)
+    if len(shape) == 3:
+        tiles = -(-shape[0] // 16) * -(-shape[1] // 16) * -(-shape[2] // 16)
+        faces = 1352
+    else:
+        tiles = -(-shape[0] // 32) * -(-shape[1] // 64)
+        faces = 188
+    assert 5 * n <= st["k_label_tile"]["units"] <= evals * (14 * n + 16 * faces * tiles)
     assert st["k_jump"]["work_launches"] >= evals
     # classification sweeps: one full, one incremental per apply
     assert c["sweeps"] == 1 + rounds + c["r_rounds"]
