@@ -111,7 +111,7 @@ struct Field {
   uint32_t fz_cap;  // entries of lw[0] (at least nface; room for a launch's freezes in k_csmall)
   uint8_t* tdirty;  // per label tile: bit 0 terminals to recompute, bit 1 recomputed and not yet checked
   uint32_t* texit;  // per label tile and direction: bitmap over the shell cells its lines leave through
-  uint32_t* tsnap;  // per label tile, direction and shell cell: the exit's label at the tile's last check
+  uint32_t* tsnap;  // per label tile, in the order of its exit list: each exit's label at the tile's last check
   uint8_t* twrong;  // per label tile: its last check found a wrong label
   uint8_t* cls;     // false-type bits of g per vertex (FPmax, FPmin, FNmax, FNmin), padded to kEmitTile
   uint32_t* cases;  // the round's cases of the current type

@@ -1407,7 +1407,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_rcheck(GroupArgs<T> A) {
         uint32_t sl = q[k] >= 0 ? (uint32_t)tile * (uint32_t)LG::NFACE + (uint32_t)s_slotd[s] : 0u;
         if (!MSZ_IN(st, sl, F.nface)) sl = 0;
         lab[k] = q[k] >= 0 ? F.lw[d][sl] & ~kRes : 0u;
-        old[k] = (q[k] >= 0 && job) ? F.tsnap[((size_t)tile * 2 + d) * LG::SHELL + s] : 0u;
+        // the snapshot is kept in the order of the tile's exit list, which
+        // only changes when the tile is recomputed (and then examined)
+        old[k] = (q[k] >= 0 && job) ? F.tsnap[(size_t)tile * 2 * LG::SHELL + j0 + k * kThreads] : 0u;
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -1415,7 +1417,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_rcheck(GroupArgs<T> A) {
         const int d = q[k] >= kShW * 32 ? 1 : 0, s = q[k] - d * kShW * 32;
         s_lab[d][s] = lab[k];
         if (job && old[k] != lab[k]) {
-          F.tsnap[((size_t)tile * 2 + d) * LG::SHELL + s] = lab[k];
+          F.tsnap[(size_t)tile * 2 * LG::SHELL + j0 + k * kThreads] = lab[k];
           relabel = 1;
         }
       }
