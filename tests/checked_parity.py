@@ -2,8 +2,9 @@
 
 Run as a separate process with MSZ_LIBRARY=checked (tests/test_gpu_checked.py
 does): small and ragged fields, f32 and f64, 2D and 3D, the hand-worked
-golden cases, a batch, the allocation-free entry point and a capped run,
-each compared with the oracle bit for bit. Any bounds check that fires ends
+golden cases, a batch, the allocation-free entry point, a capped run and
+the 3600 x 2400 ocean record at 1e-3 x range, each compared with the oracle
+bit for bit. Any bounds check that fires ends
 a fix with MSZ_ERR_CHECK, so a clean run also shows that no index read from
 device data left its range. Prints "checked parity ok <cases>" and exits 0.
 """
@@ -101,6 +102,36 @@ def main():
     assert r.status == 0 and r.counts.as_dict() == ref.counts
     ne = int(r.n_edits)
     assert np.array_equal(idx[:ne].cpu().numpy(), ref.edit_idx.astype(np.int32))
+    n += 1
+    # a full-size record (rounds of more than 64K cases, the cluster kernel
+    # handing the field back to the grid kernels, long label walks): every
+    # digest and counter of the oracle's record
+    import hashlib
+
+    rec = json.load(open(os.path.join(ROOT, "tests", "golden", "fullsize_ocean_1e-3.json")))
+
+    class OnDevice:
+        def __getattr__(self, name):
+            fn = getattr(synth, name)
+            return lambda *a, **k: fn(*a, device="cuda", **k)
+
+    def digest(a):
+        if hasattr(a, "detach"):
+            a = a.detach().cpu().numpy()
+        return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+    f = eval(rec["generator"], {"__builtins__": {}}, {"synth": OnDevice()}).contiguous()
+    xi = synth.xi_for(f, rec["rel"])
+    fh = synth.quantise_torch(f, xi)
+    assert digest(f) == rec["sha256"]["f"] and digest(fh) == rec["sha256"]["fhat"]
+    p = msz.Plan(tuple(f.shape), f.dtype)
+    r = p.fix(f, fh, xi, check=False)
+    p.close()
+    assert r.status == rec["status"] and r.counts == rec["counts"], (r.status, r.counts)
+    assert digest(r.edit_idx.to(torch.int32).cpu().numpy().astype("<u4")) == rec["sha256"]["edit_idx"]
+    assert digest(r.edit_val) == rec["sha256"]["edit_val"]
+    assert digest(r.label_max.reshape(-1).cpu().numpy().astype("<i4")) == rec["sha256"]["label_max"]
+    assert digest(r.label_min.reshape(-1).cpu().numpy().astype("<i4")) == rec["sha256"]["label_min"]
     n += 1
     print(f"checked parity ok {n}", flush=True)
 
