@@ -49,7 +49,8 @@ typedef enum {
   MSZ_ERR_BOUND = -4,      /* fhat violates |fhat - f| <= xi at some vertex */
   MSZ_ERR_OOM = -5,        /* device or host allocation failed */
   MSZ_ERR_NOCONVERGE = -6, /* round cap reached (msz_options.max_rounds); the result still
-                              holds the edit list of the field after its last round (no labels) */
+                              holds the edit list of the field after its last round; its label
+                              arrays hold f's labels, which g's do not match yet */
   MSZ_ERR_TIMEOUT = -7,    /* a bounded device-side wait gave up */
   MSZ_ERR_CUDA = -8,       /* a CUDA runtime call failed */
   MSZ_ERR_BUSY = -9,       /* server: no free slot / request id unknown or not finished */
@@ -365,11 +366,11 @@ int msz_decode_edits(const void* in_dev, uint64_t in_bytes, const void* fhat_dev
  * Inputs (orig_dev, decomp_dev: N values) and outputs are the caller's
  * device buffers: edit_idx_dev / edit_val_dev hold N entries (worst case),
  * label_max_dev / label_min_dev hold N labels. out->edit_idx etc. point to
- * them (the label buffers also serve as scratch during the call). Every
+ * them (the label buffers hold f's labels during the call). Every
  * other array of the loop lives in one static device array of 64 MiB that
- * each GPU loading the library holds until exit; a field needs about 37
- * bytes per vertex (float32, 3D; 30 in 2D) or 41 (float64, 3D; 34 in 2D) of
- * it, so up to about 1.79 M (float32) / 1.62 M (float64) vertices in 3D.
+ * each GPU loading the library holds until exit; a field needs about 33
+ * bytes per vertex (float32, 3D; 26 in 2D) or 37 (float64, 3D; 30 in 2D) of
+ * it, so up to about 2.0 M (float32) / 1.79 M (float64) vertices in 3D.
  * Larger fields are rejected with MSZ_ERR_TOO_LARGE before any work. The
  * first call on a device (and the first after the device's context was
  * reset) looks up the array's device address (cudaGetSymbolAddress) with

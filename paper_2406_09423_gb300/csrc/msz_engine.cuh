@@ -96,12 +96,11 @@ struct Field {
   uint8_t* fdir;
   uint8_t* gdir;
   uint8_t* flags;
-  int32_t* Mf;    // f's labels once f's evaluation is done
-  int32_t* mf;
-  int32_t* Pup;   // outputs: max / min labels once the field has converged
+  int32_t* Mf;    // f's labels once f's evaluation is done: the output arrays Pup / Pdn,
+  int32_t* mf;    // which hold the final labels once the field has converged (g's equal f's)
+  int32_t* Pup;   // outputs: max / min labels
   int32_t* Pdn;
-  uint32_t* term; // tile terminals (kTermFlag form) of the current evaluation; Pup's memory
-                  // (the outputs are written only at emission)
+  uint32_t* term; // tile terminals (kTermFlag form) of the current evaluation
   // per direction (0: ascending lines / max labels, 1: descending / min)
   // exit tables, one slot per face cell of every label tile (exit_slot)
   uint32_t* lf[2];  // first-level entries: a label (kRes) or the slot of the next exit on the line

@@ -133,8 +133,7 @@ struct FieldBufs {
   uint8_t* fdir = nullptr;
   uint8_t* gdir = nullptr;
   uint8_t* flags = nullptr;
-  int32_t* Mf = nullptr;
-  int32_t* mf = nullptr;
+  uint32_t* term = nullptr;
   int32_t* Pup = nullptr;
   int32_t* Pdn = nullptr;
   uint32_t* lf[2] = {nullptr, nullptr};
@@ -186,8 +185,7 @@ void carve_field(Bump& b, const Geom& G, int dtype, bool with_outputs, FieldBufs
   B.fdir = (uint8_t*)b.take(n);
   B.gdir = (uint8_t*)b.take(n);
   B.flags = (uint8_t*)b.take(nt * kEmitTile);
-  B.Mf = (int32_t*)b.take(n * 4);
-  B.mf = (int32_t*)b.take(n * 4);
+  B.term = (uint32_t*)b.take(n * 4);
   const size_t nf = exit_slots(G);
   for (int d = 0; d < 2; ++d) {
     B.lf[d] = (uint32_t*)b.take(nf * 4);
@@ -317,11 +315,13 @@ struct Group {
       F.fdir = B.fdir;
       F.gdir = B.gdir;
       F.flags = B.flags;
-      F.Mf = B.Mf;
-      F.mf = B.mf;
+      // f's labels are resolved straight into the output arrays: the loop
+      // ends only when g's labels equal them, so they are the final labels
+      F.Mf = B.Pup;
+      F.mf = B.Pdn;
       F.Pup = B.Pup;
       F.Pdn = B.Pdn;
-      F.term = reinterpret_cast<uint32_t*>(B.Pup);
+      F.term = B.term;
       for (int d = 0; d < 2; ++d) {
         F.lf[d] = B.lf[d];
         F.lw[d] = B.lw[d];

@@ -1837,16 +1837,8 @@ __global__ void __launch_bounds__(kThreads) k_emit_count(GroupArgs<T> A) {
     const Field<T>& F = A.fields[i];
     const int tile = u_ - pre[i];
     const int base = tile * kEmitTile + threadIdx.x * kEmitItems;
-    // final labels of g: the loop ends only after an R-check found every
-    // vertex's g labels equal to f's, whose labels are resolved in Mf / mf
-    // (a field stopped by the round cap has no final labels)
-    const int v1 = min(F.G.n, (tile + 1) * kEmitTile);
-    if (F.st->phase == PH_DONE) {
-      for (int v = tile * kEmitTile + threadIdx.x; v < v1; v += kThreads) {
-        F.Pup[v] = F.Mf[v];
-        F.Pdn[v] = F.mf[v];
-      }
-    }
+    // (the final labels are already in place: f's, resolved into the
+    // output arrays, which g's equal once the loop has converged)
     __syncthreads();
     if (threadIdx.x == 0) s = 0;
     __syncthreads();
