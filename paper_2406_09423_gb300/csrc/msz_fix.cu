@@ -540,6 +540,11 @@ struct msz_engine_s {
   void* block = nullptr;  // owned device block (null for the static scratch)
   size_t block_bytes = 0;
   cudaStream_t cap_stream = nullptr;
+  // groups after the first run their steps on these streams, forked from
+  // and joined back into the launching stream (engines with several groups)
+  cudaStream_t grp_stream[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[3] = {nullptr, nullptr, nullptr};
   cudaGraphExec_t graph = nullptr;
   bool use_graph = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -637,6 +642,11 @@ int setup_groups(msz_engine_s* E) {
 void free_engine(msz_engine_s* E) {
   if (E->graph) cudaGraphExecDestroy(E->graph);
   if (E->cap_stream) cudaStreamDestroy(E->cap_stream);
+  for (int k = 0; k < 3; ++k) {
+    if (E->grp_stream[k]) cudaStreamDestroy(E->grp_stream[k]);
+    if (E->join_ev[k]) cudaEventDestroy(E->join_ev[k]);
+  }
+  if (E->fork_ev) cudaEventDestroy(E->fork_ev);
   if (E->block) cudaFree(E->block);
   if (E->in_f) cudaFree(E->in_f);
   if (E->in_fhat) cudaFree(E->in_fhat);
@@ -752,15 +762,52 @@ int64_t engine_bytes(int nf, const int* ndim, const int64_t* dims, const int* dt
   return bytes;
 }
 
+// Issues `steps` steps of every group on stream s (also inside a stream
+// capture). The groups' fields are disjoint and every kernel touches only its
+// own group's fields, so with several groups each runs its steps on a stream
+// of its own, forked from s and joined back into it: one group's latency-bound
+// rounds no longer wait behind another's.
+int issue_steps(msz_engine_s* E, cudaStream_t s, int steps, int jumps) {
+  int ng = 0;
+  E->each_group([&](auto& g) { ng += g.empty() ? 0 : 1; });
+  if (ng <= 1) {
+    for (int i = 0; i < steps; ++i) E->each_group([&](auto& g) { g.step(s, jumps); });
+    return MSZ_OK;
+  }
+  if (!E->fork_ev && cudaEventCreateWithFlags(&E->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+    return MSZ_ERR_CUDA;
+  for (int k = 0; k < ng - 1; ++k) {
+    if (!E->grp_stream[k] && cudaStreamCreateWithFlags(&E->grp_stream[k], cudaStreamNonBlocking) != cudaSuccess)
+      return MSZ_ERR_CUDA;
+    if (!E->join_ev[k] && cudaEventCreateWithFlags(&E->join_ev[k], cudaEventDisableTiming) != cudaSuccess)
+      return MSZ_ERR_CUDA;
+  }
+  if (cudaEventRecord(E->fork_ev, s) != cudaSuccess) return MSZ_ERR_CUDA;
+  int k = 0, rc = MSZ_OK;
+  E->each_group([&](auto& g) {
+    if (g.empty() || rc != MSZ_OK) return;
+    cudaStream_t gs = (k == 0) ? s : E->grp_stream[k - 1];
+    if (k > 0 && cudaStreamWaitEvent(gs, E->fork_ev, 0) != cudaSuccess) rc = MSZ_ERR_CUDA;
+    for (int i = 0; i < steps; ++i) g.step(gs, jumps);
+    if (k > 0 && cudaEventRecord(E->join_ev[k - 1], gs) != cudaSuccess) rc = MSZ_ERR_CUDA;
+    ++k;
+  });
+  for (int j = 0; j < k - 1 && rc == MSZ_OK; ++j)
+    if (cudaStreamWaitEvent(s, E->join_ev[j], 0) != cudaSuccess) rc = MSZ_ERR_CUDA;
+  return rc;
+}
+
 // Timed runs keep kJumpsPerStep jump launches per step (the slot table of
-// the per-kernel statistics).
-void launch_steps(msz_engine_s* E, cudaStream_t s, int steps, bool timed) {
+// the per-kernel statistics; single-field engines).
+int launch_steps(msz_engine_s* E, cudaStream_t s, int steps, bool timed) {
   const int jumps = timed ? kJumpsPerStep : E->tune.jumps_per_step;
+  E->launches += (uint64_t)steps * E->launches_per_step(jumps);
+  if (!timed) return issue_steps(E, s, steps, jumps);
   for (int i = 0; i < steps; ++i) {
-    cudaEvent_t* e = timed ? E->tev[i] : nullptr;
+    cudaEvent_t* e = E->tev[i];
     E->each_group([&](auto& g) { g.step(s, jumps, e, E->d_steplog, i); });
   }
-  E->launches += (uint64_t)steps * E->launches_per_step(jumps);
+  return MSZ_OK;
 }
 
 // Per-launch device times of a timed chunk, split into launches that did work
@@ -796,9 +843,12 @@ int ensure_graph(msz_engine_s* E) {
     return MSZ_ERR_CUDA;
   cudaGraph_t gr = nullptr;
   if (cudaStreamBeginCapture(E->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MSZ_ERR_CUDA;
-  for (int i = 0; i < E->tune.graph_steps; ++i)
-    E->each_group([&](auto& g) { g.step(E->cap_stream, E->tune.jumps_per_step); });
-  if (cudaStreamEndCapture(E->cap_stream, &gr) != cudaSuccess) return MSZ_ERR_CUDA;
+  const int irc = issue_steps(E, E->cap_stream, E->tune.graph_steps, E->tune.jumps_per_step);
+  const cudaError_t ce = cudaStreamEndCapture(E->cap_stream, &gr);
+  if (irc != MSZ_OK || ce != cudaSuccess) {
+    if (gr) cudaGraphDestroy(gr);
+    return MSZ_ERR_CUDA;
+  }
   const cudaError_t r = cudaGraphInstantiate(&E->graph, gr, 0);
   cudaGraphDestroy(gr);
   return r == cudaSuccess ? MSZ_OK : MSZ_ERR_CUDA;
@@ -853,7 +903,7 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
       for (int i = 0; i < chunk; ++i) cudaGraphLaunch(E->graph, s);
       E->launches += (uint64_t)chunk * gsteps * E->launches_per_step(E->tune.jumps_per_step);
     } else {
-      launch_steps(E, s, std::min(chunk * gsteps, kMaxChunk), timed);
+      if (launch_steps(E, s, std::min(chunk * gsteps, kMaxChunk), timed) != MSZ_OK) return MSZ_ERR_CUDA;
     }
     if (cudaMemcpyAsync(H, E->d_states, sizeof(DevState) * nf, cudaMemcpyDeviceToHost, s) != cudaSuccess)
       return MSZ_ERR_CUDA;
@@ -1673,12 +1723,11 @@ void srv_worker(msz_server_s* S) {
     }
     // one chunk: init of newly admitted fields, steps, emission of converged ones
     E->each_group([&](auto& g) { g.init(S->stream); });
-    for (int k = 0; k < S->steps_per_chunk; ++k)
-      E->each_group([&](auto& g) { g.step(S->stream, E->tune.jumps_per_step); });
+    const bool issued = issue_steps(E, S->stream, S->steps_per_chunk, E->tune.jumps_per_step) == MSZ_OK;
     E->each_group([&](auto& g) { g.emit(S->stream); });
     S->launches += (uint64_t)S->steps_per_chunk * E->launches_per_step(E->tune.jumps_per_step);
     cudaMemcpyAsync(E->h_states, E->d_states, sizeof(DevState) * S->slots_n, cudaMemcpyDeviceToHost, S->stream);
-    const bool ok = cudaStreamSynchronize(S->stream) == cudaSuccess;
+    const bool ok = cudaStreamSynchronize(S->stream) == cudaSuccess && issued;
     const uint64_t t = now_ns();
     std::lock_guard<std::mutex> lk(S->mu);
     for (int i = 0; i < S->slots_n; ++i) {
