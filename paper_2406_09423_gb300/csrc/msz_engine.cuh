@@ -125,6 +125,7 @@ struct Field {
   Geom G;
   SweepTiling TL;
   int units[NKIND];
+  int small_cluster;  // blocks of the cluster that runs the field's small C-loop rounds
 };
 
 // Kernel argument: one (dtype, dimension) group of fields.

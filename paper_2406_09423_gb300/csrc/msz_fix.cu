@@ -244,7 +244,8 @@ struct Group {
   GroupArgs<T> args{};
   bool tma = false;
   int grid[NKIND] = {};
-  bool small_ok = false;  // a k_csmall cluster fits on the device
+  bool small_ok[2] = {false, false};  // a k_csmall cluster of 16 / 4 blocks fits on the device
+  bool small_has[2] = {false, false};  // some field's small rounds run in that cluster size
   size_t label_smem[2] = {0, 0};  // f's pass, g's passes
   int grid_label[2] = {0, 0};
   int grid_rcheck = 0;
@@ -301,7 +302,9 @@ struct Group {
   }
 
   // Builds descriptors, tensor maps, prefix sums and launch shapes.
-  int setup(const Geom* geoms, const FieldBufs* bufs, DevState* d_states, bool allow_tma, const msz_tuning& tn) {
+  // engine_fields: the fields of the whole engine (all groups)
+  int setup(const Geom* geoms, const FieldBufs* bufs, DevState* d_states, bool allow_tma, const msz_tuning& tn,
+            int engine_fields) {
     std::memset(h_maps, 0, sizeof(CUtensorMap) * 2 * nf);
     std::memset(h_prefix, 0, sizeof(int) * NKIND * (nf + 1));
     tma = allow_tma;
@@ -390,20 +393,33 @@ struct Group {
     grid_label[1] = occ_grid((const void*)k_label_tile<T, ND, true>, kThreads, label_smem[1], args.total[K_LABEL]);
     grid_rcheck = occ_grid((const void*)k_rcheck<T, ND>, kThreads, 0, args.total[K_LABEL]);
     if (cudaGetLastError() != cudaSuccess) return MSZ_ERR_CUDA;
-    {
+    // a device without clusters of a size runs those fields' rounds on the
+    // grid kernels; ncl: how many clusters of the size fit at once
+    auto cluster_fits = [&](const void* fn, int cs, int& ncl) {
       cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(kSmallCluster);
+      cfg.gridDim = dim3(cs);
       cfg.blockDim = dim3(kSmallThreads);
       cudaLaunchAttribute at;
       at.id = cudaLaunchAttributeClusterDimension;
-      at.val.clusterDim.x = kSmallCluster;
+      at.val.clusterDim.x = cs;
       at.val.clusterDim.y = at.val.clusterDim.z = 1;
       cfg.attrs = &at;
       cfg.numAttrs = 1;
-      int ncl = 0;
-      if (kSmallCluster > 8) cudaFuncSetAttribute(k_csmall<T, ND>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      small_ok = cudaOccupancyMaxActiveClusters(&ncl, k_csmall<T, ND>, &cfg) == cudaSuccess && ncl > 0;
-      cudaGetLastError();  // a device without clusters of this size runs every round on the grid kernels
+      ncl = 0;
+      if (cs > 8) cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      const bool ok = cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg) == cudaSuccess && ncl > 0;
+      cudaGetLastError();
+      return ok;
+    };
+    int ncl16 = 0, ncl4 = 0;
+    small_ok[0] = cluster_fits((const void*)k_csmall<T, ND, kSmallCluster>, kSmallCluster, ncl16);
+    small_ok[1] = cluster_fits((const void*)k_csmall<T, ND, kSmallClusterLite>, kSmallClusterLite, ncl4);
+    const bool lite = small_ok[1] && engine_fields > ncl16;  // more fields than 16-block clusters fit
+    small_has[0] = small_has[1] = false;
+    for (int j = 0; j < nf; ++j) {
+      Field<T>& F = h_fields[j];
+      F.small_cluster = (lite && F.G.n <= kSmallLiteVertices) ? kSmallClusterLite : kSmallCluster;
+      small_has[F.small_cluster == kSmallCluster ? 0 : 1] = true;
     }
     return MSZ_OK;
   }
@@ -473,7 +489,12 @@ struct Group {
     k_gather<T, ND><<<grid[K_CASE], kThreads, 0, s>>>(a());
     if (small) {
       const GroupArgs<T> x = a();  // the slot counts even when the kernel is left out
-      if (small_ok && args.small_rounds > 0) k_csmall<T, ND><<<nf * kSmallCluster, kSmallThreads, 0, s>>>(x);
+      if (args.small_rounds > 0) {
+        if (small_ok[0] && small_has[0])
+          k_csmall<T, ND, kSmallCluster><<<nf * kSmallCluster, kSmallThreads, 0, s>>>(x);
+        if (small_ok[1] && small_has[1])
+          k_csmall<T, ND, kSmallClusterLite><<<nf * kSmallClusterLite, kSmallThreads, 0, s>>>(x);
+      }
     }
     k_mark<T, ND><<<grid[K_SPARSE], kThreads, 0, s>>>(a());
   }
@@ -634,7 +655,7 @@ int setup_groups(msz_engine_s* E) {
   int rc = MSZ_OK;
   const bool allow_tma = !(E->opt.flags & MSZ_OPT_NO_TMA);
   E->each_group([&](auto& g) {
-    if (rc == MSZ_OK && !g.empty()) rc = g.setup(E->geoms, E->bufs, E->d_states, allow_tma, E->tune);
+    if (rc == MSZ_OK && !g.empty()) rc = g.setup(E->geoms, E->bufs, E->d_states, allow_tma, E->tune, E->nf);
   });
   return rc;
 }

@@ -1631,7 +1631,13 @@ __global__ void __launch_bounds__(kThreads) k_apply(GroupArgs<T> A) {
 // counters live in the shared memory of its block 0.
 // ---------------------------------------------------------------------------
 constexpr int kSmallThreads = 1024;
-constexpr int kSmallCluster = 16;  // blocks per field (a non-portable cluster size)
+constexpr int kSmallCluster = 16;     // blocks per field (a non-portable cluster size)
+constexpr int kSmallClusterLite = 4;  // blocks per small field of an engine with many fields
+// In an engine with more fields than 16-block clusters fit on the device at
+// once, fields of at most kSmallLiteVertices vertices take a 4-block cluster:
+// their rounds rarely hold more cases than it does, and a quarter of the SMs
+// per field lets four times as many fields run their rounds at once.
+constexpr int kSmallLiteVertices = 1 << 22;
 constexpr uint32_t kSmallSpan = (uint32_t)kSmallThreads * kSmallCluster;
 constexpr int kSmallPer = 4;  // cases per thread
 constexpr uint32_t kSmallCases = kSmallSpan * kSmallPer;  // the most a launch can hold (A.small_cases <= this)
@@ -1665,14 +1671,16 @@ __device__ __forceinline__ void warp_add_shared(const uint32_t (&v)[N], uint32_t
   }
 }
 
-template <class T, int ND>
-__global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallThreads) k_csmall(GroupArgs<T> A) {
-  const int fi = (int)blockIdx.x / kSmallCluster;  // a cluster per field
+template <class T, int ND, int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kSmallThreads) k_csmall(GroupArgs<T> A) {
+  constexpr uint32_t kSpan = (uint32_t)kSmallThreads * CS;  // the cluster's threads
+  const int fi = (int)blockIdx.x / CS;  // a cluster per field
   if (fi >= A.nf) return;
   const Field<T>& F = A.fields[fi];
+  if (F.small_cluster != CS) return;  // the field's rounds run in the other cluster size
   DevState* st = F.st;
   // the same for the whole cluster: nothing writes the state before the first barrier
-  const uint32_t cap = min(A.small_cases, kSmallCases);
+  const uint32_t cap = min(A.small_cases, kSpan * kSmallPer);
   if (!(st->phase == PH_C && st->action == ACT_REQUEST && st->ncase <= cap)) return;
   constexpr int R = 2 * Slots<ND>::NPOS + 1;
   // block 0's: touched count, freezes, next list length, go, apply sums (2), count changes (4)
@@ -1697,7 +1705,7 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
     int cv[kSmallPer];
 #pragma unroll
     for (int k = 0; k < kSmallPer; ++k) {
-      const uint32_t j = gt + (uint32_t)k * kSmallSpan;
+      const uint32_t j = gt + (uint32_t)k * kSpan;
       cv[k] = j < nc ? (int)F.cases[j] : -1;
       if (cv[k] >= 0 && !MSZ_IN(st, cv[k], F.G.n)) cv[k] = -1;
     }
@@ -1718,14 +1726,14 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
     cluster_barrier();
     if (const uint32_t nfz = C[1]) {
       // a warp per freeze, a lane per vertex of the anchor's closed ring
-      for (uint32_t q = gt >> 5; q < nfz; q += kSmallSpan >> 5)
+      for (uint32_t q = gt >> 5; q < nfz; q += kSpan >> 5)
         freeze_ring_warp<T, ND>(F, (int)F.lw[0][q], (int)(threadIdx.x & 31), ts);
       cluster_barrier();
     }
     const uint32_t nt = C[0];
     {
       uint32_t acc[2] = {0, 0};
-      for (uint32_t j = gt; j < nt; j += kSmallSpan) {
+      for (uint32_t j = gt; j < nt; j += kSpan) {
         const uint32_t u = F.touched[j];
         if (MSZ_IN(st, u, F.G.n)) apply_vertex(F, (int)u, acc);
       }
@@ -1744,7 +1752,7 @@ __global__ void __cluster_dims__(kSmallCluster, 1, 1) __launch_bounds__(kSmallTh
       // them: first the vertices the reclassification gives the type.
       const uint32_t stamp = (uint32_t)r1;
       uint32_t acc[4] = {0, 0, 0, 0};
-      for (uint32_t j = gt; j < nt * R; j += kSmallSpan) {
+      for (uint32_t j = gt; j < nt * R; j += kSpan) {
         int vc = 0;
         const uint32_t u = F.touched[j / R];
         const uint32_t ch = MSZ_IN(st, u, F.G.n) ? reclass_item<T, ND>(F, (int)u, (int)(j % R), stamp, acc, vc) : 0u;
