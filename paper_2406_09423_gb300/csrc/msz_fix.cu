@@ -252,6 +252,7 @@ struct Group {
 
   // Host arrays for nf fields (null pointers while measuring).
   void host_carve(HostArena& h) {
+    if (nf == 0) return;  // an empty group is never set up or launched
     members = h.take<int>(std::max(nf, 1));
     h_fields = h.take<Field<T>>(std::max(nf, 1));
     h_prefix = h.take<int>(NKIND * (nf + 1));
@@ -261,6 +262,7 @@ struct Group {
 
   // Device bytes of the group's descriptor arrays.
   void carve(Bump& b) {
+    if (nf == 0) return;
     d_fields = (Field<T>*)b.take(sizeof(Field<T>) * std::max(nf, 1), 64);
     d_prefix = (int*)b.take(sizeof(int) * NKIND * (nf + 1), 64);
     d_maps = (CUtensorMap*)b.take(sizeof(CUtensorMap) * 2 * std::max(nf, 1), 128);
@@ -520,6 +522,10 @@ struct Group {
 };
 
 constexpr int kMaxChunk = 32;
+// Groups per (dtype, dimension) class: a batch's fields of one class are
+// dealt to these in turn, so that fields that need many rounds hold back only
+// their own group's launches.
+constexpr int kSubGroups = 2;
 constexpr int kKinds = 4;
 
 // Defaults and ranges of msz_tuning.
@@ -554,18 +560,20 @@ struct msz_engine_s {
   DevState* d_states = nullptr;
   DevState* h_states = nullptr;  // pinned when owned, caller-provided otherwise
   bool h_states_pinned = false;
-  Group<float, 2> gf2;
-  Group<float, 3> gf3;
-  Group<double, 2> gd2;
-  Group<double, 3> gd3;
+  // a class's fields are dealt in turn to kSubGroups groups, each of which
+  // runs its steps on a stream of its own (issue_steps)
+  Group<float, 2> gf2[kSubGroups];
+  Group<float, 3> gf3[kSubGroups];
+  Group<double, 2> gd2[kSubGroups];
+  Group<double, 3> gd3[kSubGroups];
   void* block = nullptr;  // owned device block (null for the static scratch)
   size_t block_bytes = 0;
   cudaStream_t cap_stream = nullptr;
   // groups after the first run their steps on these streams, forked from
   // and joined back into the launching stream (engines with several groups)
-  cudaStream_t grp_stream[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t grp_stream[4 * kSubGroups - 1] = {};
   cudaEvent_t fork_ev = nullptr;
-  cudaEvent_t join_ev[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t join_ev[4 * kSubGroups - 1] = {};
   cudaGraphExec_t graph = nullptr;
   bool use_graph = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -584,10 +592,23 @@ struct msz_engine_s {
 
   template <class Fn>
   void each_group(Fn&& fn) {
-    fn(gf2);
-    fn(gf3);
-    fn(gd2);
-    fn(gd3);
+    for (int k = 0; k < kSubGroups; ++k) fn(gf2[k]);
+    for (int k = 0; k < kSubGroups; ++k) fn(gf3[k]);
+    for (int k = 0; k < kSubGroups; ++k) fn(gd2[k]);
+    for (int k = 0; k < kSubGroups; ++k) fn(gd3[k]);
+  }
+  // Calls fn on the group that takes the k-th field (counted from 0) of a
+  // class.
+  template <class Fn>
+  void class_group(int dtype, int nd, int k, Fn&& fn) {
+    const int j = k % kSubGroups;
+    if (dtype == MSZ_F32) {
+      if (nd == 3) fn(gf3[j]);
+      else fn(gf2[j]);
+    } else {
+      if (nd == 3) fn(gd3[j]);
+      else fn(gd2[j]);
+    }
   }
   int launches_per_step(int jumps) {
     int n = 0;
@@ -621,33 +642,27 @@ size_t layout_engine(msz_engine_s* E, unsigned char* base, bool with_outputs) {
   return b.off;
 }
 
-template <class G>
-G& group_of(msz_engine_s* E, int dtype, int nd) {
-  if (dtype == MSZ_F32) return *reinterpret_cast<G*>(nd == 3 ? (void*)&E->gf3 : (void*)&E->gf2);
-  return *reinterpret_cast<G*>(nd == 3 ? (void*)&E->gd3 : (void*)&E->gd2);
-}
 
 // Group sizes from the fields' dtypes and dimensions.
 void assign_counts(msz_engine_s* E, const int* ndim, const int* dtype) {
-  E->gf2.nf = E->gf3.nf = E->gd2.nf = E->gd3.nf = 0;
+  E->each_group([](auto& g) { g.nf = 0; });
+  int cls[4] = {0, 0, 0, 0};  // fields per class so far
   for (int i = 0; i < E->nf; ++i) {
-    if (dtype[i] == MSZ_F32) ++(ndim[i] == 3 ? E->gf3.nf : E->gf2.nf);
-    else ++(ndim[i] == 3 ? E->gd3.nf : E->gd2.nf);
+    int& k = cls[(dtype[i] == MSZ_F32 ? 0 : 2) + (ndim[i] == 3 ? 1 : 0)];
+    E->class_group(dtype[i], ndim[i], k++, [](auto& g) { ++g.nf; });
   }
 }
 
-// Fills the groups' member lists (host arrays must exist).
-void assign_members(msz_engine_s* E) {
-  int k2f = 0, k3f = 0, k2d = 0, k3d = 0;
-  for (int i = 0; i < E->nf; ++i) {
-    const bool d3 = E->geoms[i].nd == 3;
-    if (E->dtypes[i] == MSZ_F32) {
-      if (d3) E->gf3.members[k3f++] = i;
-      else E->gf2.members[k2f++] = i;
-    } else {
-      if (d3) E->gd3.members[k3d++] = i;
-      else E->gd2.members[k2d++] = i;
-    }
+// Fills the groups' member lists (host arrays must exist). fields: the
+// engine fields to place, in order (all of them, or a server's running slots).
+void assign_members(msz_engine_s* E, const int* fields, int n) {
+  E->each_group([](auto& g) { g.nf = 0; });
+  int cls[4] = {0, 0, 0, 0};
+  for (int j = 0; j < n; ++j) {
+    const int i = fields ? fields[j] : j;
+    const int nd = E->geoms[i].nd;
+    int& k = cls[(E->dtypes[i] == MSZ_F32 ? 0 : 2) + (nd == 3 ? 1 : 0)];
+    E->class_group(E->dtypes[i], nd, k++, [&](auto& g) { g.members[g.nf++] = i; });
   }
 }
 
@@ -663,7 +678,7 @@ int setup_groups(msz_engine_s* E) {
 void free_engine(msz_engine_s* E) {
   if (E->graph) cudaGraphExecDestroy(E->graph);
   if (E->cap_stream) cudaStreamDestroy(E->cap_stream);
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4 * kSubGroups - 1; ++k) {
     if (E->grp_stream[k]) cudaStreamDestroy(E->grp_stream[k]);
     if (E->join_ev[k]) cudaEventDestroy(E->join_ev[k]);
   }
@@ -694,7 +709,7 @@ int host_engine(msz_engine_s* E, int nf, const int* ndim, const int64_t* dims, c
     E->dtypes[i] = dtype[i];
     E->bufs[i] = FieldBufs{};
   }
-  assign_members(E);
+  assign_members(E, nullptr, E->nf);
   return MSZ_OK;
 }
 
@@ -900,7 +915,7 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
   if (E->ev0) cudaEventRecord(E->ev0, s);
   E->launches = 0;
   E->each_group([&](auto& g) { g.init(s); });
-  E->launches += (E->gf2.empty() ? 0 : 1) + (E->gf3.empty() ? 0 : 1) + (E->gd2.empty() ? 0 : 1) + (E->gd3.empty() ? 0 : 1);
+  E->each_group([&](auto& g) { E->launches += g.empty() ? 0 : 1; });
   const bool timed = (E->opt.flags & MSZ_OPT_TIME_KERNELS) != 0;
   if (timed && !E->tev_ready) {
     for (int i = 0; i < kMaxChunk; ++i)
@@ -955,8 +970,7 @@ int run_engine(msz_engine_s* E, const void* const* f, const void* const* fhat, c
     chunk = std::max(1, std::min(chunk * 2, kMaxChunk / gsteps));
   }
   E->each_group([&](auto& g) { g.emit(s); });
-  E->launches += 3ull * ((E->gf2.empty() ? 0 : 1) + (E->gf3.empty() ? 0 : 1) + (E->gd2.empty() ? 0 : 1) +
-                         (E->gd3.empty() ? 0 : 1));
+  E->each_group([&](auto& g) { E->launches += g.empty() ? 0ull : 3ull; });
   if (E->ev1) cudaEventRecord(E->ev1, s);
   if (cudaMemcpyAsync(H, E->d_states, sizeof(DevState) * nf, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return MSZ_ERR_CUDA;
@@ -1602,22 +1616,10 @@ namespace {
 // Group membership from the running slots; re-uploads descriptors.
 int srv_rebuild(msz_server_s* S) {
   msz_engine_s* E = S->E;
-  int k2f = 0, k3f = 0, k2d = 0, k3d = 0;
-  for (int i = 0; i < S->slots_n; ++i) {
-    if (S->slots[i].state != 1) continue;
-    const bool d3 = E->geoms[i].nd == 3;
-    if (E->dtypes[i] == MSZ_F32) {
-      if (d3) E->gf3.members[k3f++] = i;
-      else E->gf2.members[k2f++] = i;
-    } else {
-      if (d3) E->gd3.members[k3d++] = i;
-      else E->gd2.members[k2d++] = i;
-    }
-  }
-  E->gf2.nf = k2f;
-  E->gf3.nf = k3f;
-  E->gd2.nf = k2d;
-  E->gd3.nf = k3d;
+  std::vector<int> running;
+  for (int i = 0; i < S->slots_n; ++i)
+    if (S->slots[i].state == 1) running.push_back(i);
+  assign_members(E, running.data(), (int)running.size());
   int rc = setup_groups(E);
   if (rc != MSZ_OK) return rc;
   E->each_group([&](auto& g) {
