@@ -803,13 +803,17 @@ int64_t engine_bytes(int nf, const int* ndim, const int64_t* dims, const int* dt
 // own group's fields, so with several groups each runs its steps on a stream
 // of its own, forked from s and joined back into it: one group's latency-bound
 // rounds no longer wait behind another's.
-int issue_steps(msz_engine_s* E, cudaStream_t s, int steps, int jumps) {
+int nonempty_groups(msz_engine_s* E) {
   int ng = 0;
   E->each_group([&](auto& g) { ng += g.empty() ? 0 : 1; });
-  if (ng <= 1) {
-    for (int i = 0; i < steps; ++i) E->each_group([&](auto& g) { g.step(s, jumps); });
-    return MSZ_OK;
-  }
+  return ng;
+}
+
+// The streams and events that issue_steps forks onto (created outside any
+// stream capture).
+int ensure_group_streams(msz_engine_s* E) {
+  const int ng = nonempty_groups(E);
+  if (ng <= 1) return MSZ_OK;
   if (!E->fork_ev && cudaEventCreateWithFlags(&E->fork_ev, cudaEventDisableTiming) != cudaSuccess)
     return MSZ_ERR_CUDA;
   for (int k = 0; k < ng - 1; ++k) {
@@ -818,6 +822,16 @@ int issue_steps(msz_engine_s* E, cudaStream_t s, int steps, int jumps) {
     if (!E->join_ev[k] && cudaEventCreateWithFlags(&E->join_ev[k], cudaEventDisableTiming) != cudaSuccess)
       return MSZ_ERR_CUDA;
   }
+  return MSZ_OK;
+}
+
+int issue_steps(msz_engine_s* E, cudaStream_t s, int steps, int jumps) {
+  const int ng = nonempty_groups(E);
+  if (ng <= 1) {
+    for (int i = 0; i < steps; ++i) E->each_group([&](auto& g) { g.step(s, jumps); });
+    return MSZ_OK;
+  }
+  if (!E->fork_ev) return MSZ_ERR_CUDA;  // ensure_group_streams not called
   if (cudaEventRecord(E->fork_ev, s) != cudaSuccess) return MSZ_ERR_CUDA;
   int k = 0, rc = MSZ_OK;
   E->each_group([&](auto& g) {
@@ -838,7 +852,7 @@ int issue_steps(msz_engine_s* E, cudaStream_t s, int steps, int jumps) {
 int launch_steps(msz_engine_s* E, cudaStream_t s, int steps, bool timed) {
   const int jumps = timed ? kJumpsPerStep : E->tune.jumps_per_step;
   E->launches += (uint64_t)steps * E->launches_per_step(jumps);
-  if (!timed) return issue_steps(E, s, steps, jumps);
+  if (!timed) return ensure_group_streams(E) == MSZ_OK ? issue_steps(E, s, steps, jumps) : MSZ_ERR_CUDA;
   for (int i = 0; i < steps; ++i) {
     cudaEvent_t* e = E->tev[i];
     E->each_group([&](auto& g) { g.step(s, jumps, e, E->d_steplog, i); });
@@ -878,6 +892,7 @@ int ensure_graph(msz_engine_s* E) {
   if (!E->cap_stream && cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return MSZ_ERR_CUDA;
   cudaGraph_t gr = nullptr;
+  if (ensure_group_streams(E) != MSZ_OK) return MSZ_ERR_CUDA;
   if (cudaStreamBeginCapture(E->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MSZ_ERR_CUDA;
   const int irc = issue_steps(E, E->cap_stream, E->tune.graph_steps, E->tune.jumps_per_step);
   const cudaError_t ce = cudaStreamEndCapture(E->cap_stream, &gr);
@@ -1746,7 +1761,8 @@ void srv_worker(msz_server_s* S) {
     }
     // one chunk: init of newly admitted fields, steps, emission of converged ones
     E->each_group([&](auto& g) { g.init(S->stream); });
-    const bool issued = issue_steps(E, S->stream, S->steps_per_chunk, E->tune.jumps_per_step) == MSZ_OK;
+    const bool issued = ensure_group_streams(E) == MSZ_OK &&
+                        issue_steps(E, S->stream, S->steps_per_chunk, E->tune.jumps_per_step) == MSZ_OK;
     E->each_group([&](auto& g) { g.emit(S->stream); });
     S->launches += (uint64_t)S->steps_per_chunk * E->launches_per_step(E->tune.jumps_per_step);
     cudaMemcpyAsync(E->h_states, E->d_states, sizeof(DevState) * S->slots_n, cudaMemcpyDeviceToHost, S->stream);
