@@ -201,11 +201,13 @@ int msz_fix_host(msz_plan p, const void* orig_host, const void* decomp_host, dou
 
 /* Batched form: many independent fields of uneven shapes and mixed
  * float32 / float64 corrected together (Sec. 5's per-vertex parallelism
- * applied across fields). Every kernel of a step works on all fields of a
- * (dtype, dimension) group at once; each field keeps its own state machine
- * and drops out when it converges, so the results are bit-identical to
- * msz_fix on each field alone. The step sequence is captured once in a CUDA
- * graph and replayed.
+ * applied across fields). The fields of each (dtype, dimension) class are
+ * dealt in turn to two groups; every kernel of a step works on all fields of
+ * a group at once, and the groups run their steps concurrently on streams of
+ * their own, forked from and joined back into `stream`. Each field keeps its
+ * own state machine and drops out when it converges, so the results are
+ * bit-identical to msz_fix on each field alone. The step sequence is
+ * captured once in a CUDA graph and replayed.
  *   n fields; ndim[i], dims[3*i .. 3*i+2], dtype[i] as for msz_plan_create.
  *   msz_batch_fix: orig_dev[i], decomp_dev[i], xi[i] per field; results[i]
  *   receives field i's result (device arrays owned by the batch, valid until
