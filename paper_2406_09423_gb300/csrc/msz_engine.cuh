@@ -443,6 +443,54 @@ __device__ void ctrl_after_apply(DevState* st, uint32_t act) {
   ctrl_after_apply_counted(st, act);
 }
 
+// The same two transitions for the C-loop rounds of a thread-block cluster
+// (k_csmall), made by its one bookkeeping thread, which is the only writer of
+// the field's state during the launch and keeps the type counts and the round
+// number in registers: nothing is read from the state on the round's path.
+// In the C-loop the apply and R-check accumulators (acc_ap, acc_r) are zero,
+// so the apply's sums go straight into the counters; the increments are
+// atomics whose result is not used.
+//
+// After the apply of C-loop round r (its type's case count `cases`, before
+// the apply; max_rounds: st->max_rounds): what
+// ctrl_after_apply_counted(st, ACT_MARK_C) does.
+__device__ void ctrl_after_apply_small(DevState* st, uint32_t type, uint32_t dec, uint32_t frz, uint64_t cases,
+                                       uint32_t ntouch, uint64_t r, uint64_t max_rounds) {
+  atomicAdd((unsigned long long*)&st->cnt.dec_edits, (unsigned long long)dec);
+  atomicAdd((unsigned long long*)&st->cnt.freezes, (unsigned long long)frz);
+  atomicAdd((unsigned long long*)&st->cnt.c_rounds[type], 1ull);
+  atomicAdd((unsigned long long*)&st->cnt.c_cases[type], (unsigned long long)cases);
+  atomicAdd((unsigned long long*)&st->ticks, 1ull);
+  st->ntouch = ntouch;
+  st->rounds = r;
+  st->action = ACT_RECLASS;
+  if (r > max_rounds) {
+    st->phase = PH_ERR;
+    st->status = MSZ_ERR_NOCONVERGE;
+    st->action = ACT_NONE;
+  }
+}
+
+// After the reclassification that follows: the type counts c are stored;
+// when the type still has cases, at most cap of them, all len of them in the
+// case list, the state lists the next round (what ctrl_after_classify_counted
+// and the listing of the cases leave) and it returns true; otherwise the
+// general transition runs and it returns false.
+__device__ bool ctrl_after_classify_small(DevState* st, uint32_t type, const uint32_t (&c)[4], uint32_t len,
+                                          uint32_t cap, bool timeout) {
+  for (int t = 0; t < 4; ++t) st->counts[t] = c[t];
+  if (!timeout && c[type] != 0 && c[type] <= cap && len == c[type]) {
+    st->ntouch = 0;
+    st->ncase = len;
+    st->action = ACT_REQUEST;
+    atomicAdd((unsigned long long*)&st->cnt.sweeps, 1ull);
+    atomicAdd((unsigned long long*)&st->ticks, 1ull);
+    return true;
+  }
+  ctrl_after_classify_counted(st);
+  return false;
+}
+
 // ---------------------------------------------------------------------------
 // Edit requests (Sec. 5.1 deterministic mode): idempotent flags collected
 // from one snapshot of g, applied afterwards; a freeze overrides a decrease.

@@ -786,8 +786,8 @@ __device__ __forceinline__ uint32_t reclass_update(const Field<T>& F, int v, uin
 // One reclassification item: ring slot s of touched vertex u (slot 2 * NPOS:
 // u itself). The first item to reach a vertex in the round claims it (epoch
 // stamp) and recomputes its false-type bits and its direction byte in g; the
-// tile counts and acc move by the difference. When the bits change it
-// returns 0x10000 | (old << 8) | new and sets vc to the vertex, else 0.
+// tile counts and acc move by the difference. The claimer gets
+// 0x10000 | (old << 8) | new and vc = the vertex; any other item gets 0.
 template <class T, int ND>
 __device__ __forceinline__ uint32_t reclass_item(const Field<T>& F, int u, int s, uint32_t stamp, uint32_t (&acc)[4],
                                                  int& vc) {
@@ -806,14 +806,10 @@ __device__ __forceinline__ uint32_t reclass_item(const Field<T>& F, int u, int s
     if (x < 0 || x >= G.nx || y < 0 || y >= G.ny || z < 0 || z >= G.nz) return 0;
     v = u + dx + dy * G.nx + dz * G.nxny;
   }
-  // The class inputs load while the claim is in flight (g does not change
-  // during a reclassification); only the claimer uses them.
-  const uint32_t prev = atomicExch(&F.epoch[v], stamp);
-  const uint8_t dv = direction_of<T, ND>(F.g, G, v, x, y, z);
-  const uint8_t fd = F.fdir[v];
-  const unsigned ob = F.cls[v];
-  if (prev == stamp) return 0;
-  return reclass_update(F, v, dv, fd, ob, acc, vc);
+  // Only the claimer loads the class inputs: in a round whose rings
+  // overlap, most items lose the claim.
+  if (atomicExch(&F.epoch[v], stamp) == stamp) return 0;
+  return reclass_update(F, v, direction_of<T, ND>(F.g, G, v, x, y, z), F.fdir[v], F.cls[v], acc, vc);
 }
 
 // The same for vertex v at (x, y, z) without a claim (a pass over every vertex).
@@ -825,12 +821,14 @@ __device__ __forceinline__ uint32_t reclass_vertex(const Field<T>& F, int v, int
 
 // Vertex v's new direction byte dv in g, f's direction byte fd and its old
 // false-type bits ob: the byte and the bits are stored, the counts move.
+// Returns 0x10000 | (ob << 8) | nb and sets vc = v.
 template <class T>
 __device__ __forceinline__ uint32_t reclass_update(const Field<T>& F, int v, uint8_t dv, uint8_t fd, unsigned ob,
                                                    uint32_t (&acc)[4], int& vc) {
   F.gdir[v] = dv;  // g's direction bytes stay exact for the requests and the labels
   const unsigned nb = case_bits(dv, fd);
-  if (nb == ob) return 0;
+  vc = v;
+  if (nb == ob) return 0x10000u | (ob << 8) | nb;
   F.cls[v] = (uint8_t)nb;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
@@ -840,8 +838,7 @@ __device__ __forceinline__ uint32_t reclass_update(const Field<T>& F, int v, uin
       acc[c] += d;
     }
   }
-  vc = v;
-  return (ob << 8) | nb | 0x10000u;
+  return 0x10000u | (ob << 8) | nb;
 }
 
 // Incremental classification after an apply. A vertex's false-type bits
@@ -1682,23 +1679,37 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kSmallThreads) k_cs
   // the same for the whole cluster: nothing writes the state before the first barrier
   const uint32_t cap = min(A.small_cases, kSpan * kSmallPer);
   if (!(st->phase == PH_C && st->action == ACT_REQUEST && st->ncase <= cap)) return;
-  constexpr int R = 2 * Slots<ND>::NPOS + 1;
-  // block 0's: touched count, freezes, next list length, go, apply sums (2), count changes (4)
+  // The sub-loop's type stays while the cluster runs (a round of another type
+  // goes back to the grid), and each round adds one to st->rounds.
+  const uint32_t type = st->T;
+  uint64_t r1 = st->rounds;
+  const uint64_t max_rounds = st->max_rounds;
+  constexpr int NPOS = Slots<ND>::NPOS;
+  constexpr int R = 2 * NPOS + 1;
+  // block 0's: touched count, freezes, next list length, 1 + the round's case
+  // count (0: stop), apply sums (2), count changes (4)
   __shared__ uint32_t s_ctl[10];
   uint32_t* const C = in_block0(s_ctl);
   TouchSink ts;
   ts.n = &C[0];  // the cluster counts the round's touched list itself
   const uint32_t gt = cluster_rank() * kSmallThreads + threadIdx.x;
+  // the bookkeeping thread's copy of the type counts (it alone writes them
+  // during the launch), and whether the field has timed out
+  uint32_t cnt[4] = {0, 0, 0, 0};
+  bool timeout = false;
   if (gt == 0) {
     for (int k = 0; k < 10; ++k) C[k] = 0;
-    C[3] = 1;
+    C[3] = st->ncase + 1;
+    for (int c = 0; c < 4; ++c) cnt[c] = st->counts[c];
+    timeout = (vload(&st->err_bits) & E_TIMEOUT) != 0;
   }
   uint32_t rounds = 0;
   for (int it = 0; it < A.small_rounds; ++it) {
     cluster_barrier();  // the round's case list, state and counters are in place
-    if (!C[3]) break;
-    const uint32_t type = st->T, nc = st->ncase;
-    const uint64_t r1 = st->rounds + 1;  // the round's number once applied
+    const uint32_t go = C[3];
+    if (!go) break;
+    const uint32_t nc = go - 1;
+    ++r1;  // the round's number once applied
     // requests (Eqs. 2-5) for this thread's cases, all from one snapshot of
     // g: decreases at once; freezes are listed (lw[0], idle in the C-loop)
     // for the warps below, since a freeze marks a whole ring
@@ -1740,55 +1751,48 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kSmallThreads) k_cs
       warp_add_shared<2>(acc, C + 4);
     }
     cluster_barrier();
-    if (gt == 0) {
-      st->acc_ap[0] += C[4];
-      st->acc_ap[1] += C[5];
-      st->ntouch = nt;
-      ctrl_after_apply_counted(st, ACT_MARK_C);
-    }
-    if (r1 > st->max_rounds) break;  // the round cap: the bookkeeping above ends the fix
+    if (gt == 0) ctrl_after_apply_small(st, type, C[4], C[5], cnt[type], nt, r1, max_rounds);
+    if (r1 > max_rounds) break;  // the round cap: the bookkeeping above ends the fix
     {
-      // The old cases are in registers, so the next list can be written over
-      // them: first the vertices the reclassification gives the type.
+      // Reclassification, and the next list in the same pass: every vertex
+      // the round claims (the closed rings of the touched vertices, and this
+      // round's cases, each claimed by the thread holding it) is listed by
+      // its claimer when it has the type after the apply. A vertex no item
+      // claims kept its bits and was no case, so the list ends up holding
+      // every vertex of the type. The old cases are in registers, so the
+      // list is written over them. Ring items run from the top of the
+      // cluster's threads down, the cases sit at the bottom.
       const uint32_t stamp = (uint32_t)r1;
       uint32_t acc[4] = {0, 0, 0, 0};
-      for (uint32_t j = gt; j < nt * R; j += kSpan) {
-        int vc = 0;
-        const uint32_t u = F.touched[j / R];
-        const uint32_t ch = MSZ_IN(st, u, F.G.n) ? reclass_item<T, ND>(F, (int)u, (int)(j % R), stamp, acc, vc) : 0u;
-        if (((ch >> type) & 1u) && !((ch >> (8 + type)) & 1u)) {
+      auto list = [&](uint32_t ch, int vc) {
+        if ((ch >> type) & 1u) {
           const uint32_t q = atomicAdd(&C[2], 1u);
           if (MSZ_IN(st, q, F.G.n)) F.cases[q] = (uint32_t)vc;
         }
+      };
+      for (uint32_t j = kSpan - 1 - gt; j < nt * R; j += kSpan) {
+        int vc = 0;
+        const uint32_t u = F.touched[j / R];
+        list(MSZ_IN(st, u, F.G.n) ? reclass_item<T, ND>(F, (int)u, (int)(j % R), stamp, acc, vc) : 0u, vc);
       }
-      warp_add_shared<4>(acc, C + 6);
-    }
-    cluster_barrier();
-    // then this round's cases that kept the type
 #pragma unroll
-    for (int k = 0; k < kSmallPer; ++k)
-      if (cv[k] >= 0 && ((F.cls[cv[k]] >> type) & 1u)) {
-        const uint32_t q = atomicAdd(&C[2], 1u);
-        if (MSZ_IN(st, q, F.G.n)) F.cases[q] = (uint32_t)cv[k];
-      }
-    if (gt == 0) {
-      for (int c = 0; c < 4; ++c) st->counts[c] += C[6 + c];
-      ctrl_after_classify_counted(st);
+      for (int k = 0; k < kSmallPer; ++k)
+        if (cv[k] >= 0) {
+          int vc = 0;
+          list(reclass_item<T, ND>(F, cv[k], 2 * NPOS, stamp, acc, vc), vc);
+        }
+      warp_add_shared<4>(acc, C + 6);
     }
     cluster_barrier();
     ++rounds;
     if (gt == 0) {
+      for (int c = 0; c < 4; ++c) cnt[c] += C[6 + c];
       // go on with the same type while its round stays small and the list
       // holds every vertex of the type; otherwise the grid's gather lists it
       const uint32_t len = C[2];
-      const bool go = st->phase == PH_C && st->action == ACT_GATHER && st->T == type &&
-                      st->counts[type] <= cap && len == st->counts[type];
-      if (go) {
-        st->ncase = len;
-        st->action = ACT_REQUEST;
-      }
+      const bool more = ctrl_after_classify_small(st, type, cnt, len, cap, timeout);
       for (int k = 0; k < 10; ++k) C[k] = 0;
-      C[3] = go;
+      C[3] = more ? len + 1 : 0;
     }
   }
   // block 0's shared memory stays until every block is done with it
