@@ -548,8 +548,11 @@ __device__ __forceinline__ void mark(const Field<T>& F, int u, uint8_t bit, cons
 enum : int { RQ_DEC = 0, RQ_FROZEN = 1, RQ_BOUND = 2 };
 template <class T>
 __device__ __forceinline__ int request_cause(const Field<T>& F, int t) {
-  if (F.flags[t] & FL_FROZEN) return RQ_FROZEN;
-  return F.g[t] > lower_bound_of(F.f[t], F.xi) ? RQ_DEC : RQ_BOUND;
+  // the three loads issued together (one round trip, not two)
+  const uint8_t fl = F.flags[t];
+  const T gt = F.g[t], ft = F.f[t];
+  if (fl & FL_FROZEN) return RQ_FROZEN;
+  return gt > lower_bound_of(ft, F.xi) ? RQ_DEC : RQ_BOUND;
 }
 template <class T>
 __device__ __forceinline__ bool request_decreases(const Field<T>& F, int t) {

@@ -1564,13 +1564,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_rcheck(GroupArgs<T> A) {
 // tiles around u are marked dirty.
 template <class T>
 __device__ __forceinline__ void apply_vertex(const Field<T>& F, int u, uint32_t (&acc)[2]) {
+  // u's flags, g and f loaded together (one round trip, not two); no other
+  // thread writes them during the apply
   uint8_t bb = F.flags[u];
+  const T gu = F.g[u], fu = F.f[u];
   if (bb & FL_FREEZE) {
-    F.g[u] = F.f[u];
+    F.g[u] = fu;
     bb = (uint8_t)((bb & ~(FL_DEC | FL_FREEZE)) | FL_FROZEN | FL_EDITED);
     ++acc[1];
   } else if (bb & FL_DEC) {
-    F.g[u] = decrease(F.g[u], lower_bound_of(F.f[u], F.xi));
+    F.g[u] = decrease(gu, lower_bound_of(fu, F.xi));
     bb = (uint8_t)((bb & ~FL_DEC) | FL_EDITED);
     ++acc[0];
   }
