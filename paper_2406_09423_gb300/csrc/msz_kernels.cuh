@@ -1137,7 +1137,7 @@ __global__ void __launch_bounds__(kThreads, JOB ? 6 : 4) k_label_tile(GroupArgs<
         if (!MSZ_IN(st, b & kTermIdx, LG::HALO)) b = kTermFlag;
         const uint32_t a2 = double_half(PP, a, true);
         const uint32_t b2 = double_half(PP, b, false);
-        if (a2 != a || b2 != b) PP[c] = a2 | (b2 << 16);
+        PP[c] = a2 | (b2 << 16);  // stored even when unchanged: fewer instructions than the test
         if (a2 & b2 & kTermFlag) live &= ~(1u << k);
       }
     }
