@@ -618,21 +618,6 @@ __device__ __forceinline__ void freeze_ring_warp(const Field<T>& F, int a, int l
   if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE, ts);
 }
 
-// request() by a whole warp (lane = the thread's lane) for a case of kind
-// k: lane 0 decides; a freeze marks the closed 1-ring with one lane per
-// vertex.
-template <class T, int ND>
-__device__ __forceinline__ void request_warp(const Field<T>& F, int a, int t, int lane, int k) {
-  int cause = 0;
-  if (lane == 0) cause = request_cause(F, t);
-  cause = __shfl_sync(kFull, cause, 0);
-  if (cause == RQ_DEC) {
-    if (lane == 0) mark(F, t, FL_DEC);
-    return;
-  }
-  if (lane == 0) count_freeze_req(F.st, k, cause);
-  freeze_ring_warp<T, ND>(F, a, lane);
-}
 
 
 }  // namespace msz

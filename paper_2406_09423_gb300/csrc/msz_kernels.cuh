@@ -739,11 +739,14 @@ __global__ void __launch_bounds__(kThreads) k_gather(GroupArgs<T> A) {
   tl.flush(A, K_CASE, pre_flush, done);
 }
 
-// C-loop requests for the listed cases (Eqs. 2-5), one case per warp over
-// the whole grid (a freeze marks its ring one vertex per lane): FPmax and
-// FNmin edit the false vertex itself; FPmin and FNmax edit its neighbour
-// that is maximal in g, which is its steepest ascent since it is not a
-// maximum of g's ring.
+// C-loop requests for the listed cases (Eqs. 2-5), one case per thread over
+// the whole grid: FPmax and FNmin edit the false vertex itself; FPmin and
+// FNmax edit its neighbour that is maximal in g, which is its steepest ascent
+// since it is not a maximum of g's ring. A decrease is one flag mark; a
+// request that freezes its anchor's closed ring lists the anchor in shared
+// memory, and the block's warps mark the listed rings after its cases, a
+// lane per ring vertex. All requests read the same snapshot (nothing they
+// write is read by another request), so the order does not matter.
 template <class T, int ND>
 __global__ void __launch_bounds__(kThreads) k_mark(GroupArgs<T> A) {
   const int* pre = A.prefix + K_SPARSE * (A.nf + 1);
@@ -754,27 +757,44 @@ __global__ void __launch_bounds__(kThreads) k_mark(GroupArgs<T> A) {
     st->ticks++;
     log_work(A);
   };
+  constexpr uint32_t kMFreeze = 1024;
+  __shared__ uint32_t s_fz[kMFreeze];
+  __shared__ uint32_t s_nfz;
+  if (threadIdx.x == 0) s_nfz = 0;
   UnitTally tl;
   MSZ_ACTIVE_UNITS(A, K_SPARSE, pre, i, active) {
     const Field<T>& F = A.fields[i];
     DevState* st = F.st;
     uint64_t b, e;
-    // one case per warp: kThreads / 32 cases per unit
-    const uint32_t act = sparse_slice(st->ncase, F.units[K_SPARSE], u_ - pre[i], b, e, kThreads / 32);
+    const uint32_t act = sparse_slice(st->ncase, F.units[K_SPARSE], u_ - pre[i], b, e);
     if ((uint32_t)(u_ - pre[i]) >= act) continue;  // left out: not counted
     tl.enter(A, K_SPARSE, i, none, done);
     tl.target = act;
     const uint32_t type = st->T;
     if (threadIdx.x == 0) log_units(A, st, KID_MARK, e - b);
-    const int lane = threadIdx.x & 31;
-    for (uint64_t j = b + (threadIdx.x >> 5); j < e; j += kThreads / 32) {
+    __syncthreads();  // the freeze list is empty
+    for (uint64_t j = b + threadIdx.x; j < e; j += kThreads) {
       const int v = (int)F.cases[j];
       if (!MSZ_IN(st, v, F.G.n)) continue;
       const uint8_t d = F.gdir[v];  // exact: reclassified after every apply
       const int t = (type == FPMAX || type == FNMIN) ? v : v + slot_offset(d & 15, ND, F.G.nx, F.G.nxny);
       if (!MSZ_IN(st, t, F.G.n)) continue;
-      request_warp<T, ND>(F, v, t, lane, (int)type);
+      const int cause = request_cause(F, t);
+      if (cause == RQ_DEC) {
+        mark(F, t, FL_DEC);
+        continue;
+      }
+      count_freeze_req(st, (int)type, cause);
+      const uint32_t q = atomicAdd(&s_nfz, 1u);
+      if (q < kMFreeze) s_fz[q] = (uint32_t)v;
+      else request<T, ND>(F, v, t);  // list full: the same freeze, vertex by vertex
     }
+    __syncthreads();
+    const uint32_t nfz = min(s_nfz, kMFreeze);
+    for (uint32_t q = threadIdx.x >> 5; q < nfz; q += kThreads / 32)
+      freeze_ring_warp<T, ND>(F, (int)s_fz[q], (int)(threadIdx.x & 31));
+    __syncthreads();  // every thread has read the list and its count
+    if (threadIdx.x == 0) s_nfz = 0;
   }
   tl.flush(A, K_SPARSE, none, done);
 }
