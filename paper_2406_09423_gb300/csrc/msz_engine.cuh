@@ -618,6 +618,4 @@ __device__ __forceinline__ void freeze_ring_warp(const Field<T>& F, int a, int l
   if (!(F.flags[u] & FL_FROZEN)) mark(F, u, FL_FREEZE, ts);
 }
 
-
-
 }  // namespace msz
